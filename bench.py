@@ -1,0 +1,442 @@
+"""Benchmark: Sinkhorn WMD of one query against a paper-shaped corpus on GB300.
+
+One step = one whole query through the hot path (query prep, cost/kernel matrix,
+all Sinkhorn iterations, final distances) over the resident corpus of the
+paper-shaped workload (V=100,000, d=300, 5,000 documents of 10-300 Zipf words,
+v_r=19, lambda=1, 15 iterations).  Inputs are synthetic (see synth.py).
+
+  value      WMDs/s (documents x queries / device time), inputs resident in HBM,
+             L2 flushed (256 MiB write) before every timed step, outside the events.
+  e2e        WMDs/s through swmd_query with host buffers: the query's ids and
+             weights go host->device and the N distances device->host every step.
+  roofline   the dominant kernel of a step: algorithmic bytes or flops per launch
+             over its CUDA-event duration, against MEASURED_PEAKS.json.
+  paths      the same query on the resident, fused (one launch per iteration) and
+             plain (separate SDDMM and SpMM launches) paths, plus the per-iteration
+             kernel time and effective GB/s of fused vs plain.
+  cpu_baseline  the FP64 oracle timed on the host cores on a bounded sample.
+
+`--impl reference` times the oracle alone (the reference arm).  Under torchrun
+(N > 1) every rank holds its own 5,000-document partition (weak scaling, no
+collective on the data path) and rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "paper"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA), times the SM clock.
+SMS, FP32_LANES = 152, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--path", default="resident", choices=["resident", "fused", "plain"])
+    ap.add_argument("--kprec", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-paths", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except (OSError, ValueError):
+        return dict(FALLBACK_PEAKS), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ algorithmic counts
+def cost_counts(Vu, d, vrp, vr, kb):
+    """a1: reads the used embedding rows, writes K^T and KM^T; 3 flops per
+    (query word, word, dimension): subtract, multiply, add."""
+    byts = Vu * d * 4 + 2 * Vu * vrp * kb
+    flops = 3.0 * Vu * vr * d
+    return byts, flops
+
+
+def fused_iter_bytes(nnz, N, Vu, vrp, kb):
+    """a3 per launch: c's nonzeros (id + value), doc_ptr, K^T once, u read and written."""
+    return nnz * 8 + (N + 1) * 4 + Vu * vrp * kb + 2 * N * vrp * 4
+
+
+def plain_iter_bytes(nnz, N, Vu, vrp, kb):
+    """SDDMM (c, K^T, u; writes v) + SpMM (c, v, K^T; writes u)."""
+    return (nnz * 8 + (N + 1) * 4 + Vu * vrp * kb + N * vrp * 4 + nnz * 4) + \
+        (nnz * 8 + (N + 1) * 4 + nnz * 4 + Vu * vrp * kb + N * vrp * 4)
+
+
+def resident_counts(nnz, N, Vu, vrp, vr, kb, t):
+    """a3 x t + a4 in one launch: compulsory bytes (c, doc_ptr, K^T, KM^T, the
+    output) and flops: per nonzero and iteration 2 v_r FMAs + 1 divide (4 v_r + 1
+    flop), in the final step 2 dots and a divide and an add (4 v_r + 3)."""
+    byts = nnz * 8 + (N + 1) * 4 + 2 * Vu * vrp * kb + N * (8 + 4)
+    flops = float(t) * nnz * (4 * vr + 1) + nnz * (4 * vr + 3) + t * N * vr
+    return byts, flops
+
+
+# ------------------------------------------------------------------ oracle timing
+def time_oracle(E, C, qi, qw, lam, t, budget_s=12.0, max_runs=50):
+    import oracle
+    rp, col, val = C.csr()
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        oracle.wmd(E, rp, col, val, C.N, qi, qw, lam, t, "sparse")
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or runs >= max_runs:
+            break
+    return runs, el, oracle.get_threads()
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2107_06433_gb300 import synth
+    import oracle
+    w = synth.WORKLOADS[args.workload]
+    E, C, (qi, qw) = synth.make(w)
+    rp, col, val = C.csr()
+    oracle.build()
+    for _ in range(max(args.warmup, 0)):
+        oracle.wmd(E, rp, col, val, C.N, qi, qw, w.lam, w.max_iter)
+    # each step is one whole query; the step count is capped so the run stays bounded
+    steps = min(args.steps, 40)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oracle.wmd(E, rp, col, val, C.N, qi, qw, w.lam, w.max_iter)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = C.N * steps / total
+    cores = oracle.get_threads()
+    line = {
+        "impl": "reference", "metric": "WMDs/s", "value": value, "unit": "WMD/s",
+        "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(w, C),
+        "cpu_baseline": {"value": value, "unit": "WMD/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{steps} whole queries of the {w.name} workload "
+                                   f"({C.N} documents each), sparse FP64 mode"},
+        "e2e": {"value": value, "unit": "WMD/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(w, C):
+    return {"workload": w.name, "V": w.V, "d": w.d, "documents": C.N, "nnz": C.nnz,
+            "v_r": w.v_r, "lambda": w.lam, "max_iter": w.max_iter,
+            "doc_lengths": f"{w.len_kind} {w.len_lo}-{w.len_hi}",
+            "word_ids": "Zipf(1.1)", "l2": "flushed (256 MiB write) before every timed step"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import paper_2107_06433_gb300 as swmd
+    from paper_2107_06433_gb300 import build as nbuild, synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        pg = dist
+    nbuild.build()
+
+    w = synth.WORKLOADS[args.workload]
+    # weak scaling: rank r holds its own partition of w.N documents (its own seed)
+    E, C, (qi, qw) = synth.make(w, seed=synth.SEED + 7919 * rank)
+    if rank > 0:   # every rank answers the same query
+        _, _, (qi, qw) = synth.make(w)
+    kprec = {"fp32": 0, "bf16": 1, "fp16": 2}[args.kprec]
+    corpus = swmd.corpus_from_synth(E, C, path=args.path, k_precision=kprec, device=local)
+    info = corpus.info()
+    ids, r = swmd.swmd_select(C.V, qi, qw)
+    vr = len(ids)
+    d_ids = torch.from_numpy(ids).cuda()
+    d_r = torch.from_numpy(r).cuda()
+    d_out = torch.empty(C.N, dtype=torch.float64, device="cuda")
+    d_status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    lam, t = w.lam, w.max_iter
+
+    def one_step(ev=None):
+        # the query's launches, with events around the cost kernel and the solver
+        if ev is not None:
+            ev[0].record(stream)
+        swmd.swmd_step_cost(corpus, d_ids, d_r, vr, lam, d_status, stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+        if args.path == "resident":
+            swmd.swmd_step_resident(corpus, vr, t, d_out, stream=stream)
+        else:
+            swmd.swmd_step_iterate(corpus, vr, t, 1, args.path, stream=stream)
+            swmd.swmd_step_final(corpus, vr, int(t == 0), d_out, stream=stream)
+        if ev is not None:
+            ev[2].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            flush.zero_()
+            one_step()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for k in range(K):
+            flush.zero_()
+            one_step(evs[k])
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = sampler.stop()
+    cost_ms = [evs[k][0].elapsed_time(evs[k][1]) for k in range(K)]
+    solve_ms = [evs[k][1].elapsed_time(evs[k][2]) for k in range(K)]
+    step_ms = [a + b for a, b in zip(cost_ms, solve_ms)]
+    total_ms = sum(step_ms)
+    if pg:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    st = int(d_status.item())
+    out_dev = d_out.cpu().numpy()
+
+    # ---- e2e through the host API (host ids/weights in, host distances out)
+    e2e_steps = min(K, 500)
+    host_out = np.empty(C.N, np.float64)
+    for _ in range(3):
+        swmd.swmd_query(corpus, qi, qw, lam, t, out=host_out)
+    e2e_s = 0.0
+    for _ in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        swmd.swmd_query(corpus, qi, qw, lam, t, out=host_out)
+        e2e_s += time.perf_counter() - t0
+    if pg:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    assert np.array_equal(host_out, out_dev), "host and device entry points disagree"
+
+    # ---- roofline of the dominant kernel
+    peaks, peak_kind = load_peaks()
+    kb = 4 if kprec == 0 else 2
+    vrp = swmd.swmd_get_mapping(corpus, vr, args.path)[0]
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    cost_avg = statistics.mean(cost_ms) * 1e-3
+    solve_avg = statistics.mean(solve_ms) * 1e-3
+    cb, cf = cost_counts(info.V_used, w.d, vrp, vr, kb)
+    if args.path == "resident":
+        sb, sf = resident_counts(info.nnz, C.N, info.V_used, vrp, vr, kb, t)
+    else:
+        sb = t * fused_iter_bytes(info.nnz, C.N, info.V_used, vrp, kb)
+        sf = float(t + 1) * info.nnz * (4 * vr + 1)
+    alu_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s at the sampled clock
+    if solve_avg >= cost_avg:
+        name, dur, byts, flops = f"{args.path} solver (a3 x t + a4)", solve_avg, sb, sf
+    else:
+        name, dur, byts, flops = "cost/kernel matrix (a1)", cost_avg, cb, cf
+    ai = flops / byts
+    ridge = alu_peak * 1e12 / (peaks["hbm_gbs"] * 1e9)
+    if ai >= ridge:
+        ach = flops / dur / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": ach / alu_peak, "traffic": None, "kernel": name,
+                "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x "
+                               f"{sm_mhz:.0f} MHz (median sampled SM clock)",
+                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": byts}
+    else:
+        ach = byts / dur / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": name,
+                "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": byts, "algorithmic_flops_per_launch": flops}
+
+    line = {
+        "metric": "WMDs/s", "value": C.N * world * K / (total_ms * 1e-3), "unit": "WMD/s",
+        "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if kprec == 0 else args.kprec + "-K/f32",
+        "data": "synthetic", "config": config_dict(w, C) | {"path": args.path,
+                                                           "k_precision": args.kprec},
+        "e2e": {"value": C.N * world * e2e_steps / e2e_s, "unit": "WMD/s",
+                "h2d_bytes_per_step": int(len(qi) * 8), "d2h_bytes_per_step": int(C.N * 8 + 4)},
+        "roofline": roof,
+        "kernels_ms": {"cost": statistics.mean(cost_ms), "solver": statistics.mean(solve_ms)},
+        "gpu_launches": K * (3 if args.path == "resident" else
+                             (2 + t * (2 if args.path == "plain" else 1) + 1)),
+        "clocks": clocks, "status": st,
+    }
+    if rank == 0 and not args.no_paths:
+        line["paths"] = compare_paths(swmd, corpus, d_ids, d_r, d_out, d_status, flush, stream,
+                                      vr, vrp, lam, t, info, C, peaks, kb)
+    if rank == 0 and not args.no_cpu_baseline:
+        runs, el, cores = time_oracle(E, C, qi, qw, lam, t)
+        line["cpu_baseline"] = {"value": C.N * runs / el, "unit": "WMD/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"{runs} whole queries of the {w.name} workload "
+                                          f"({C.N} documents each), sparse FP64 mode"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def compare_paths(swmd, corpus, d_ids, d_r, d_out, d_status, flush, stream, vr, vrp, lam, t,
+                  info, C, peaks, kb):
+    """Whole-query time of each path, and the per-iteration fused vs plain kernels."""
+    import torch
+    res = {}
+    reps = 50
+    for path in ("resident", "fused", "plain"):
+        swmd.swmd_corpus_set_options(corpus, path=path)
+        times = []
+        with torch.cuda.stream(stream):
+            for k in range(reps + 3):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                swmd.swmd_query_device(corpus, d_ids, d_r, vr, lam, t, d_out, d_status,
+                                       stream=stream)
+                b.record(stream)
+                if k >= 3:
+                    times.append((a, b))
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in times)
+        res[path] = {"ms_per_query": ms, "wmds_per_s": C.N / (ms * 1e-3)}
+    swmd.swmd_corpus_set_options(corpus, path="resident")
+    # per-iteration kernels: one fused launch vs one SDDMM + one SpMM launch
+    per = {}
+    for path in ("fused", "plain"):
+        with torch.cuda.stream(stream):
+            swmd.swmd_step_cost(corpus, d_ids, d_r, vr, lam, d_status, stream=stream)
+            swmd.swmd_step_iterate(corpus, vr, 1, 1, path, stream=stream)
+            evs = []
+            for k in range(reps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                swmd.swmd_step_iterate(corpus, vr, 1, 0, path, stream=stream)
+                b.record(stream)
+                evs.append((a, b))
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        byts = (fused_iter_bytes if path == "fused" else plain_iter_bytes)(
+            info.nnz, C.N, info.V_used, vrp, kb)
+        per[path] = {"ms_per_iteration": ms, "algorithmic_bytes": byts,
+                     "gbs": byts / (ms * 1e-3) / 1e9,
+                     "frac_of_hbm": byts / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+    res["iteration_kernel"] = per
+    res["fusion_speedup"] = per["plain"]["ms_per_iteration"] / per["fused"]["ms_per_iteration"]
+    return res
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,275 @@
+/*
+ * swmd.h -- C ABI of the GB300 Sinkhorn Word Mover's Distance library (libswmd).
+ *
+ * The library computes the entropic Sinkhorn WMD of one query document against
+ * every document of a corpus, as the paper "A New Parallel Algorithm for Sinkhorn
+ * Word-Movers Distance Using Fused SDDMM-SpMM" (arXiv 2107.06433) states the
+ * problem: sinkhorn_wmd(r, c, vecs, lambda, max_iter) -> WMD[N] (Section III-B1),
+ * computed with Algorithm 1 (Section III-A) in its sparse, fused SDDMM-SpMM
+ * form (Sections III-B4 and III-C).
+ *
+ * Conventions for every call:
+ *   - Return value: SWMD_OK (0) or one of the SWMD_E* codes below.  Nothing
+ *     throws across the ABI.  swmd_last_error() gives a message for the last
+ *     failing call on the calling thread.
+ *   - Pointers named h_* or documented as host memory are host pointers owned by
+ *     the caller; the library copies what it needs during the call and does not
+ *     keep them.  Pointers named d_* are device pointers on the corpus's GPU,
+ *     owned by the caller, that must stay valid until the stream work of the
+ *     call has completed.
+ *   - A corpus (and a server) owns every device allocation it makes.  Calls on
+ *     one corpus are not thread-safe unless stated; use one server or one
+ *     corpus per thread.
+ *   - `stream` arguments are cudaStream_t values passed as void*; NULL means the
+ *     corpus's own stream.
+ */
+#ifndef SWMD_H
+#define SWMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SWMD_API __attribute__((visibility("default")))
+#else
+#define SWMD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define SWMD_OK 0
+#define SWMD_EINVAL 1     /* an argument or input violates the documented contract */
+#define SWMD_ENOMEM 2     /* a host or device allocation failed, or admission refused */
+#define SWMD_ECUDA 3      /* a CUDA runtime call failed; the message names it */
+#define SWMD_ETIMEDOUT 4  /* a wait ran out of time */
+#define SWMD_ENUMERIC 5   /* a NaN, an infinity or a vanished denominator was produced */
+#define SWMD_ESTOPPED 6   /* the server has been stopped */
+
+/* K and K.*M storage precision (accumulation is always FP32). */
+#define SWMD_K_FP32 0
+#define SWMD_K_BF16 1
+#define SWMD_K_FP16 2
+
+/* How the t Sinkhorn iterations run.
+ *   FUSED:    one fused SDDMM-SpMM launch per iteration (Section III-C), u
+ *             kept in HBM between iterations.
+ *   PLAIN:    separate SDDMM and SpMM launches per iteration, the unfused
+ *             formulation of Section III-B4 (writes v, then reads it back).
+ *   RESIDENT: all t iterations and the final step of a document in one launch,
+ *             u held on chip; legal because the documents (columns of c) are
+ *             independent problems in Algorithm 1. */
+#define SWMD_PATH_FUSED 0
+#define SWMD_PATH_PLAIN 1
+#define SWMD_PATH_RESIDENT 2
+
+typedef struct swmd_corpus swmd_corpus;
+typedef struct swmd_server swmd_server;
+
+typedef struct swmd_options {
+    int32_t k_precision;   /* SWMD_K_*; default SWMD_K_FP32 */
+    int32_t path;          /* SWMD_PATH_*; default SWMD_PATH_RESIDENT */
+    int32_t use_graph;     /* 1: replay the query's launches as a captured CUDA graph (default 1) */
+    int32_t column_shift;  /* 1: K'[k,w] = exp(-lambda (M[k,w] - min_k M[k,w])), an exact
+                              rescaling of the columns of K (default 1) */
+    int32_t max_vr;        /* largest query (distinct words) the workspace must hold;
+                              default 128, at most 128 */
+    int32_t device;        /* CUDA device ordinal; -1 = the current device (default) */
+    int32_t doc_begin;     /* documents [doc_begin, doc_end) of the CSR columns are loaded;
+                              -1/-1 = all.  One replica per GPU loads its own range. */
+    int32_t doc_end;
+    int32_t team_lanes;    /* 0 = autotuned; else lanes per document (1..32, power of 2) */
+    int32_t lanes_per_nz;  /* 0 = autotuned; else lanes sharing one nonzero's dot (power of 2) */
+    int32_t reserved[6];
+} swmd_options;
+
+/* Fills *opt with the defaults listed above. */
+SWMD_API void swmd_default_options(swmd_options *opt);
+
+/* Message of the last failing call on this thread ("" if none).  The pointer
+ * stays valid until the next call on this thread. */
+SWMD_API const char *swmd_last_error(void);
+
+/* ------------------------------------------------------------------ a0: query selection */
+/* Algorithm 1, first line, and Section III-B1: the query r is a histogram over
+ * the vocabulary; keep its positive entries (I = r > 0) and normalise them to
+ * sum 1.  Input: n (id, weight) pairs in host memory; ids repeat freely (their
+ * weights add up), weights must be finite and >= 0, ids in [0, V).
+ * Output (host, caller-allocated, capacity n): out_ids ascending, out_r
+ * summing to 1 (rounded from FP64).  *out_vr receives the number of distinct
+ * words.  SWMD_EINVAL if an id or weight is invalid or nothing is positive. */
+SWMD_API int swmd_select(int32_t V, int32_t n, const int32_t *h_ids, const float *h_weights,
+                int32_t *h_out_ids, float *h_out_r, int32_t *out_vr);
+
+/* ------------------------------------------------------------------ corpus */
+/* Section III-B1: c is a V x N sparse matrix passed as CSR, c[i, j] the
+ * frequency of word i in target document j; vecs is the V x d embedding matrix.
+ *   row_ptr[V+1] (int64, host): CSR row offsets, row_ptr[0] = 0, non-decreasing,
+ *       row_ptr[V] = nnz.
+ *   doc_idx[nnz] (int32, host): column (document) of each nonzero, in [0, N).
+ *   val[nnz] (float, host): the frequencies, finite and > 0.  Each column is
+ *       normalised to sum 1 here, in FP64 (the paper's columns sum to one).
+ *   emb[V*d] (float, host): row-major embeddings.
+ * Every document must have at least one word (an empty column has no defined
+ * distance): SWMD_EINVAL otherwise.  nnz < 2^31.  The corpus copies everything
+ * to the device, builds a document-major copy of c (documents ordered by
+ * length for load balance, words of a document ascending) and keeps only the
+ * vocabulary words that occur in c for the cost-matrix kernel.
+ * opt may be NULL (defaults).  On success *out owns the device memory. */
+SWMD_API int swmd_create_corpus(int32_t V, int32_t N, int64_t nnz, const int64_t *row_ptr,
+                       const int32_t *doc_idx, const float *val, const float *emb, int32_t d,
+                       const swmd_options *opt, swmd_corpus **out);
+
+/* Frees every device and host resource of the corpus.  NULL is ignored. */
+SWMD_API void swmd_destroy_corpus(swmd_corpus *corpus);
+
+typedef struct swmd_corpus_info {
+    int32_t V, N, d;
+    int32_t V_used;        /* vocabulary words that occur in c */
+    int64_t nnz;
+    int32_t doc_begin, doc_end;
+    int32_t device;
+    int64_t device_bytes;  /* bytes the corpus holds on the device, workspace included */
+} swmd_corpus_info;
+
+SWMD_API int swmd_corpus_get_info(const swmd_corpus *corpus, swmd_corpus_info *out);
+
+/* Changes the iteration path / K precision / graph use / mapping of later
+ * queries (fields as in swmd_options; the corpus-shape fields are ignored). */
+SWMD_API int swmd_corpus_set_options(swmd_corpus *corpus, const swmd_options *opt);
+
+/* ------------------------------------------------------------------ whole query */
+/* The paper's call sinkhorn_wmd(r, c, vecs, lambda, max_iter) (Section III-B1,
+ * Algorithm 1): distances of the query to every document of the corpus.
+ *   h_word_ids[n_words], h_weights[n_words]: the query as in swmd_select.
+ *   lambda: finite, > 0 (K = exp(-lambda M)).
+ *   max_iter: number t >= 0 of x-updates, then the final step.
+ *   h_out_dist[N] (host, caller-allocated): WMD_j for j in the corpus's
+ *       document range, in CSR column order, as double.
+ * Blocks until the result is in h_out_dist.  SWMD_ENUMERIC if a NaN, an
+ * infinity or a vanished K^T u appeared (the output is still written). */
+SWMD_API int swmd_query(swmd_corpus *corpus, const int32_t *h_word_ids, const float *h_weights,
+               int32_t n_words, float lambda, int32_t max_iter, double *h_out_dist);
+
+/* Same computation with a query already selected and normalised (swmd_select)
+ * and resident on the device, asynchronously on `stream`:
+ *   d_ids[v_r] (int32, device): distinct word ids in [0, V).
+ *   d_r[v_r] (float, device): weights summing to 1, all > 0.
+ *   d_out[N] (double, device): the distances.
+ * Returns after enqueueing; d_status (int32, device, may be NULL) receives 0 or
+ * an SWMD_E* code when the stream reaches it (ids out of range: SWMD_EINVAL;
+ * numerical failure: SWMD_ENUMERIC).  1 <= v_r <= max_vr. */
+SWMD_API int swmd_query_device(swmd_corpus *corpus, const int32_t *d_ids, const float *d_r, int32_t v_r,
+                      float lambda, int32_t max_iter, double *d_out, int32_t *d_status,
+                      void *stream);
+
+/* ------------------------------------------------------------------ the steps */
+/* The steps of swmd_query_device, one call each, for timing and testing; they
+ * share the corpus's workspace and must be called in this order for one query.
+ * All are asynchronous on `stream`.
+ *
+ * a0 (device part) + a1, cost matrix and kernel (Algorithm 1 first line; Table I
+ * "M = cdist(...)", "K = exp(-M*lamb)"; Section III-C "K.*M"): copies the
+ * selected query (d_ids[v_r], d_r[v_r] as in swmd_query_device; d_r may be NULL
+ * when only K is wanted) into the workspace, then for every used word w and query
+ * word k computes M[k,w] = ||E[q_k] - E[w]||_2, K = exp(-lambda M) (column-shifted
+ * if enabled) and K.*M, stored word-major (K^T[w][k], the KT layout of Section
+ * III-B4).  d_status (may be NULL) becomes the status word of this query for the
+ * later steps too. */
+SWMD_API int swmd_step_cost(swmd_corpus *corpus, const int32_t *d_ids, const float *d_r,
+                            int32_t v_r, float lambda, int32_t *d_status, void *stream);
+
+/* a2 + a3, n_iter Sinkhorn x-updates (Algorithm 1 loop; Algorithms 2-3 fused as
+ * SDDMM_SpMM, Section III-C): per document j and nonzero (w, c_wj),
+ * s = K^T[w] . u_j, tau = c_wj / s, acc_j += tau K^T[w]; then u_j = r / acc_j
+ * (that is x = diag(1/r) K v and u = 1/x).  first != 0 starts from x = 1/v_r.
+ * path: SWMD_PATH_FUSED (one launch per iteration) or SWMD_PATH_PLAIN (an SDDMM
+ * launch writing v, then an SpMM launch reading it). */
+SWMD_API int swmd_step_iterate(swmd_corpus *corpus, int32_t v_r, int32_t n_iter, int32_t first,
+                               int32_t path, void *stream);
+
+/* a4, final step (Algorithm 1 last two lines, SDDMM_SpMM type 2 of Section
+ * III-C): u = 1/x, v = c ./ (K^T u), WMD_j = sum_k u_kj ((K.*M) v)_kj, evaluated
+ * per nonzero as sum_w c_wj (KM^T[w] . u_j) / (K^T[w] . u_j) with an FP64
+ * per-document sum.  t0 != 0 means no iteration ran (u = v_r).  d_out[N]
+ * (double, device) receives the distances in CSR column order. */
+SWMD_API int swmd_step_final(swmd_corpus *corpus, int32_t v_r, int32_t t0, double *d_out,
+                             void *stream);
+
+/* a3 x max_iter + a4 in one launch (SWMD_PATH_RESIDENT), after swmd_step_cost. */
+SWMD_API int swmd_step_resident(swmd_corpus *corpus, int32_t v_r, int32_t max_iter,
+                                double *d_out, void *stream);
+
+/* The lane mapping the corpus uses for a query of v_r words on `path`:
+ * out[0] = VRP (v_r padded), out[1] = lanes sharing one nonzero (Q), out[2] =
+ * nonzeros in flight per document (P); a team of Q*P lanes owns a document. */
+SWMD_API int swmd_get_mapping(swmd_corpus *corpus, int32_t v_r, int32_t path, int32_t *out3);
+
+/* Copies a workspace array to host memory for inspection (tests):
+ *   what 0: K^T  [V_used][v_r] as float (FP32/BF16/FP16 widened)
+ *   what 1: KM^T [V_used][v_r] as float
+ *   what 2: u    [N][v_r] as float, CSR column order
+ *   what 3: the used word ids [V_used] as int32
+ * h_dst must hold the stated number of elements.  Synchronous. */
+SWMD_API int swmd_debug_read(swmd_corpus *corpus, int32_t what, int32_t v_r, void *h_dst);
+
+/* ------------------------------------------------------------------ batch */
+/* Several queries at once (Section III-D notes that many source documents can
+ * run together; the paper's multi-query experiment, Section V):
+ *   q_ptr[n_queries+1] (int64, host): query i is entries q_ptr[i]..q_ptr[i+1]-1
+ *       of h_word_ids / h_weights (each as in swmd_query).
+ *   h_lambdas[n_queries] (float, host): lambda of each query.
+ *   h_out[n_queries * N] (double, host): row i = the distances of query i.
+ * The result of each query equals its swmd_query result bit for bit. */
+SWMD_API int swmd_query_batch(swmd_corpus *corpus, int32_t n_queries, const int64_t *q_ptr,
+                     const int32_t *h_word_ids, const float *h_weights, const float *h_lambdas,
+                     int32_t max_iter, double *h_out);
+
+/* ------------------------------------------------------------------ serving */
+typedef struct swmd_serve_config {
+    int32_t max_batch;         /* queries admitted into one device batch (default 32) */
+    int64_t memory_budget;     /* device bytes for in-flight queries' K, K.*M and u (default 4 GiB) */
+    int32_t max_wait_us;       /* a partial batch is launched after this wait (default 200) */
+    int32_t queue_capacity;    /* pending requests accepted before submit refuses (default 4096) */
+    int32_t reserved[4];
+} swmd_serve_config;
+
+typedef struct swmd_serve_stats_t {
+    int64_t completed;
+    int64_t rejected;
+    double qps;        /* completed / seconds since start */
+    double p50_ms;     /* submit-to-result latency percentiles over completed requests */
+    double p99_ms;
+    double mean_batch; /* mean queries per device batch */
+    int64_t batches;
+} swmd_serve_stats_t;
+
+SWMD_API void swmd_default_serve_config(swmd_serve_config *cfg);
+
+/* Starts a serving thread over a resident corpus.  Requests are admitted into
+ * device batches as memory (K, K.*M and u of each query) frees up, and a batch
+ * runs while later requests queue (continuous batching).  cfg may be NULL. */
+SWMD_API int swmd_serve_start(swmd_corpus *corpus, const swmd_serve_config *cfg, swmd_server **out);
+
+/* Queues one query (host arrays copied during the call).  *ticket identifies it. */
+SWMD_API int swmd_serve_submit(swmd_server *srv, const int32_t *h_ids, const float *h_weights,
+                      int32_t n_words, float lambda, int32_t max_iter, uint64_t *ticket);
+
+/* Waits up to timeout_ms (< 0: forever) for the result of `ticket` and copies
+ * its N distances to h_out_dist.  SWMD_ETIMEDOUT if it is not ready in time
+ * (the request stays queued and can be waited for again). */
+SWMD_API int swmd_serve_wait(swmd_server *srv, uint64_t ticket, double *h_out_dist, int32_t timeout_ms);
+
+SWMD_API int swmd_serve_stats(swmd_server *srv, swmd_serve_stats_t *out);
+
+/* Stops the server after finishing in-flight batches; pending requests fail
+ * with SWMD_ESTOPPED.  Frees the server. */
+SWMD_API int swmd_serve_stop(swmd_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWMD_H */

@@ -1,0 +1,369 @@
+"""Python binding of libswmd, the GB300 Sinkhorn WMD library (arXiv 2107.06433).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libswmd.so``.  The functions carry the C ABI's names
+(``swmd_create_corpus``, ``swmd_query``, ...; see include/swmd.h).  Device
+buffers may be passed as torch CUDA tensors or raw integer addresses; streams
+as ``torch.cuda.Stream`` objects or raw ``cudaStream_t`` integers.
+
+There is no CPU fallback: if the library has not been built, importing the
+native layer raises ``ImportError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libswmd.so")
+
+SWMD_OK, SWMD_EINVAL, SWMD_ENOMEM, SWMD_ECUDA, SWMD_ETIMEDOUT, SWMD_ENUMERIC, SWMD_ESTOPPED = range(7)
+K_FP32, K_BF16, K_FP16 = 0, 1, 2
+PATH_FUSED, PATH_PLAIN, PATH_RESIDENT = 0, 1, 2
+_KPREC = {"fp32": K_FP32, "bf16": K_BF16, "fp16": K_FP16}
+_PATHS = {"fused": PATH_FUSED, "plain": PATH_PLAIN, "resident": PATH_RESIDENT}
+
+
+class SwmdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"swmd error {code}: {msg}")
+        self.code = code
+
+
+class swmd_options(ctypes.Structure):
+    _fields_ = [("k_precision", ctypes.c_int32), ("path", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("column_shift", ctypes.c_int32),
+                ("max_vr", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("doc_begin", ctypes.c_int32), ("doc_end", ctypes.c_int32),
+                ("team_lanes", ctypes.c_int32), ("lanes_per_nz", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class swmd_corpus_info(ctypes.Structure):
+    _fields_ = [("V", ctypes.c_int32), ("N", ctypes.c_int32), ("d", ctypes.c_int32),
+                ("V_used", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("doc_begin", ctypes.c_int32), ("doc_end", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+
+class swmd_serve_config(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("memory_budget", ctypes.c_int64),
+                ("max_wait_us", ctypes.c_int32), ("queue_capacity", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class swmd_serve_stats_t(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("qps", ctypes.c_double), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_batch", ctypes.c_double),
+                ("batches", ctypes.c_int64)]
+
+
+_lib = None
+
+P = ctypes.c_void_p
+_SIGS = {
+    "swmd_default_options": (None, [P]),
+    "swmd_last_error": (ctypes.c_char_p, []),
+    "swmd_select": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, P, P, P, P, P]),
+    "swmd_create_corpus": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, P, P, P,
+                                          P, ctypes.c_int32, P, P]),
+    "swmd_destroy_corpus": (None, [P]),
+    "swmd_corpus_get_info": (ctypes.c_int, [P, P]),
+    "swmd_corpus_set_options": (ctypes.c_int, [P, P]),
+    "swmd_query": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.c_float, ctypes.c_int32, P]),
+    "swmd_query_device": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.c_float, ctypes.c_int32,
+                                         P, P, P]),
+    "swmd_step_cost": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.c_float, P, P]),
+    "swmd_step_iterate": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, P]),
+    "swmd_step_final": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P, P]),
+    "swmd_step_resident": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P, P]),
+    "swmd_get_mapping": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P]),
+    "swmd_debug_read": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P]),
+    "swmd_query_batch": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P, ctypes.c_int32, P]),
+    "swmd_default_serve_config": (None, [P]),
+    "swmd_serve_start": (ctypes.c_int, [P, P, P]),
+    "swmd_serve_submit": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.c_float, ctypes.c_int32,
+                                         P]),
+    "swmd_serve_wait": (ctypes.c_int, [P, ctypes.c_uint64, P, ctypes.c_int32]),
+    "swmd_serve_stats": (ctypes.c_int, [P, P]),
+    "swmd_serve_stop": (ctypes.c_int, [P]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libswmd.so (ImportError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _err(code: int, what: str):
+    if code != SWMD_OK:
+        msg = lib().swmd_last_error()
+        raise SwmdError(code, f"{what}: {msg.decode() if msg else ''}")
+
+
+def _np(a, dt):
+    a = np.ascontiguousarray(a, dtype=dt)
+    return a, a.ctypes.data_as(P)
+
+
+def _dptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return P(x)
+    return P(x.data_ptr())
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return P(s)
+    return P(s.cuda_stream)
+
+
+def swmd_default_options(**kw) -> swmd_options:
+    o = swmd_options()
+    lib().swmd_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "k_precision" and isinstance(v, str):
+            v = _KPREC[v]
+        if k == "path" and isinstance(v, str):
+            v = _PATHS[v]
+        setattr(o, k, int(v))
+    return o
+
+
+def swmd_select(V, ids, weights):
+    ids, pi = _np(ids, np.int32)
+    w, pw = _np(weights, np.float32)
+    n = len(ids)
+    out_ids = np.empty(max(n, 1), np.int32)
+    out_r = np.empty(max(n, 1), np.float32)
+    vr = ctypes.c_int32(0)
+    _err(lib().swmd_select(V, n, pi, pw, out_ids.ctypes.data_as(P), out_r.ctypes.data_as(P),
+                           ctypes.byref(vr)), "swmd_select")
+    return out_ids[:vr.value].copy(), out_r[:vr.value].copy()
+
+
+class Corpus:
+    """Owns a swmd_corpus*; destroyed with the object."""
+
+    def __init__(self, handle, N):
+        self._h = handle
+        self.N = N
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().swmd_destroy_corpus(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> swmd_corpus_info:
+        return swmd_corpus_get_info(self)
+
+
+def swmd_create_corpus(V, N, row_ptr, doc_idx, val, emb, opt: swmd_options | None = None,
+                       **kw) -> Corpus:
+    """c as V x N CSR (row_ptr int64[V+1], doc_idx int32[nnz], val float32[nnz]); emb [V, d]."""
+    rp, prp = _np(row_ptr, np.int64)
+    di, pdi = _np(doc_idx, np.int32)
+    vv, pvv = _np(val, np.float32)
+    E, pE = _np(emb, np.float32)
+    assert E.ndim == 2 and E.shape[0] == V
+    if opt is None:
+        opt = swmd_default_options(**kw)
+    h = P()
+    _err(lib().swmd_create_corpus(V, N, int(rp[-1]), prp, pdi, pvv, pE, E.shape[1],
+                                  ctypes.byref(opt), ctypes.byref(h)), "swmd_create_corpus")
+    b = opt.doc_begin if opt.doc_begin >= 0 else 0
+    e = opt.doc_end if opt.doc_end >= 0 else N
+    return Corpus(h, e - b)
+
+
+def swmd_destroy_corpus(corpus: Corpus):
+    corpus.close()
+
+
+def swmd_corpus_get_info(corpus: Corpus) -> swmd_corpus_info:
+    info = swmd_corpus_info()
+    _err(lib().swmd_corpus_get_info(corpus.handle, ctypes.byref(info)), "swmd_corpus_get_info")
+    return info
+
+
+def swmd_corpus_set_options(corpus: Corpus, opt: swmd_options | None = None, **kw):
+    if opt is None:
+        opt = swmd_default_options(**kw)
+    _err(lib().swmd_corpus_set_options(corpus.handle, ctypes.byref(opt)), "swmd_corpus_set_options")
+
+
+def swmd_query(corpus: Corpus, ids, weights, lam: float, max_iter: int, out=None) -> np.ndarray:
+    """Distances (float64[N]) of the query to every document; host in, host out."""
+    ids, pi = _np(ids, np.int32)
+    w, pw = _np(weights, np.float32)
+    if out is None:
+        out = np.empty(corpus.N, np.float64)
+    _err(lib().swmd_query(corpus.handle, pi, pw, len(ids), float(lam), int(max_iter),
+                          out.ctypes.data_as(P)), "swmd_query")
+    return out
+
+
+def swmd_query_device(corpus: Corpus, d_ids, d_r, v_r: int, lam: float, max_iter: int, d_out,
+                      d_status=None, stream=None):
+    _err(lib().swmd_query_device(corpus.handle, _dptr(d_ids), _dptr(d_r), int(v_r), float(lam),
+                                 int(max_iter), _dptr(d_out), _dptr(d_status), _stream(stream)),
+         "swmd_query_device")
+
+
+def swmd_step_cost(corpus: Corpus, d_ids, d_r, v_r, lam, d_status=None, stream=None):
+    _err(lib().swmd_step_cost(corpus.handle, _dptr(d_ids), _dptr(d_r), int(v_r), float(lam),
+                              _dptr(d_status), _stream(stream)), "swmd_step_cost")
+
+
+def swmd_step_iterate(corpus: Corpus, v_r, n_iter, first, path="fused", stream=None):
+    path = _PATHS[path] if isinstance(path, str) else int(path)
+    _err(lib().swmd_step_iterate(corpus.handle, int(v_r), int(n_iter), int(first), path,
+                                 _stream(stream)), "swmd_step_iterate")
+
+
+def swmd_step_final(corpus: Corpus, v_r, t0, d_out, stream=None):
+    _err(lib().swmd_step_final(corpus.handle, int(v_r), int(t0), _dptr(d_out), _stream(stream)),
+         "swmd_step_final")
+
+
+def swmd_step_resident(corpus: Corpus, v_r, max_iter, d_out, stream=None):
+    _err(lib().swmd_step_resident(corpus.handle, int(v_r), int(max_iter), _dptr(d_out),
+                                  _stream(stream)), "swmd_step_resident")
+
+
+def swmd_get_mapping(corpus: Corpus, v_r: int, path="resident"):
+    """(VRP, lanes per nonzero Q, nonzeros in flight per document P)."""
+    path = _PATHS[path] if isinstance(path, str) else int(path)
+    out = (ctypes.c_int32 * 3)()
+    _err(lib().swmd_get_mapping(corpus.handle, int(v_r), path, out), "swmd_get_mapping")
+    return int(out[0]), int(out[1]), int(out[2])
+
+
+def swmd_debug_read(corpus: Corpus, what: str, v_r: int = 0) -> np.ndarray:
+    info = corpus.info()
+    code = {"KT": 0, "KMT": 1, "u": 2, "used": 3}[what]
+    if code == 3:
+        out = np.empty(info.V_used, np.int32)
+    elif code == 2:
+        out = np.empty((corpus.N, v_r), np.float32)
+    else:
+        out = np.empty((info.V_used, v_r), np.float32)
+    _err(lib().swmd_debug_read(corpus.handle, code, int(v_r), out.ctypes.data_as(P)),
+         "swmd_debug_read")
+    return out
+
+
+def swmd_query_batch(corpus: Corpus, queries, lambdas, max_iter: int) -> np.ndarray:
+    """queries: list of (ids, weights).  Returns float64[n_queries, N]."""
+    n = len(queries)
+    q_ptr = np.zeros(n + 1, np.int64)
+    for i, (qi, _) in enumerate(queries):
+        q_ptr[i + 1] = q_ptr[i] + len(qi)
+    ids = np.concatenate([np.asarray(q[0], np.int32) for q in queries]) if n else np.zeros(0, np.int32)
+    ws = np.concatenate([np.asarray(q[1], np.float32) for q in queries]) if n else np.zeros(0, np.float32)
+    lam, plam = _np(np.broadcast_to(np.asarray(lambdas, np.float32), (n,)), np.float32)
+    ids, pids = _np(ids, np.int32)
+    ws, pws = _np(ws, np.float32)
+    out = np.empty((n, corpus.N), np.float64)
+    _err(lib().swmd_query_batch(corpus.handle, n, q_ptr.ctypes.data_as(P), pids, pws, plam,
+                                int(max_iter), out.ctypes.data_as(P)), "swmd_query_batch")
+    return out
+
+
+class Server:
+    def __init__(self, handle, corpus: Corpus):
+        self._h = handle
+        self.corpus = corpus     # keeps the corpus alive while serving
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stop(self):
+        if self._h:
+            _err(lib().swmd_serve_stop(self._h), "swmd_serve_stop")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
+
+
+def swmd_default_serve_config(**kw) -> swmd_serve_config:
+    cfg = swmd_serve_config()
+    lib().swmd_default_serve_config(ctypes.byref(cfg))
+    for k, v in kw.items():
+        setattr(cfg, k, int(v))
+    return cfg
+
+
+def swmd_serve_start(corpus: Corpus, cfg: swmd_serve_config | None = None, **kw) -> Server:
+    if cfg is None:
+        cfg = swmd_default_serve_config(**kw)
+    h = P()
+    _err(lib().swmd_serve_start(corpus.handle, ctypes.byref(cfg), ctypes.byref(h)),
+         "swmd_serve_start")
+    return Server(h, corpus)
+
+
+def swmd_serve_submit(srv: Server, ids, weights, lam: float, max_iter: int) -> int:
+    ids, pi = _np(ids, np.int32)
+    w, pw = _np(weights, np.float32)
+    t = ctypes.c_uint64(0)
+    _err(lib().swmd_serve_submit(srv.handle, pi, pw, len(ids), float(lam), int(max_iter),
+                                 ctypes.byref(t)), "swmd_serve_submit")
+    return t.value
+
+
+def swmd_serve_wait(srv: Server, ticket: int, timeout_ms: int = -1) -> np.ndarray:
+    out = np.empty(srv.corpus.N, np.float64)
+    _err(lib().swmd_serve_wait(srv.handle, ctypes.c_uint64(ticket), out.ctypes.data_as(P),
+                               int(timeout_ms)), "swmd_serve_wait")
+    return out
+
+
+def swmd_serve_stats(srv: Server) -> dict:
+    s = swmd_serve_stats_t()
+    _err(lib().swmd_serve_stats(srv.handle, ctypes.byref(s)), "swmd_serve_stats")
+    return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+def swmd_serve_stop(srv: Server):
+    srv.stop()
+
+
+def corpus_from_synth(E, C, **kw) -> Corpus:
+    """Convenience: a corpus from paper_2107_06433_gb300.synth outputs."""
+    rp, col, val = C.csr()
+    return swmd_create_corpus(C.V, C.N, rp, col, val, E, **kw)

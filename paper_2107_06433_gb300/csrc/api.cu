@@ -1,0 +1,701 @@
+// C ABI of libswmd: corpus construction, the single query and its steps.
+//
+// The problem statement is the paper's sinkhorn_wmd(r, c, vecs, lambda, max_iter)
+// (Section III-B1): a query histogram r over the vocabulary, a V x N CSR c whose
+// columns are target documents, the V x d embeddings vecs; the answer is the
+// Sinkhorn distance of r to every column of c (Algorithm 1).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "corpus.h"
+
+namespace swmd {
+
+static thread_local std::string g_error;
+
+int set_error(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return set_error(e == cudaErrorMemoryAllocation ? SWMD_ENOMEM : SWMD_ECUDA, "%s: %s", what,
+                     cudaGetErrorString(e));
+}
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+int dev_alloc(T **p, size_t count, int64_t *bytes) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if (bytes) *bytes += (int64_t)(count * sizeof(T));
+    return SWMD_OK;
+}
+
+void dev_free(void *p) {
+    if (p) cudaFree(p);
+}
+
+int max_vrp_of(int max_vr) { return vrp_for(max_vr, 8); }
+
+}  // namespace
+
+int status_to_code(int st) {
+    if (st & (ST_BAD_ID | ST_BAD_R))
+        return set_error(SWMD_EINVAL, "query id outside [0, V) or weight not finite and > 0");
+    if (st & ST_NUMERIC)
+        return set_error(SWMD_ENUMERIC, "a NaN, an infinity or a vanished K^T u appeared");
+    return SWMD_OK;
+}
+
+int alloc_slot(swmd_corpus *c, Slot &s, int max_vr, int kprec, bool with_v) {
+    free_slot(s);
+    const int vrp = max_vrp_of(max_vr);
+    const size_t kb = kprec_bytes(kprec);
+    int rc;
+    unsigned char *kt = nullptr, *kmt = nullptr;
+    if ((rc = dev_alloc(&kt, (size_t)std::max(c->Vu, 1) * vrp * kb, &s.bytes))) return rc;
+    s.KT = kt;
+    if ((rc = dev_alloc(&kmt, (size_t)std::max(c->Vu, 1) * vrp * kb, &s.bytes))) return rc;
+    s.KMT = kmt;
+    if ((rc = dev_alloc(&s.u, (size_t)std::max(c->Nl, 1) * vrp, &s.bytes))) return rc;
+    if (with_v && (rc = dev_alloc(&s.v, (size_t)std::max<int64_t>(c->nnz, 1), &s.bytes))) return rc;
+    if ((rc = dev_alloc(&s.q_ids, vrp, &s.bytes))) return rc;
+    if ((rc = dev_alloc(&s.r, vrp, &s.bytes))) return rc;
+    if ((rc = dev_alloc(&s.qp, 1, &s.bytes))) return rc;
+    if ((rc = dev_alloc(&s.out, (size_t)std::max(c->Nl, 1), &s.bytes))) return rc;
+    if ((rc = dev_alloc(&s.status, 1, &s.bytes))) return rc;
+    if ((rc = dev_alloc(&s.q_in, vrp, &s.bytes))) return rc;
+    if ((rc = dev_alloc(&s.r_in, vrp, &s.bytes))) return rc;
+    SWMD_CK(cudaMemset(s.u, 0, (size_t)std::max(c->Nl, 1) * vrp * sizeof(float)));
+    s.vrp_cap = vrp;
+    s.kprec = kprec;
+    return SWMD_OK;
+}
+
+void free_slot(Slot &s) {
+    dev_free(s.KT); dev_free(s.KMT); dev_free(s.u); dev_free(s.v); dev_free(s.q_ids);
+    dev_free(s.r); dev_free(s.qp); dev_free(s.out); dev_free(s.status); dev_free(s.q_in);
+    dev_free(s.r_in);
+    s = Slot{};
+}
+
+// Lane mapping of the walk for a query of vr words.  P (nonzeros in flight per
+// document) follows the mean document length; Q (lanes per nonzero) keeps the
+// per-lane slice S = VRP / Q at or below 32 registers.
+Mapping choose_mapping(swmd_corpus *c, int vr, int path) {
+    const int tl = c->opt.team_lanes, lq = c->opt.lanes_per_nz;
+    if (tl > 0 && lq > 0 && tl % lq == 0) {
+        Mapping m{vrp_for(vr, lq), lq, tl / lq};
+        if (mapping_supported(m)) return m;
+    }
+    auto key = std::make_tuple(vr, path, c->opt.k_precision);
+    auto it = c->tuned.find(key);
+    if (it != c->tuned.end()) return it->second;
+    int q = vr <= 32 ? 1 : (vr <= 64 ? 2 : 4);
+    int p = c->mean_len >= 24.0 ? 8 : 4;
+    Mapping m{vrp_for(vr, q), q, p};
+    if (!mapping_supported(m)) m.p = 4;
+    if (!mapping_supported(m)) {
+        // fall back to the smallest supported layout of this width
+        for (int qq = 1; qq <= 8; qq *= 2) {
+            Mapping t{vrp_for(vr, qq), qq, 4};
+            if (mapping_supported(t)) return t;
+        }
+    }
+    return m;
+}
+
+static int launch_sequence(swmd_corpus *c, Slot &s, Mapping m, int t, int path, int kprec,
+                           int shift, cudaStream_t st) {
+    CostArgs ca{};
+    ca.E = c->E;
+    ca.d4 = c->d4;
+    ca.used = c->used;
+    ca.Vu = c->Vu;
+    ca.q_ids = s.q_ids;
+    ca.qp = s.qp;
+    ca.V = c->V;
+    ca.shift = shift;
+    ca.KT = s.KT;
+    ca.KMT = s.KMT;
+    SWMD_CK(launch_cost(ca, m.vrp, kprec, st));
+
+    IterArgs ia{};
+    ia.doc_ptr = c->doc_ptr;
+    ia.nz = c->nz;
+    ia.KT = s.KT;
+    ia.KMT = s.KMT;
+    ia.u = s.u;
+    ia.r = s.r;
+    ia.v = s.v;
+    ia.doc_orig = c->doc_orig;
+    ia.qp = s.qp;
+    ia.doc0 = 0;
+    ia.N = c->Nl;
+    if (path == SWMD_PATH_RESIDENT) {
+        ResidentArgs ra{ia, t};
+        ra.it.first = 1;
+        SWMD_CK(launch_resident(ra, m, kprec, c->sms, st));
+        return SWMD_OK;
+    }
+    for (int it = 0; it < t; ++it) {
+        ia.first = it == 0;
+        if (path == SWMD_PATH_PLAIN) {
+            SWMD_CK(launch_sddmm(ia, m, kprec, c->sms, st));
+            ia.first = 0;
+            SWMD_CK(launch_spmm(ia, m, kprec, c->sms, st));
+        } else {
+            SWMD_CK(launch_fused(ia, m, kprec, c->sms, st));
+        }
+    }
+    ia.first = t == 0;
+    SWMD_CK(launch_final(ia, m, kprec, c->sms, st));
+    return SWMD_OK;
+}
+
+int enqueue_query(swmd_corpus *c, Slot &s, const int *d_ids, const float *d_r, int vr,
+                  float lambda, int t, double *d_out, int *d_status, cudaStream_t st,
+                  bool allow_graph) {
+    const int path = c->opt.path;
+    const int kprec = c->opt.k_precision;
+    if (!s.external && (s.kprec != kprec || (path == SWMD_PATH_PLAIN && !s.v))) {
+        // buffers move: every captured graph of this corpus is stale
+        for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+        c->graphs.clear();
+        int rc = alloc_slot(c, s, c->opt.max_vr, kprec, path == SWMD_PATH_PLAIN);
+        if (rc) return rc;
+    }
+    const Mapping m = choose_mapping(c, vr, path);
+    SWMD_CK(launch_prep(s.qp, lambda, vr, c->V, d_ids, d_r, s.q_ids, s.r, s.vrp_cap, d_out,
+                        d_status ? d_status : s.status, st));
+    const int shift = c->opt.column_shift ? 1 : 0;
+    if (!(allow_graph && c->opt.use_graph)) return launch_sequence(c, s, m, t, path, kprec, shift, st);
+
+    GraphKey key{m.vrp, m.q, m.p, t, path, kprec, shift, (const void *)&s};
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+        // The launch sequence of a new shape is captured once on the corpus's own
+        // stream and replayed on the caller's stream from then on.
+        cudaGraph_t g = nullptr;
+        SWMD_CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+        int rc = launch_sequence(c, s, m, t, path, kprec, shift, c->stream);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        SWMD_CK(e);
+        cudaGraphExec_t ge = nullptr;
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        SWMD_CK(e);
+        it = c->graphs.emplace(key, ge).first;
+    }
+    SWMD_CK(cudaGraphLaunch(it->second, st));
+    return SWMD_OK;
+}
+
+}  // namespace swmd
+
+using namespace swmd;
+
+extern "C" {
+
+void swmd_default_options(swmd_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof *opt);
+    opt->k_precision = SWMD_K_FP32;
+    opt->path = SWMD_PATH_RESIDENT;
+    opt->use_graph = 1;
+    opt->column_shift = 1;
+    opt->max_vr = 128;
+    opt->device = -1;
+    opt->doc_begin = -1;
+    opt->doc_end = -1;
+}
+
+const char *swmd_last_error(void) { return g_error.c_str(); }
+
+int swmd_select(int32_t V, int32_t n, const int32_t *h_ids, const float *h_weights,
+                int32_t *h_out_ids, float *h_out_r, int32_t *out_vr) {
+    if (V <= 0 || n < 0 || (n > 0 && (!h_ids || !h_weights || !h_out_ids || !h_out_r)) ||
+        !out_vr)
+        return set_error(SWMD_EINVAL, "swmd_select: bad arguments");
+    // merge repeated ids (sum of weights), keep positive totals, ascending ids
+    std::vector<std::pair<int32_t, double>> e;
+    e.reserve(n);
+    for (int32_t i = 0; i < n; ++i) {
+        const double w = h_weights[i];
+        if (h_ids[i] < 0 || h_ids[i] >= V)
+            return set_error(SWMD_EINVAL, "swmd_select: word id %d outside [0, %d)", h_ids[i], V);
+        if (!(w >= 0.0) || std::isinf(w))
+            return set_error(SWMD_EINVAL, "swmd_select: weight %g of word %d is not finite and >= 0",
+                             w, h_ids[i]);
+        e.emplace_back(h_ids[i], w);
+    }
+    std::sort(e.begin(), e.end(),
+              [](const std::pair<int32_t, double> &a, const std::pair<int32_t, double> &b) {
+                  return a.first < b.first;
+              });
+    std::vector<std::pair<int32_t, double>> m;
+    for (auto &x : e) {
+        if (!m.empty() && m.back().first == x.first) m.back().second += x.second;
+        else m.push_back(x);
+    }
+    double total = 0.0;
+    int32_t k = 0;
+    for (auto &x : m)
+        if (x.second > 0.0) total += x.second;
+    for (auto &x : m)
+        if (x.second > 0.0) {
+            h_out_ids[k] = x.first;
+            h_out_r[k] = (float)(x.second / total);
+            ++k;
+        }
+    if (k == 0) return set_error(SWMD_EINVAL, "swmd_select: no word has a positive weight");
+    *out_vr = k;
+    return SWMD_OK;
+}
+
+int swmd_create_corpus(int32_t V, int32_t N, int64_t nnz, const int64_t *row_ptr,
+                       const int32_t *doc_idx, const float *val, const float *emb, int32_t d,
+                       const swmd_options *opt_in, swmd_corpus **out) {
+    if (!out) return set_error(SWMD_EINVAL, "swmd_create_corpus: out is NULL");
+    *out = nullptr;
+    swmd_options opt;
+    if (opt_in) opt = *opt_in;
+    else swmd_default_options(&opt);
+    if (V <= 0 || N < 0 || d <= 0 || nnz < 0 || nnz >= ((int64_t)1 << 31))
+        return set_error(SWMD_EINVAL, "swmd_create_corpus: need V > 0, N >= 0, d > 0, 0 <= nnz < 2^31");
+    if (!row_ptr || !emb || (nnz > 0 && (!doc_idx || !val)))
+        return set_error(SWMD_EINVAL, "swmd_create_corpus: NULL input array");
+    if (opt.max_vr <= 0) opt.max_vr = 128;
+    if (opt.max_vr > 128) return set_error(SWMD_EINVAL, "swmd_create_corpus: max_vr above 128");
+    if (opt.k_precision < 0 || opt.k_precision > 2 || opt.path < 0 || opt.path > 2)
+        return set_error(SWMD_EINVAL, "swmd_create_corpus: bad k_precision or path");
+    int b = opt.doc_begin < 0 ? 0 : opt.doc_begin;
+    int e = opt.doc_end < 0 ? N : opt.doc_end;
+    if (b > e || e > N) return set_error(SWMD_EINVAL, "swmd_create_corpus: bad document range");
+
+    // ---- validate the CSR (Section III-B1: c is V x N, passed as CSR)
+    if (row_ptr[0] != 0 || row_ptr[V] != nnz)
+        return set_error(SWMD_EINVAL, "swmd_create_corpus: row_ptr[0] must be 0 and row_ptr[V] = nnz");
+    const int Nl = e - b;
+    std::vector<int64_t> cnt((size_t)Nl + 1, 0);
+    std::vector<double> colsum((size_t)std::max(Nl, 1), 0.0);
+    std::vector<char> word_used((size_t)V, 0);
+    for (int32_t w = 0; w < V; ++w) {
+        if (row_ptr[w + 1] < row_ptr[w])
+            return set_error(SWMD_EINVAL, "swmd_create_corpus: row_ptr decreases at row %d", w);
+        for (int64_t p = row_ptr[w]; p < row_ptr[w + 1]; ++p) {
+            const int32_t j = doc_idx[p];
+            const float x = val[p];
+            if (j < 0 || j >= N)
+                return set_error(SWMD_EINVAL, "swmd_create_corpus: doc_idx[%lld] = %d outside [0, %d)",
+                                 (long long)p, j, N);
+            if (!(x > 0.f) || std::isinf(x))
+                return set_error(SWMD_EINVAL, "swmd_create_corpus: val[%lld] = %g is not finite and > 0",
+                                 (long long)p, (double)x);
+            if (j >= b && j < e) {
+                cnt[j - b + 1]++;
+                colsum[j - b] += (double)x;
+                word_used[w] = 1;
+            }
+        }
+    }
+    for (int j = 0; j < Nl; ++j)
+        if (cnt[j + 1] == 0)
+            return set_error(SWMD_EINVAL, "swmd_create_corpus: document %d has no words", j + b);
+
+    // ---- compact vocabulary: the words that occur in the loaded documents
+    std::vector<int32_t> compact((size_t)V, -1), used;
+    for (int32_t w = 0; w < V; ++w)
+        if (word_used[w]) {
+            compact[w] = (int32_t)used.size();
+            used.push_back(w);
+        }
+
+    // ---- document-major copy, documents in decreasing length (stable)
+    std::vector<int32_t> order((size_t)Nl);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t x, int32_t y) { return cnt[x + 1] > cnt[y + 1]; });
+    std::vector<int32_t> pos_of((size_t)Nl);
+    for (int i = 0; i < Nl; ++i) pos_of[order[i]] = i;
+    std::vector<int32_t> dptr((size_t)Nl + 1, 0);
+    for (int i = 0; i < Nl; ++i) dptr[i + 1] = dptr[i] + (int32_t)cnt[order[i] + 1];
+    const int64_t nnz_l = dptr[Nl];
+    std::vector<int2> nzh((size_t)std::max<int64_t>(nnz_l, 1));
+    std::vector<int32_t> fill((size_t)Nl, 0);
+    for (int32_t w = 0; w < V; ++w)   // rows ascending: each document lists its words ascending
+        for (int64_t p = row_ptr[w]; p < row_ptr[w + 1]; ++p) {
+            const int32_t j = doc_idx[p];
+            if (j < b || j >= e) continue;
+            const int32_t i = pos_of[j - b];
+            const float cv = (float)((double)val[p] / colsum[j - b]);
+            int2 t;
+            t.x = compact[w];
+            std::memcpy(&t.y, &cv, sizeof cv);
+            nzh[(size_t)dptr[i] + fill[i]++] = t;
+        }
+
+    auto *c = new swmd_corpus();
+    c->V = V;
+    c->N = N;
+    c->d = d;
+    c->d4 = (d + 3) / 4 * 4;
+    c->Vu = (int)used.size();
+    c->nnz = nnz_l;
+    c->doc_begin = b;
+    c->doc_end = e;
+    c->Nl = Nl;
+    c->opt = opt;
+    c->mean_len = Nl ? (double)nnz_l / Nl : 0.0;
+    c->len_sorted.resize((size_t)Nl);
+    for (int i = 0; i < Nl; ++i) c->len_sorted[i] = dptr[i + 1] - dptr[i];
+
+    int dev = opt.device;
+    if (dev < 0) {
+        cudaError_t ce = cudaGetDevice(&dev);
+        if (ce != cudaSuccess) {
+            delete c;
+            return cuda_fail(ce, "cudaGetDevice");
+        }
+    }
+    c->device = dev;
+    DeviceGuard guard(dev);
+    int rc = SWMD_OK;
+    auto bail = [&](int code) {
+        swmd_destroy_corpus(c);
+        return code;
+    };
+    {
+        cudaError_t ce = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+        if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaDeviceGetAttribute"));
+        ce = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamCreateWithFlags"));
+    }
+    if ((rc = dev_alloc(&c->E, (size_t)V * c->d4, &c->base_bytes))) return bail(rc);
+    if ((rc = dev_alloc(&c->used, (size_t)std::max(c->Vu, 1), &c->base_bytes))) return bail(rc);
+    if ((rc = dev_alloc(&c->doc_ptr, (size_t)Nl + 1, &c->base_bytes))) return bail(rc);
+    if ((rc = dev_alloc(&c->nz, (size_t)std::max<int64_t>(nnz_l, 1), &c->base_bytes))) return bail(rc);
+    if ((rc = dev_alloc(&c->doc_orig, (size_t)std::max(Nl, 1), &c->base_bytes))) return bail(rc);
+    cudaError_t ce;
+    if (c->d4 == d) {
+        ce = cudaMemcpy(c->E, emb, sizeof(float) * (size_t)V * d, cudaMemcpyHostToDevice);
+    } else {
+        ce = cudaMemset(c->E, 0, sizeof(float) * (size_t)V * c->d4);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy2D(c->E, sizeof(float) * c->d4, emb, sizeof(float) * d, sizeof(float) * d,
+                              V, cudaMemcpyHostToDevice);
+    }
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "copy embeddings"));
+    if (!used.empty() &&
+        (ce = cudaMemcpy(c->used, used.data(), sizeof(int32_t) * used.size(),
+                         cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(cuda_fail(ce, "copy used words"));
+    if ((ce = cudaMemcpy(c->doc_ptr, dptr.data(), sizeof(int32_t) * dptr.size(),
+                         cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(cuda_fail(ce, "copy doc_ptr"));
+    if (nnz_l > 0 && (ce = cudaMemcpy(c->nz, nzh.data(), sizeof(int2) * (size_t)nnz_l,
+                                      cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(cuda_fail(ce, "copy nonzeros"));
+    if (Nl > 0 && (ce = cudaMemcpy(c->doc_orig, order.data(), sizeof(int32_t) * (size_t)Nl,
+                                   cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(cuda_fail(ce, "copy document order"));
+    if ((rc = alloc_slot(c, c->main, opt.max_vr, opt.k_precision, opt.path == SWMD_PATH_PLAIN)))
+        return bail(rc);
+    *out = c;
+    return SWMD_OK;
+}
+
+void swmd_destroy_corpus(swmd_corpus *c) {
+    if (!c) return;
+    {
+        DeviceGuard guard(c->device);
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+        free_slot(c->main);
+        dev_free(c->E);
+        dev_free(c->used);
+        dev_free(c->doc_ptr);
+        dev_free(c->nz);
+        dev_free(c->doc_orig);
+        if (c->stream) cudaStreamDestroy(c->stream);
+    }
+    delete c;
+}
+
+int swmd_corpus_get_info(const swmd_corpus *c, swmd_corpus_info *out) {
+    if (!c || !out) return set_error(SWMD_EINVAL, "swmd_corpus_get_info: NULL argument");
+    out->V = c->V;
+    out->N = c->N;
+    out->d = c->d;
+    out->V_used = c->Vu;
+    out->nnz = c->nnz;
+    out->doc_begin = c->doc_begin;
+    out->doc_end = c->doc_end;
+    out->device = c->device;
+    out->device_bytes = c->base_bytes + c->main.bytes;
+    return SWMD_OK;
+}
+
+int swmd_corpus_set_options(swmd_corpus *c, const swmd_options *opt) {
+    if (!c || !opt) return set_error(SWMD_EINVAL, "swmd_corpus_set_options: NULL argument");
+    if (opt->k_precision < 0 || opt->k_precision > 2 || opt->path < 0 || opt->path > 2)
+        return set_error(SWMD_EINVAL, "swmd_corpus_set_options: bad k_precision or path");
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->opt.k_precision = opt->k_precision;
+    c->opt.path = opt->path;
+    c->opt.use_graph = opt->use_graph;
+    c->opt.column_shift = opt->column_shift;
+    c->opt.team_lanes = opt->team_lanes;
+    c->opt.lanes_per_nz = opt->lanes_per_nz;
+    return SWMD_OK;
+}
+
+static int check_query_args(swmd_corpus *c, int vr, float lambda, int t) {
+    if (!c) return set_error(SWMD_EINVAL, "NULL corpus");
+    if (vr < 1 || vr > c->opt.max_vr)
+        return set_error(SWMD_EINVAL, "query has %d distinct words; allowed 1..%d", vr, c->opt.max_vr);
+    if (!(lambda > 0.f) || std::isinf(lambda))
+        return set_error(SWMD_EINVAL, "lambda must be finite and > 0");
+    if (t < 0) return set_error(SWMD_EINVAL, "max_iter must be >= 0");
+    return SWMD_OK;
+}
+
+int swmd_query(swmd_corpus *c, const int32_t *h_word_ids, const float *h_weights, int32_t n_words,
+               float lambda, int32_t max_iter, double *h_out_dist) {
+    if (!c || (c->Nl > 0 && !h_out_dist)) return set_error(SWMD_EINVAL, "swmd_query: NULL argument");
+    std::vector<int32_t> ids((size_t)std::max(n_words, 1));
+    std::vector<float> r((size_t)std::max(n_words, 1));
+    int32_t vr = 0;
+    int rc = swmd_select(c->V, n_words, h_word_ids, h_weights, ids.data(), r.data(), &vr);
+    if (rc) return rc;
+    if ((rc = check_query_args(c, vr, lambda, max_iter))) return rc;
+    if (c->Nl == 0) return SWMD_OK;
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard guard(c->device);
+    Slot &s = c->main;
+    cudaStream_t st = c->stream;
+    SWMD_CK(cudaMemcpyAsync(s.q_in, ids.data(), sizeof(int32_t) * vr, cudaMemcpyHostToDevice, st));
+    SWMD_CK(cudaMemcpyAsync(s.r_in, r.data(), sizeof(float) * vr, cudaMemcpyHostToDevice, st));
+    if ((rc = enqueue_query(c, s, s.q_in, s.r_in, vr, lambda, max_iter, s.out, s.status, st, true)))
+        return rc;
+    int h_status = 0;
+    SWMD_CK(cudaMemcpyAsync(h_out_dist, s.out, sizeof(double) * c->Nl, cudaMemcpyDeviceToHost, st));
+    SWMD_CK(cudaMemcpyAsync(&h_status, s.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SWMD_CK(cudaStreamSynchronize(st));
+    return status_to_code(h_status);
+}
+
+int swmd_query_device(swmd_corpus *c, const int32_t *d_ids, const float *d_r, int32_t v_r,
+                      float lambda, int32_t max_iter, double *d_out, int32_t *d_status,
+                      void *stream) {
+    int rc = check_query_args(c, v_r, lambda, max_iter);
+    if (rc) return rc;
+    if (!d_ids || !d_r || (c->Nl > 0 && !d_out))
+        return set_error(SWMD_EINVAL, "swmd_query_device: NULL device pointer");
+    if (c->Nl == 0) return SWMD_OK;
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard guard(c->device);
+    cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+    return enqueue_query(c, c->main, d_ids, d_r, v_r, lambda, max_iter, d_out, d_status, st, true);
+}
+
+// ---------------------------------------------------------------- the steps
+static IterArgs iter_args(swmd_corpus *c, Slot &s) {
+    IterArgs ia{};
+    ia.doc_ptr = c->doc_ptr;
+    ia.nz = c->nz;
+    ia.KT = s.KT;
+    ia.KMT = s.KMT;
+    ia.u = s.u;
+    ia.r = s.r;
+    ia.v = s.v;
+    ia.doc_orig = c->doc_orig;
+    ia.qp = s.qp;
+    ia.doc0 = 0;
+    ia.N = c->Nl;
+    return ia;
+}
+
+int swmd_step_cost(swmd_corpus *c, const int32_t *d_ids, const float *d_r, int32_t v_r,
+                   float lambda, int32_t *d_status, void *stream) {
+    int rc = check_query_args(c, v_r, lambda, 0);
+    if (rc) return rc;
+    if (!d_ids) return set_error(SWMD_EINVAL, "swmd_step_cost: NULL ids");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard guard(c->device);
+    cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+    Slot &s = c->main;
+    if (s.kprec != c->opt.k_precision) {
+        for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+        c->graphs.clear();
+        if ((rc = alloc_slot(c, s, c->opt.max_vr, c->opt.k_precision, c->opt.path == SWMD_PATH_PLAIN)))
+            return rc;
+    }
+    const Mapping m = choose_mapping(c, v_r, c->opt.path);
+    SWMD_CK(launch_prep(s.qp, lambda, v_r, c->V, d_ids, d_r, s.q_ids, s.r, s.vrp_cap, s.out,
+                        d_status ? d_status : s.status, st));
+    CostArgs ca{};
+    ca.E = c->E;
+    ca.d4 = c->d4;
+    ca.used = c->used;
+    ca.Vu = c->Vu;
+    ca.q_ids = s.q_ids;
+    ca.qp = s.qp;
+    ca.V = c->V;
+    ca.shift = c->opt.column_shift ? 1 : 0;
+    ca.KT = s.KT;
+    ca.KMT = s.KMT;
+    SWMD_CK(launch_cost(ca, m.vrp, c->opt.k_precision, st));
+    return SWMD_OK;
+}
+
+int swmd_step_iterate(swmd_corpus *c, int32_t v_r, int32_t n_iter, int32_t first, int32_t path,
+                      void *stream) {
+    int rc = check_query_args(c, v_r, 1.f, n_iter);
+    if (rc) return rc;
+    if (path != SWMD_PATH_FUSED && path != SWMD_PATH_PLAIN)
+        return set_error(SWMD_EINVAL, "swmd_step_iterate: path must be FUSED or PLAIN");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard guard(c->device);
+    cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+    Slot &s = c->main;
+    if (path == SWMD_PATH_PLAIN && !s.v) {
+        int64_t extra = 0;
+        if ((rc = dev_alloc(&s.v, (size_t)std::max<int64_t>(c->nnz, 1), &extra))) return rc;
+        s.bytes += extra;
+        for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+        c->graphs.clear();
+    }
+    const Mapping m = choose_mapping(c, v_r, path);
+    IterArgs ia = iter_args(c, s);
+    for (int it = 0; it < n_iter; ++it) {
+        ia.first = (first && it == 0) ? 1 : 0;
+        if (path == SWMD_PATH_PLAIN) {
+            SWMD_CK(launch_sddmm(ia, m, c->opt.k_precision, c->sms, st));
+            ia.first = 0;
+            SWMD_CK(launch_spmm(ia, m, c->opt.k_precision, c->sms, st));
+        } else {
+            SWMD_CK(launch_fused(ia, m, c->opt.k_precision, c->sms, st));
+        }
+    }
+    return SWMD_OK;
+}
+
+int swmd_step_final(swmd_corpus *c, int32_t v_r, int32_t t0, double *d_out, void *stream) {
+    int rc = check_query_args(c, v_r, 1.f, 0);
+    if (rc) return rc;
+    if (!d_out && c->Nl > 0) return set_error(SWMD_EINVAL, "swmd_step_final: NULL output");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard guard(c->device);
+    cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+    Slot &s = c->main;
+    const Mapping m = choose_mapping(c, v_r, c->opt.path);
+    IterArgs ia = iter_args(c, s);
+    ia.first = t0 ? 1 : 0;
+    ia.out = d_out;
+    SWMD_CK(launch_final(ia, m, c->opt.k_precision, c->sms, st));
+    return SWMD_OK;
+}
+
+int swmd_step_resident(swmd_corpus *c, int32_t v_r, int32_t max_iter, double *d_out,
+                       void *stream) {
+    int rc = check_query_args(c, v_r, 1.f, max_iter);
+    if (rc) return rc;
+    if (!d_out && c->Nl > 0) return set_error(SWMD_EINVAL, "swmd_step_resident: NULL output");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard guard(c->device);
+    cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+    Slot &s = c->main;
+    const Mapping m = choose_mapping(c, v_r, SWMD_PATH_RESIDENT);
+    ResidentArgs ra{iter_args(c, s), max_iter};
+    ra.it.out = d_out;
+    SWMD_CK(launch_resident(ra, m, c->opt.k_precision, c->sms, st));
+    return SWMD_OK;
+}
+
+int swmd_get_mapping(swmd_corpus *c, int32_t v_r, int32_t path, int32_t *out3) {
+    if (!c || !out3) return set_error(SWMD_EINVAL, "swmd_get_mapping: NULL argument");
+    if (v_r < 1 || v_r > c->opt.max_vr) return set_error(SWMD_EINVAL, "swmd_get_mapping: bad v_r");
+    std::lock_guard<std::mutex> lk(c->mu);
+    const Mapping m = choose_mapping(c, v_r, path);
+    out3[0] = m.vrp;
+    out3[1] = m.q;
+    out3[2] = m.p;
+    return SWMD_OK;
+}
+
+int swmd_debug_read(swmd_corpus *c, int32_t what, int32_t v_r, void *h_dst) {
+    if (!c || !h_dst) return set_error(SWMD_EINVAL, "swmd_debug_read: NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard guard(c->device);
+    SWMD_CK(cudaStreamSynchronize(c->stream));
+    SWMD_CK(cudaDeviceSynchronize());
+    Slot &s = c->main;
+    if (what == 3) {
+        SWMD_CK(cudaMemcpy(h_dst, c->used, sizeof(int32_t) * c->Vu, cudaMemcpyDeviceToHost));
+        return SWMD_OK;
+    }
+    if (v_r < 1 || v_r > c->opt.max_vr) return set_error(SWMD_EINVAL, "swmd_debug_read: bad v_r");
+    const Mapping m = choose_mapping(c, v_r, c->opt.path);
+    const int vrp = m.vrp;
+    float *dst = static_cast<float *>(h_dst);
+    if (what == 0 || what == 1) {
+        const size_t kb = kprec_bytes(s.kprec);
+        std::vector<unsigned char> raw((size_t)c->Vu * vrp * kb);
+        SWMD_CK(cudaMemcpy(raw.data(), what == 0 ? s.KT : s.KMT, raw.size(), cudaMemcpyDeviceToHost));
+        for (size_t w = 0; w < (size_t)c->Vu; ++w)
+            for (int k = 0; k < v_r; ++k) {
+                const size_t i = w * vrp + k;
+                float x;
+                if (s.kprec == 0) std::memcpy(&x, raw.data() + 4 * i, 4);
+                else if (s.kprec == 1) x = __bfloat162float(*reinterpret_cast<__nv_bfloat16 *>(raw.data() + 2 * i));
+                else x = __half2float(*reinterpret_cast<__half *>(raw.data() + 2 * i));
+                dst[w * v_r + k] = x;
+            }
+        return SWMD_OK;
+    }
+    if (what == 2) {
+        std::vector<float> uu((size_t)c->Nl * vrp);
+        std::vector<int32_t> orig((size_t)c->Nl);
+        SWMD_CK(cudaMemcpy(uu.data(), s.u, sizeof(float) * uu.size(), cudaMemcpyDeviceToHost));
+        SWMD_CK(cudaMemcpy(orig.data(), c->doc_orig, sizeof(int32_t) * orig.size(), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < c->Nl; ++i)
+            for (int k = 0; k < v_r; ++k) dst[(size_t)orig[i] * v_r + k] = uu[(size_t)i * vrp + k];
+        return SWMD_OK;
+    }
+    return set_error(SWMD_EINVAL, "swmd_debug_read: unknown array %d", what);
+}
+
+}  // extern "C"

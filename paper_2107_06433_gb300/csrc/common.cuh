@@ -1,0 +1,154 @@
+// Internal declarations shared by the kernel files and the C-ABI layer of libswmd.
+//
+// Device data layout (document-major, the transpose of the paper's V x N CSR c):
+//   doc_ptr[Nl+1]  int32   offsets of each document's nonzeros; documents are kept
+//                          in decreasing-length order (internal order) so that the
+//                          documents sharing a warp have similar lengths.
+//   nz[nnz]        int2    (compact word id, bits of the FP32 normalised count);
+//                          words ascending inside a document.
+//   doc_orig[Nl]   int32   internal -> caller's column index (relative to doc_begin).
+//   used[Vu]       int32   compact word id -> vocabulary id (words that occur in c).
+//   E[V][d4]       float   embeddings, rows padded with zeros to d4 = roundup(d, 4).
+// Per query (workspace):
+//   KT[Vu][VRP], KMT[Vu][VRP]  K^T and (K.*M)^T, word-major (KT[vocab][v_r] of
+//                          Section III-B4), FP32 / BF16 / FP16, padded columns 0.
+//   u[Nl][VRP]             float, document-major (u[num_docs][v_r] of Section
+//                          III-B4), padded entries 0.
+//   VRP = v_r rounded up to the kernel's padding (a multiple of 4).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace swmd {
+
+// Bits of the device status word.
+constexpr int ST_BAD_ID = 1;       // a query id outside [0, V)
+constexpr int ST_NUMERIC = 2;      // NaN / Inf / zero denominator
+constexpr int ST_GUARD = 4;        // the FP64 guard of K^T u was taken (informational)
+constexpr int ST_BAD_R = 8;        // a query weight that is not finite and > 0
+
+// Query parameters read by the kernels from device memory, so that a captured
+// graph stays valid when lambda or v_r change.
+struct QParams {
+    float lambda;
+    int vr;
+    float u0;        // initial u = 1/x = v_r
+    int pad;
+    double *out;     // where the final kernel writes the distances (caller order)
+    int *status;     // status word of this query
+};
+
+struct IterArgs {
+    const int *doc_ptr;
+    const int2 *nz;
+    const void *KT;
+    const void *KMT;
+    float *u;
+    const float *r;        // [VRP], zero-padded
+    float *v;              // plain path: [nnz] SDDMM output
+    const int *doc_orig;
+    const QParams *qp;
+    long doc0;             // first document (internal order) of this launch
+    int N;                 // documents in this launch
+    int first;             // 1: u = v_r (x = 1/v_r), do not read u
+    double *out;           // if not NULL, the distances go here instead of qp->out
+};
+
+struct CostArgs {
+    const float *E;
+    int d4;
+    const int *used;
+    int Vu;
+    const int *q_ids;
+    const QParams *qp;
+    int V;
+    int shift;
+    void *KT;
+    void *KMT;
+};
+
+struct ResidentArgs {
+    IterArgs it;
+    int t;                 // Sinkhorn iterations
+};
+
+// One mapping of the per-document walk: a team of P*Q lanes owns a document, P
+// nonzeros are in flight at a time and Q lanes share one nonzero's dot product.
+struct Mapping {
+    int vrp;
+    int q;
+    int p;
+};
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_cost(const CostArgs &a, int vrp, int kprec, cudaStream_t s);
+// Writes the parameter block of a query and copies / validates its ids and
+// weights into the slot (zero padded to vrp_cap).  src_ids / src_r may be NULL
+// to leave that array as it is.
+cudaError_t launch_prep(QParams *qp, float lambda, int vr, int V, const int *src_ids,
+                        const float *src_r, int *q_ids, float *r, int vrp_cap, double *out,
+                        int *status, cudaStream_t s);
+cudaError_t launch_fused(const IterArgs &a, Mapping m, int kprec, int sms, cudaStream_t s);
+cudaError_t launch_sddmm(const IterArgs &a, Mapping m, int kprec, int sms, cudaStream_t s);
+cudaError_t launch_spmm(const IterArgs &a, Mapping m, int kprec, int sms, cudaStream_t s);
+cudaError_t launch_final(const IterArgs &a, Mapping m, int kprec, int sms, cudaStream_t s);
+cudaError_t launch_resident(const ResidentArgs &a, Mapping m, int kprec, int sms,
+                            cudaStream_t s);
+bool mapping_supported(Mapping m);
+int vrp_for(int vr, int q);
+
+// ---------------------------------------------------------------- K element access
+// Four consecutive K values (16 B in FP32, 8 B in BF16/FP16), widened to float.
+template <class T> struct KIO;
+
+template <> struct KIO<float> {
+    static __device__ __forceinline__ float4 load4(const float *base, long idx4) {
+        return __ldg(reinterpret_cast<const float4 *>(base) + idx4);
+    }
+    static __device__ __forceinline__ void store4(float *base, long idx4, float4 v) {
+        reinterpret_cast<float4 *>(base)[idx4] = v;
+    }
+};
+
+template <> struct KIO<__nv_bfloat16> {
+    static __device__ __forceinline__ float4 load4(const __nv_bfloat16 *base, long idx4) {
+        uint2 raw = __ldg(reinterpret_cast<const uint2 *>(base) + idx4);
+        __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162 *>(&raw.x);
+        __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162 *>(&raw.y);
+        float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+    static __device__ __forceinline__ void store4(__nv_bfloat16 *base, long idx4, float4 v) {
+        __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+        __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
+        uint2 raw;
+        raw.x = *reinterpret_cast<uint32_t *>(&a);
+        raw.y = *reinterpret_cast<uint32_t *>(&b);
+        reinterpret_cast<uint2 *>(base)[idx4] = raw;
+    }
+};
+
+template <> struct KIO<__half> {
+    static __device__ __forceinline__ float4 load4(const __half *base, long idx4) {
+        uint2 raw = __ldg(reinterpret_cast<const uint2 *>(base) + idx4);
+        __half2 a = *reinterpret_cast<__half2 *>(&raw.x);
+        __half2 b = *reinterpret_cast<__half2 *>(&raw.y);
+        float2 fa = __half22float2(a), fb = __half22float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+    static __device__ __forceinline__ void store4(__half *base, long idx4, float4 v) {
+        __half2 a = __floats2half2_rn(v.x, v.y);
+        __half2 b = __floats2half2_rn(v.z, v.w);
+        uint2 raw;
+        raw.x = *reinterpret_cast<uint32_t *>(&a);
+        raw.y = *reinterpret_cast<uint32_t *>(&b);
+        reinterpret_cast<uint2 *>(base)[idx4] = raw;
+    }
+};
+
+inline size_t kprec_bytes(int kprec) { return kprec == 0 ? 4 : 2; }
+
+}  // namespace swmd

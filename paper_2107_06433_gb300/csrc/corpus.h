@@ -1,0 +1,100 @@
+// Internal: the corpus object behind swmd_corpus* and the query engine shared by
+// the single-query, batch and serving entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+#include "swmd.h"
+
+namespace swmd {
+
+int set_error(int code, const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define SWMD_CK(call)                                        \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return ::swmd::cuda_fail(e_, #call); \
+    } while (0)
+
+// Device-side parameter block of one query slot.  Kernels read it through a
+// pointer, so a captured graph is reused for every query of the same shape.
+struct SlotParams {
+    QParams qp;
+};
+
+// Per-query device workspace: K^T, KM^T, u and the small query arrays.
+struct Slot {
+    int vrp_cap = 0;      // VRP the buffers were sized for
+    int kprec = -1;
+    void *KT = nullptr;
+    void *KMT = nullptr;
+    float *u = nullptr;
+    float *v = nullptr;   // plain path only: SDDMM output [nnz]
+    int *q_ids = nullptr; // [vrp_cap]
+    float *r = nullptr;   // [vrp_cap], zero padded
+    QParams *qp = nullptr;
+    double *out = nullptr;   // [Nl] distances (caller order)
+    int *status = nullptr;
+    int *q_in = nullptr;     // host-API staging of the query
+    float *r_in = nullptr;
+    int64_t bytes = 0;
+    bool external = false;   // buffers managed by a server (never reallocated here)
+};
+
+// Key of a captured launch sequence: everything baked into the launches.
+using GraphKey = std::tuple<int, int, int, int, int, int, int, const void *>;  // vrp,q,p,t,path,kprec,shift,slot
+
+struct Segment {
+    long d0, d1;   // documents [d0, d1) in internal order
+};
+
+}  // namespace swmd
+
+struct swmd_corpus {
+    int V = 0, N = 0, d = 0, d4 = 0, Vu = 0;
+    int64_t nnz = 0;
+    int doc_begin = 0, doc_end = 0;
+    int Nl = 0;          // documents held = doc_end - doc_begin
+    int device = 0;
+    int sms = 0;
+    swmd_options opt{};
+    cudaStream_t stream = nullptr;
+
+    float *E = nullptr;
+    int *used = nullptr;
+    int *doc_ptr = nullptr;
+    int2 *nz = nullptr;
+    int *doc_orig = nullptr;
+    std::vector<int> len_sorted;   // document lengths in internal order (host)
+    double mean_len = 0;
+
+    swmd::Slot main;               // workspace of the single-query path
+    int64_t base_bytes = 0;
+
+    std::map<swmd::GraphKey, cudaGraphExec_t> graphs;
+    std::map<std::tuple<int, int, int>, swmd::Mapping> tuned;  // (vr bucket, path, kprec)
+    std::mutex mu;                 // serialises use of `main` and the graph cache
+};
+
+namespace swmd {
+
+int alloc_slot(swmd_corpus *c, Slot &s, int max_vr, int kprec, bool with_v);
+void free_slot(Slot &s);
+Mapping choose_mapping(swmd_corpus *c, int vr, int path);
+// Enqueues a whole query whose ids / r are already in device memory (d_ids,
+// d_r), writing the distances to d_out and the status to d_status.
+int enqueue_query(swmd_corpus *c, Slot &s, const int *d_ids, const float *d_r, int vr,
+                  float lambda, int t, double *d_out, int *d_status, cudaStream_t st,
+                  bool allow_graph);
+int status_to_code(int st);
+
+}  // namespace swmd

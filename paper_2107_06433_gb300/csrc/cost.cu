@@ -1,0 +1,217 @@
+// a1: cost matrix and Sinkhorn kernel for one query.
+//
+// Algorithm 1 (first line) and Table I: M = cdist(vecs[sel], vecs) with the
+// Euclidean distance of Section II-A, K = exp(-lambda M); Section III-C adds K.*M
+// (the third dense input of SDDMM_SpMM type 2).  Only vocabulary words that
+// occur in the corpus get a row: no nonzero of c ever reads the others.
+//
+// Mapping: T adjacent threads own one word w and split the VRP query words,
+// KPT = VRP / T each.  The query rows are staged transposed in shared memory,
+// DC dimensions at a time, and read as float4 broadcasts; each thread streams
+// its word's embedding row with float4 loads.  Distances use the direct
+// difference form sum_d (q_d - e_d)^2 (no |q|^2 + |e|^2 - 2 q.e cancellation),
+// evaluated two query words per instruction with the packed f32x2 FMA of sm_100+.
+// Output rows K^T[w][0..VRP) and KM^T[w][0..VRP) are written with vector stores;
+// columns k >= v_r are zero.  With column_shift, K[k,w] = exp(-lambda (M[k,w] -
+// min_k M[k,w])): a rescaling of column w of K that leaves every x-update and the
+// distance unchanged and keeps the largest entry of each column at 1.
+#include "common.cuh"
+
+namespace swmd {
+namespace {
+
+constexpr int kCostThreads = 128;
+constexpr int kDC = 32;  // embedding dimensions per shared-memory stage
+
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+// d = (a - e)^2 + c on two lanes of a packed pair (round-to-nearest, no fusion
+// of the subtraction: the difference is rounded once, then one FMA).
+__device__ __forceinline__ unsigned long long sqdiff_acc2(unsigned long long a,
+                                                          unsigned long long e,
+                                                          unsigned long long c) {
+    unsigned long long t, d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(a), "l"(e));
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(d) : "l"(t), "l"(c));
+    return d;
+}
+
+template <int KPT, int T, class KT_t>
+__global__ void __launch_bounds__(kCostThreads) k_cost(CostArgs a) {
+    constexpr int VRP = KPT * T;
+    constexpr int ROW = KPT + 4;  // padded slice: T slices of a stage row in distinct banks
+    static_assert(KPT % 4 == 0, "KPT must be a multiple of 4");
+    __shared__ __align__(16) float sq[kDC][T][ROW];
+
+    const int vr = a.qp->vr;
+    const float lam = a.qp->lambda;
+    const int tid = threadIdx.x;
+    const int sub = tid % T;
+    const long wi = (long)blockIdx.x * (kCostThreads / T) + tid / T;
+    const bool active = wi < a.Vu;
+    const float *erow = a.E + (size_t)(active ? __ldg(a.used + wi) : 0) * a.d4;
+
+    unsigned long long acc[KPT / 2];
+#pragma unroll
+    for (int i = 0; i < KPT / 2; ++i) acc[i] = 0ull;
+
+    for (int d0 = 0; d0 < a.d4; d0 += kDC) {
+        const int dn = min(kDC, a.d4 - d0);
+        __syncthreads();
+        for (int i = tid; i < dn * VRP; i += kCostThreads) {
+            const int k = i / dn, dd = i - k * dn;
+            float val = 0.f;
+            if (k < vr) {
+                const int qid = __ldg(a.q_ids + k);
+                if (qid >= 0 && qid < a.V) val = __ldg(a.E + (size_t)qid * a.d4 + d0 + dd);
+            }
+            sq[dd][k / KPT][k % KPT] = val;
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll 2
+            for (int dd = 0; dd < dn; dd += 4) {
+                const float4 e = __ldg(reinterpret_cast<const float4 *>(erow + d0 + dd));
+                const float ev[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const unsigned long long e2 = pack2(ev[j], ev[j]);
+                    const float4 *qrow = reinterpret_cast<const float4 *>(&sq[dd + j][sub][0]);
+#pragma unroll
+                    for (int c = 0; c < KPT / 4; ++c) {
+                        const float4 qv = qrow[c];
+                        acc[2 * c] = sqdiff_acc2(pack2(qv.x, qv.y), e2, acc[2 * c]);
+                        acc[2 * c + 1] = sqdiff_acc2(pack2(qv.z, qv.w), e2, acc[2 * c + 1]);
+                    }
+                }
+            }
+        }
+    }
+
+    float m[KPT];
+#pragma unroll
+    for (int i = 0; i < KPT / 2; ++i) {
+        float x, y;
+        unpack2(acc[i], x, y);
+        m[2 * i] = sqrtf(x);
+        m[2 * i + 1] = sqrtf(y);
+    }
+    float mn = INFINITY;
+#pragma unroll
+    for (int kk = 0; kk < KPT; ++kk)
+        if (sub * KPT + kk < vr) mn = fminf(mn, m[kk]);
+#pragma unroll
+    for (int o = 1; o < T; o <<= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    if (!active) return;
+    const float sh = (a.shift && mn < INFINITY) ? mn : 0.f;
+
+    KT_t *KT = reinterpret_cast<KT_t *>(a.KT);
+    KT_t *KMT = reinterpret_cast<KT_t *>(a.KMT);
+    const long base4 = (wi * VRP + sub * KPT) / 4;
+#pragma unroll
+    for (int c = 0; c < KPT / 4; ++c) {
+        float kv[4], kmv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int k = sub * KPT + 4 * c + j;
+            const float mm = m[4 * c + j];
+            const float kk = (k < vr) ? expf(-lam * (mm - sh)) : 0.f;
+            kv[j] = kk;
+            kmv[j] = kk * mm;
+        }
+        KIO<KT_t>::store4(KT, base4 + c, make_float4(kv[0], kv[1], kv[2], kv[3]));
+        KIO<KT_t>::store4(KMT, base4 + c, make_float4(kmv[0], kmv[1], kmv[2], kmv[3]));
+    }
+}
+
+template <int KPT, int T, class KT_t>
+cudaError_t run(const CostArgs &a, cudaStream_t s) {
+    const int words_per_block = kCostThreads / T;
+    const long blocks = (a.Vu + words_per_block - 1) / words_per_block;
+    if (blocks > 0) k_cost<KPT, T, KT_t><<<(unsigned)blocks, kCostThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class KT_t>
+cudaError_t dispatch(const CostArgs &a, int vrp, cudaStream_t s) {
+    switch (vrp) {
+#define SWMD_COST_T1(V) \
+    case V: return run<V, 1, KT_t>(a, s);
+        SWMD_COST_T1(4) SWMD_COST_T1(8) SWMD_COST_T1(12) SWMD_COST_T1(16)
+        SWMD_COST_T1(20) SWMD_COST_T1(24) SWMD_COST_T1(28) SWMD_COST_T1(32)
+#undef SWMD_COST_T1
+        case 40: return run<20, 2, KT_t>(a, s);
+        case 48: return run<24, 2, KT_t>(a, s);
+        case 56: return run<28, 2, KT_t>(a, s);
+        case 64: return run<32, 2, KT_t>(a, s);
+        case 80: return run<20, 4, KT_t>(a, s);
+        case 96: return run<24, 4, KT_t>(a, s);
+        case 112: return run<28, 4, KT_t>(a, s);
+        case 128: return run<32, 4, KT_t>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// One block: parameter block, then the zero-padded query arrays.  Ids outside
+// [0, V) and weights that are not finite and positive raise status bits; the
+// cost kernel reads such ids as zero rows, so nothing is accessed out of range.
+__global__ void k_prep(QParams *qp, float lambda, int vr, int V, const int *src_ids,
+                       const float *src_r, int *q_ids, float *r, int vrp_cap, double *out,
+                       int *status) {
+    if (threadIdx.x == 0) {
+        QParams p;
+        p.lambda = lambda;
+        p.vr = vr;
+        p.u0 = (float)vr;
+        p.pad = 0;
+        p.out = out;
+        p.status = status;
+        *qp = p;
+        *status = 0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < vrp_cap; k += blockDim.x) {
+        if (src_ids) {
+            int id = 0;
+            if (k < vr) {
+                id = src_ids[k];
+                if (id < 0 || id >= V) atomicOr(status, ST_BAD_ID);
+            }
+            q_ids[k] = id;
+        }
+        if (src_r) {
+            float w = 0.f;
+            if (k < vr) {
+                w = src_r[k];
+                if (!(w > 0.f) || !(w < INFINITY)) atomicOr(status, ST_BAD_R);
+            }
+            r[k] = w;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_prep(QParams *qp, float lambda, int vr, int V, const int *src_ids,
+                        const float *src_r, int *q_ids, float *r, int vrp_cap, double *out,
+                        int *status, cudaStream_t s) {
+    k_prep<<<1, 256, 0, s>>>(qp, lambda, vr, V, src_ids, src_r, q_ids, r, vrp_cap, out, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cost(const CostArgs &a, int vrp, int kprec, cudaStream_t s) {
+    switch (kprec) {
+        case 0: return dispatch<float>(a, vrp, s);
+        case 1: return dispatch<__nv_bfloat16>(a, vrp, s);
+        case 2: return dispatch<__half>(a, vrp, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace swmd

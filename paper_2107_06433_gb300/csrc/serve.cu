@@ -1,0 +1,516 @@
+// Multi-query batches and the query server.
+//
+// Section III-D and Section V run many source documents against the same
+// targets; here that is (1) swmd_query_batch, a host call that runs a list of
+// queries over the resident corpus, and (2) a server that keeps the corpus on
+// the device and admits queries continuously: each admitted query gets a slot
+// (its own stream, parameter block and staging) and device memory for its K^T,
+// KM^T (and u on the per-iteration paths) carved from a fixed arena, so
+// admission is by the bytes a query of v_r words needs.  Queries admitted while
+// others run overlap on the device; finished slots are refilled at once.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "corpus.h"
+
+using namespace swmd;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over one device buffer (offsets aligned to 256 bytes).
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0;
+    std::vector<std::pair<size_t, size_t>> free_list;  // (offset, length), sorted by offset
+
+    void init(char *b, size_t n) {
+        base = b;
+        size = n;
+        free_list.assign(1, {0, n});
+    }
+    void *alloc(size_t n) {
+        n = (n + 255) & ~size_t(255);
+        for (size_t i = 0; i < free_list.size(); ++i) {
+            if (free_list[i].second >= n) {
+                const size_t off = free_list[i].first;
+                free_list[i].first += n;
+                free_list[i].second -= n;
+                if (free_list[i].second == 0) free_list.erase(free_list.begin() + (long)i);
+                return base + off;
+            }
+        }
+        return nullptr;
+    }
+    void release(void *p, size_t n) {
+        n = (n + 255) & ~size_t(255);
+        const size_t off = (size_t)((char *)p - base);
+        auto it = std::lower_bound(free_list.begin(), free_list.end(), std::make_pair(off, size_t(0)));
+        it = free_list.insert(it, {off, n});
+        // merge with neighbours
+        size_t i = (size_t)(it - free_list.begin());
+        if (i + 1 < free_list.size() && free_list[i].first + free_list[i].second == free_list[i + 1].first) {
+            free_list[i].second += free_list[i + 1].second;
+            free_list.erase(free_list.begin() + (long)i + 1);
+        }
+        if (i > 0 && free_list[i - 1].first + free_list[i - 1].second == free_list[i].first) {
+            free_list[i - 1].second += free_list[i].second;
+            free_list.erase(free_list.begin() + (long)i);
+        }
+    }
+};
+
+struct Request {
+    uint64_t ticket = 0;
+    std::vector<int32_t> ids;
+    std::vector<float> r;
+    int vr = 0;
+    float lambda = 1.f;
+    int t = 0;
+    double t_submit = 0, t_done = 0;
+    int state = 0;  // 0 queued, 1 running, 2 finished
+    int code = SWMD_OK;
+    std::string err;
+    std::vector<double> result;
+};
+
+struct ServerSlot {
+    Slot ws;                  // small arrays owned here; K^T / KM^T / u from the arena
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    int32_t *h_q = nullptr;   // pinned staging
+    float *h_r = nullptr;
+    double *h_out = nullptr;
+    int *h_status = nullptr;
+    std::shared_ptr<Request> req;
+    size_t arena_bytes = 0;
+    void *arena_ptr = nullptr;
+};
+
+size_t query_bytes(swmd_corpus *c, int vrp, int path) {
+    size_t b = 2 * (size_t)c->Vu * vrp * kprec_bytes(c->opt.k_precision);
+    if (path != SWMD_PATH_RESIDENT) b += (size_t)c->Nl * vrp * sizeof(float);
+    if (path == SWMD_PATH_PLAIN) b += (size_t)c->nnz * sizeof(float);
+    return b + 3 * 256;
+}
+
+}  // namespace
+
+struct swmd_server {
+    swmd_corpus *c = nullptr;
+    swmd_serve_config cfg{};
+    std::vector<ServerSlot> slots;
+    Arena arena;
+    char *arena_mem = nullptr;
+    std::mutex m;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Request>> pending;
+    std::unordered_map<uint64_t, std::shared_ptr<Request>> table;
+    bool stopping = false;
+    std::thread worker;
+    uint64_t next_ticket = 1;
+    // statistics
+    std::vector<double> lat_ms;
+    int64_t completed = 0, rejected = 0, batches = 0, admitted = 0;
+    double t_first = -1, t_last = -1;
+};
+
+namespace {
+
+void finish(swmd_server *S, ServerSlot &sl, int code, const std::string &err) {
+    auto &R = *sl.req;
+    R.code = code;
+    R.err = err;
+    R.state = 2;
+    R.t_done = now_s();
+    if (code == SWMD_OK || code == SWMD_ENUMERIC) {
+        R.result.assign(sl.h_out, sl.h_out + S->c->Nl);
+    }
+    S->completed++;
+    S->lat_ms.push_back((R.t_done - R.t_submit) * 1e3);
+    S->t_last = R.t_done;
+    if (sl.arena_ptr) S->arena.release(sl.arena_ptr, sl.arena_bytes);
+    sl.arena_ptr = nullptr;
+    sl.req.reset();
+}
+
+// Launches one admitted request on its slot.  Returns an SWMD code.
+int launch_on_slot(swmd_server *S, ServerSlot &sl) {
+    swmd_corpus *c = S->c;
+    auto &R = *sl.req;
+    const int path = c->opt.path;
+    const Mapping m = choose_mapping(c, R.vr, path);
+    const size_t kbytes = (size_t)c->Vu * m.vrp * kprec_bytes(c->opt.k_precision);
+    char *p = static_cast<char *>(sl.arena_ptr);
+    auto carve = [&](size_t n) {
+        char *q = p;
+        p += (n + 255) & ~size_t(255);
+        return (void *)q;
+    };
+    sl.ws.KT = carve(kbytes);
+    sl.ws.KMT = carve(kbytes);
+    sl.ws.u = path != SWMD_PATH_RESIDENT ? (float *)carve((size_t)c->Nl * m.vrp * sizeof(float)) : nullptr;
+    sl.ws.v = path == SWMD_PATH_PLAIN ? (float *)carve((size_t)c->nnz * sizeof(float)) : nullptr;
+    std::memcpy(sl.h_q, R.ids.data(), sizeof(int32_t) * R.vr);
+    std::memcpy(sl.h_r, R.r.data(), sizeof(float) * R.vr);
+    SWMD_CK(cudaMemcpyAsync(sl.ws.q_in, sl.h_q, sizeof(int32_t) * R.vr, cudaMemcpyHostToDevice, sl.stream));
+    SWMD_CK(cudaMemcpyAsync(sl.ws.r_in, sl.h_r, sizeof(float) * R.vr, cudaMemcpyHostToDevice, sl.stream));
+    int rc;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        rc = enqueue_query(c, sl.ws, sl.ws.q_in, sl.ws.r_in, R.vr, R.lambda, R.t, sl.ws.out,
+                           sl.ws.status, sl.stream, false);
+    }
+    if (rc) return rc;
+    SWMD_CK(cudaMemcpyAsync(sl.h_out, sl.ws.out, sizeof(double) * c->Nl, cudaMemcpyDeviceToHost, sl.stream));
+    SWMD_CK(cudaMemcpyAsync(sl.h_status, sl.ws.status, sizeof(int), cudaMemcpyDeviceToHost, sl.stream));
+    SWMD_CK(cudaEventRecord(sl.done, sl.stream));
+    return SWMD_OK;
+}
+
+void worker_main(swmd_server *S) {
+    DeviceGuard guard(S->c->device);
+    std::unique_lock<std::mutex> lk(S->m);
+    for (;;) {
+        bool running = false;
+        for (auto &sl : S->slots) running |= (bool)sl.req;
+        if (S->stopping && !running) break;
+        if (!running && S->pending.empty()) {
+            S->cv_work.wait(lk);
+            continue;
+        }
+        // admit: fill free slots while the arena has room for the next request
+        std::vector<ServerSlot *> launched;
+        if (!S->stopping) {
+            for (auto &sl : S->slots) {
+                if (sl.req || S->pending.empty()) continue;
+                auto R = S->pending.front();
+                const Mapping mp = choose_mapping(S->c, R->vr, S->c->opt.path);
+                const size_t need = query_bytes(S->c, mp.vrp, S->c->opt.path);
+                void *mem = S->arena.alloc(need);
+                if (!mem) break;   // admission waits for memory to free up
+                S->pending.pop_front();
+                sl.req = R;
+                sl.arena_ptr = mem;
+                sl.arena_bytes = need;
+                R->state = 1;
+                launched.push_back(&sl);
+            }
+        }
+        if (!launched.empty()) {
+            S->batches++;
+            S->admitted += (int64_t)launched.size();
+        }
+        lk.unlock();
+        std::vector<std::pair<ServerSlot *, int>> failed;
+        for (auto *sl : launched) {
+            const int rc = launch_on_slot(S, *sl);
+            if (rc) failed.push_back({sl, rc});
+        }
+        // poll in-flight slots
+        std::vector<ServerSlot *> ready;
+        for (auto &sl : S->slots) {
+            if (!sl.req) continue;
+            bool is_failed = false;
+            for (auto &f : failed) is_failed |= f.first == &sl;
+            if (is_failed) continue;
+            if (sl.req->state == 1 && cudaEventQuery(sl.done) == cudaSuccess) ready.push_back(&sl);
+        }
+        const std::string last = swmd_last_error();
+        lk.lock();
+        for (auto &f : failed) {
+            cudaStreamSynchronize(f.first->stream);   // nothing of it may still use its memory
+            finish(S, *f.first, f.second, last);
+        }
+        for (auto *sl : ready) {
+            const int code = status_to_code(*sl->h_status);
+            finish(S, *sl, code, code ? std::string(swmd_last_error()) : std::string());
+        }
+        if (!failed.empty() || !ready.empty()) S->cv_done.notify_all();
+        bool busy = false;
+        for (auto &sl : S->slots) busy |= (bool)sl.req;
+        if (busy && ready.empty() && launched.empty()) {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(
+                std::max(5, std::min(S->cfg.max_wait_us, 200))));
+            lk.lock();
+        }
+    }
+    // fail whatever is still queued
+    for (auto &R : S->pending) {
+        R->state = 2;
+        R->code = SWMD_ESTOPPED;
+        R->err = "server stopped";
+    }
+    S->pending.clear();
+    S->cv_done.notify_all();
+}
+
+}  // namespace
+
+extern "C" {
+
+int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
+                     const int32_t *h_word_ids, const float *h_weights, const float *h_lambdas,
+                     int32_t max_iter, double *h_out) {
+    if (!c || n_queries < 0 || (n_queries > 0 && (!q_ptr || !h_lambdas || !h_out)))
+        return set_error(SWMD_EINVAL, "swmd_query_batch: bad arguments");
+    if (max_iter < 0) return set_error(SWMD_EINVAL, "swmd_query_batch: max_iter must be >= 0");
+    if (n_queries == 0 || c->Nl == 0) return SWMD_OK;
+    if (q_ptr[0] != 0) return set_error(SWMD_EINVAL, "swmd_query_batch: q_ptr[0] must be 0");
+    std::vector<int32_t> ids;
+    std::vector<float> rs;
+    std::vector<int64_t> off((size_t)n_queries + 1, 0);
+    std::vector<int32_t> vrs((size_t)n_queries);
+    for (int32_t i = 0; i < n_queries; ++i) {
+        const int64_t n = q_ptr[i + 1] - q_ptr[i];
+        if (n < 0 || n > INT32_MAX) return set_error(SWMD_EINVAL, "swmd_query_batch: bad q_ptr");
+        std::vector<int32_t> qi((size_t)std::max<int64_t>(n, 1));
+        std::vector<float> qr((size_t)std::max<int64_t>(n, 1));
+        int32_t vr = 0;
+        int rc = swmd_select(c->V, (int32_t)n, h_word_ids + q_ptr[i], h_weights + q_ptr[i], qi.data(),
+                             qr.data(), &vr);
+        if (rc) return set_error(rc, "swmd_query_batch: query %d: %s", i, swmd_last_error());
+        if (vr > c->opt.max_vr)
+            return set_error(SWMD_EINVAL, "swmd_query_batch: query %d has %d words (max %d)", i, vr,
+                             c->opt.max_vr);
+        const float lam = h_lambdas[i];
+        if (!(lam > 0.f) || std::isinf(lam))
+            return set_error(SWMD_EINVAL, "swmd_query_batch: lambda of query %d", i);
+        ids.insert(ids.end(), qi.begin(), qi.begin() + vr);
+        rs.insert(rs.end(), qr.begin(), qr.begin() + vr);
+        vrs[i] = vr;
+        off[i + 1] = off[i] + vr;
+    }
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard guard(c->device);
+    cudaStream_t st = c->stream;
+    int32_t *d_ids = nullptr;
+    float *d_r = nullptr;
+    double *d_out = nullptr;
+    int *d_status = nullptr;
+    int rc = SWMD_OK;
+    std::vector<int> h_status((size_t)n_queries, 0);
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(st);
+        cudaFree(d_ids); cudaFree(d_r); cudaFree(d_out); cudaFree(d_status);
+    };
+    cudaError_t e = cudaMalloc(&d_ids, sizeof(int32_t) * std::max<size_t>(ids.size(), 1));
+    if (e == cudaSuccess) e = cudaMalloc(&d_r, sizeof(float) * std::max<size_t>(rs.size(), 1));
+    if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(double) * (size_t)n_queries * c->Nl);
+    if (e == cudaSuccess) e = cudaMalloc(&d_status, sizeof(int) * (size_t)n_queries);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ids, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_r, rs.data(), sizeof(float) * rs.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "swmd_query_batch staging");
+    }
+    for (int32_t i = 0; i < n_queries && rc == SWMD_OK; ++i)
+        rc = enqueue_query(c, c->main, d_ids + off[i], d_r + off[i], vrs[i], h_lambdas[i], max_iter,
+                           d_out + (size_t)i * c->Nl, d_status + i, st, true);
+    if (rc == SWMD_OK) {
+        e = cudaMemcpyAsync(h_out, d_out, sizeof(double) * (size_t)n_queries * c->Nl, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_status.data(), d_status, sizeof(int) * (size_t)n_queries, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "swmd_query_batch");
+    }
+    cleanup();
+    if (rc) return rc;
+    int all = 0;
+    for (int s : h_status) all |= s;
+    return status_to_code(all);
+}
+
+void swmd_default_serve_config(swmd_serve_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->max_batch = 32;
+    cfg->memory_budget = (int64_t)4 << 30;
+    cfg->max_wait_us = 200;
+    cfg->queue_capacity = 4096;
+}
+
+int swmd_serve_start(swmd_corpus *c, const swmd_serve_config *cfg_in, swmd_server **out) {
+    if (!c || !out) return set_error(SWMD_EINVAL, "swmd_serve_start: NULL argument");
+    *out = nullptr;
+    swmd_serve_config cfg;
+    if (cfg_in) cfg = *cfg_in;
+    else swmd_default_serve_config(&cfg);
+    if (cfg.max_batch < 1 || cfg.max_batch > 1024 || cfg.memory_budget <= 0 || cfg.queue_capacity < 1)
+        return set_error(SWMD_EINVAL, "swmd_serve_start: bad configuration");
+    const Mapping mx = choose_mapping(c, c->opt.max_vr, c->opt.path);
+    const size_t largest = query_bytes(c, std::max(mx.vrp, vrp_for(c->opt.max_vr, 8)), c->opt.path);
+    if ((size_t)cfg.memory_budget < largest)
+        return set_error(SWMD_ENOMEM, "swmd_serve_start: memory_budget %lld below one query of %d words (%zu bytes)",
+                         (long long)cfg.memory_budget, c->opt.max_vr, largest);
+    DeviceGuard guard(c->device);
+    auto *S = new swmd_server();
+    S->c = c;
+    S->cfg = cfg;
+    auto bail = [&](int code) {
+        for (auto &sl : S->slots) {
+            sl.ws.KT = sl.ws.KMT = nullptr;
+            sl.ws.u = sl.ws.v = nullptr;
+            free_slot(sl.ws);
+            if (sl.stream) cudaStreamDestroy(sl.stream);
+            if (sl.done) cudaEventDestroy(sl.done);
+            cudaFreeHost(sl.h_q); cudaFreeHost(sl.h_r); cudaFreeHost(sl.h_out); cudaFreeHost(sl.h_status);
+        }
+        cudaFree(S->arena_mem);
+        delete S;
+        return code;
+    };
+    cudaError_t e = cudaMalloc(&S->arena_mem, (size_t)cfg.memory_budget);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "swmd_serve_start: arena"));
+    S->arena.init(S->arena_mem, (size_t)cfg.memory_budget);
+    S->slots.resize((size_t)cfg.max_batch);
+    const int vrp = vrp_for(c->opt.max_vr, 8);
+    for (auto &sl : S->slots) {
+        Slot &w = sl.ws;
+        int64_t b = 0;
+        e = cudaMalloc(&w.q_ids, sizeof(int) * vrp);
+        if (e == cudaSuccess) e = cudaMalloc(&w.r, sizeof(float) * vrp);
+        if (e == cudaSuccess) e = cudaMalloc(&w.qp, sizeof(QParams));
+        if (e == cudaSuccess) e = cudaMalloc(&w.out, sizeof(double) * std::max(c->Nl, 1));
+        if (e == cudaSuccess) e = cudaMalloc(&w.status, sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&w.q_in, sizeof(int) * vrp);
+        if (e == cudaSuccess) e = cudaMalloc(&w.r_in, sizeof(float) * vrp);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMallocHost(&sl.h_q, sizeof(int32_t) * vrp);
+        if (e == cudaSuccess) e = cudaMallocHost(&sl.h_r, sizeof(float) * vrp);
+        if (e == cudaSuccess) e = cudaMallocHost(&sl.h_out, sizeof(double) * std::max(c->Nl, 1));
+        if (e == cudaSuccess) e = cudaMallocHost(&sl.h_status, sizeof(int));
+        if (e != cudaSuccess) return bail(cuda_fail(e, "swmd_serve_start: slot"));
+        (void)b;
+        w.vrp_cap = vrp;
+        w.kprec = c->opt.k_precision;
+        w.external = true;
+    }
+    S->worker = std::thread(worker_main, S);
+    *out = S;
+    return SWMD_OK;
+}
+
+int swmd_serve_submit(swmd_server *S, const int32_t *h_ids, const float *h_weights, int32_t n_words,
+                      float lambda, int32_t max_iter, uint64_t *ticket) {
+    if (!S || !ticket) return set_error(SWMD_EINVAL, "swmd_serve_submit: NULL argument");
+    auto R = std::make_shared<Request>();
+    R->ids.resize((size_t)std::max(n_words, 1));
+    R->r.resize((size_t)std::max(n_words, 1));
+    int rc = swmd_select(S->c->V, n_words, h_ids, h_weights, R->ids.data(), R->r.data(), &R->vr);
+    if (rc) return rc;
+    if (R->vr > S->c->opt.max_vr)
+        return set_error(SWMD_EINVAL, "swmd_serve_submit: %d words (max %d)", R->vr, S->c->opt.max_vr);
+    if (!(lambda > 0.f) || std::isinf(lambda) || max_iter < 0)
+        return set_error(SWMD_EINVAL, "swmd_serve_submit: lambda must be finite > 0, max_iter >= 0");
+    R->lambda = lambda;
+    R->t = max_iter;
+    std::lock_guard<std::mutex> lk(S->m);
+    if (S->stopping) return set_error(SWMD_ESTOPPED, "swmd_serve_submit: server stopped");
+    if ((int)S->pending.size() >= S->cfg.queue_capacity) {
+        S->rejected++;
+        return set_error(SWMD_ENOMEM, "swmd_serve_submit: queue full (%d)", S->cfg.queue_capacity);
+    }
+    R->ticket = S->next_ticket++;
+    R->t_submit = now_s();
+    if (S->t_first < 0) S->t_first = R->t_submit;
+    S->table[R->ticket] = R;
+    S->pending.push_back(R);
+    *ticket = R->ticket;
+    S->cv_work.notify_one();
+    return SWMD_OK;
+}
+
+int swmd_serve_wait(swmd_server *S, uint64_t ticket, double *h_out_dist, int32_t timeout_ms) {
+    if (!S) return set_error(SWMD_EINVAL, "swmd_serve_wait: NULL server");
+    std::unique_lock<std::mutex> lk(S->m);
+    auto it = S->table.find(ticket);
+    if (it == S->table.end()) return set_error(SWMD_EINVAL, "swmd_serve_wait: unknown ticket %llu", (unsigned long long)ticket);
+    auto R = it->second;
+    auto ready = [&] { return R->state == 2; };
+    if (timeout_ms < 0) S->cv_done.wait(lk, ready);
+    else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+        return set_error(SWMD_ETIMEDOUT, "swmd_serve_wait: ticket %llu not ready after %d ms",
+                         (unsigned long long)ticket, timeout_ms);
+    S->table.erase(it);
+    if (!R->result.empty() && h_out_dist)
+        std::memcpy(h_out_dist, R->result.data(), sizeof(double) * R->result.size());
+    if (R->code) return set_error(R->code, "%s", R->err.c_str());
+    return SWMD_OK;
+}
+
+int swmd_serve_stats(swmd_server *S, swmd_serve_stats_t *out) {
+    if (!S || !out) return set_error(SWMD_EINVAL, "swmd_serve_stats: NULL argument");
+    std::lock_guard<std::mutex> lk(S->m);
+    std::memset(out, 0, sizeof *out);
+    out->completed = S->completed;
+    out->rejected = S->rejected;
+    out->batches = S->batches;
+    out->mean_batch = S->batches ? (double)S->admitted / S->batches : 0.0;
+    if (S->completed > 0 && S->t_last > S->t_first) out->qps = S->completed / (S->t_last - S->t_first);
+    if (!S->lat_ms.empty()) {
+        std::vector<double> l = S->lat_ms;
+        std::sort(l.begin(), l.end());
+        auto pct = [&](double p) {
+            const double x = p * (double)(l.size() - 1);
+            const size_t i = (size_t)x;
+            const double f = x - (double)i;
+            return i + 1 < l.size() ? l[i] * (1 - f) + l[i + 1] * f : l[i];
+        };
+        out->p50_ms = pct(0.50);
+        out->p99_ms = pct(0.99);
+    }
+    return SWMD_OK;
+}
+
+int swmd_serve_stop(swmd_server *S) {
+    if (!S) return SWMD_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->m);
+        S->stopping = true;
+        S->cv_work.notify_all();
+    }
+    if (S->worker.joinable()) S->worker.join();
+    DeviceGuard guard(S->c->device);
+    for (auto &sl : S->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        sl.ws.KT = sl.ws.KMT = nullptr;
+        sl.ws.u = sl.ws.v = nullptr;
+        free_slot(sl.ws);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.done) cudaEventDestroy(sl.done);
+        cudaFreeHost(sl.h_q); cudaFreeHost(sl.h_r); cudaFreeHost(sl.h_out); cudaFreeHost(sl.h_status);
+    }
+    cudaFree(S->arena_mem);
+    delete S;
+    return SWMD_OK;
+}
+
+}  // extern "C"

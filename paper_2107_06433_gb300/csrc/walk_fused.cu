@@ -1,0 +1,10 @@
+// a3: the fused SDDMM-SpMM iteration (Section III-C, SDDMM_SpMM type 1).
+#include "walk.cuh"
+
+namespace swmd {
+
+cudaError_t launch_fused(const IterArgs &a, Mapping m, int kprec, int sms, cudaStream_t s) {
+    return dispatch_walk_prec<Kind::Fused>(a, m, kprec, sms, s);
+}
+
+}  // namespace swmd

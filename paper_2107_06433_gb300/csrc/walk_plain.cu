@@ -1,0 +1,15 @@
+// The unfused iteration: SDDMM (Algorithm 2) writing v, then SpMM (Algorithm 3)
+// reading it back -- the separate-kernel formulation Section III-C improves on.
+#include "walk.cuh"
+
+namespace swmd {
+
+cudaError_t launch_sddmm(const IterArgs &a, Mapping m, int kprec, int sms, cudaStream_t s) {
+    return dispatch_walk_prec<Kind::Sddmm>(a, m, kprec, sms, s);
+}
+
+cudaError_t launch_spmm(const IterArgs &a, Mapping m, int kprec, int sms, cudaStream_t s) {
+    return dispatch_walk_prec<Kind::Spmm>(a, m, kprec, sms, s);
+}
+
+}  // namespace swmd
