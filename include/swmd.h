@@ -165,6 +165,30 @@ SWMD_API int swmd_query_device(swmd_corpus *corpus, const int32_t *d_ids, const 
                       float lambda, int32_t max_iter, double *d_out, int32_t *d_status,
                       void *stream);
 
+/* The query of swmd_query_device for callers that cannot allocate device
+ * memory when they query -- for example a server whose memory pool already owns
+ * the device's free memory, or a latency-critical request path that must avoid
+ * the implicit synchronisation of cudaMalloc / cudaFree.  (The paper has no
+ * counterpart: it is an interface for such callers, not a step of the method.)
+ *   Arguments, layout, ownership and result as in swmd_query_device; the path is
+ *   always SWMD_PATH_RESIDENT.  The corpus is created beforehand as usual.
+ *   This call allocates nothing: the query's scratch (its parameter block, ids,
+ *   weights, K^T and KM^T) lives in one fixed device array of 16 MiB inside the
+ *   library, which every GPU that loads the library holds until the process
+ *   exits.  A query needing more (2 x V_used x VRP x bytes per K element, plus
+ *   under 2 KiB) is refused with SWMD_EINVAL and a message naming the sizes.
+ *   The first call on a device looks up the array's device address on that
+ *   device (cudaGetSymbolAddress); make that first call before any stream
+ *   capture.
+ *   All calls share the one array and it keeps the last call's contents; each
+ *   call rewrites everything it reads (the status word is cleared by the call).
+ *   Calls whose work overlaps on the GPU -- on different streams, or from
+ *   different threads or corpora on the same device -- race on the array: order
+ *   them on one stream or wait between them. */
+SWMD_API int swmd_query_noalloc(swmd_corpus *corpus, const int32_t *d_ids, const float *d_r,
+                                int32_t v_r, float lambda, int32_t max_iter, double *d_out,
+                                int32_t *d_status, void *stream);
+
 /* ------------------------------------------------------------------ the steps */
 /* The steps of swmd_query_device, one call each, for timing and testing; they
  * share the corpus's workspace and must be called in this order for one query.

@@ -82,6 +82,8 @@ _SIGS = {
     "swmd_step_final": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P, P]),
     "swmd_step_resident": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P, P]),
     "swmd_get_mapping": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P]),
+    "swmd_query_noalloc": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.c_float, ctypes.c_int32,
+                                          P, P, P]),
     "swmd_debug_read": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P]),
     "swmd_query_batch": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P, ctypes.c_int32, P]),
     "swmd_default_serve_config": (None, [P]),
@@ -237,6 +239,15 @@ def swmd_query_device(corpus: Corpus, d_ids, d_r, v_r: int, lam: float, max_iter
     _err(lib().swmd_query_device(corpus.handle, _dptr(d_ids), _dptr(d_r), int(v_r), float(lam),
                                  int(max_iter), _dptr(d_out), _dptr(d_status), _stream(stream)),
          "swmd_query_device")
+
+
+def swmd_query_noalloc(corpus: Corpus, d_ids, d_r, v_r: int, lam: float, max_iter: int, d_out,
+                       d_status=None, stream=None):
+    """swmd_query_device without any allocation in the call: the scratch lives in a
+    fixed 16 MiB device array inside the library (see include/swmd.h)."""
+    _err(lib().swmd_query_noalloc(corpus.handle, _dptr(d_ids), _dptr(d_r), int(v_r), float(lam),
+                                  int(max_iter), _dptr(d_out), _dptr(d_status), _stream(stream)),
+         "swmd_query_noalloc")
 
 
 def swmd_step_cost(corpus: Corpus, d_ids, d_r, v_r, lam, d_status=None, stream=None):
