@@ -80,9 +80,21 @@ typedef struct swmd_options {
     int32_t doc_begin;     /* documents [doc_begin, doc_end) of the CSR columns are loaded;
                               -1/-1 = all.  One replica per GPU loads its own range. */
     int32_t doc_end;
-    int32_t team_lanes;    /* 0 = autotuned; else lanes per document (1..32, power of 2) */
-    int32_t lanes_per_nz;  /* 0 = autotuned; else lanes sharing one nonzero's dot (power of 2) */
-    int32_t reserved[6];
+    int32_t team_lanes;    /* per-iteration paths: 0 = autotuned, else lanes per document
+                              (1..32, power of 2) */
+    int32_t lanes_per_nz;  /* per-iteration paths: 0 = autotuned, else lanes sharing one
+                              nonzero's dot (power of 2) */
+    int32_t tile_threads;  /* resident path: threads per block (64, 128 or 256; 0 = 128) */
+    int32_t nnz_per_lane;  /* resident path: target nonzeros per lane and pass; a document of
+                              n nonzeros gets about n / nnz_per_lane lanes (0 = 4) */
+    int32_t tile_nnz;      /* resident path: nonzeros staged per block (0 = as many as fit
+                              in about 100 KB of shared memory) */
+    int32_t cost_split;    /* cost kernel: threads sharing one word's embedding row
+                              (1, 2 or 4; 0 = 2) */
+    int32_t solver;        /* resident path kernel: 0 = automatic, 1 = K^T rows in registers
+                              (v_r <= 32), 2 = rows staged in shared memory, 3 = rows
+                              re-gathered from L2 each iteration */
+    int32_t reserved[1];
 } swmd_options;
 
 /* Fills *opt with the defaults listed above. */

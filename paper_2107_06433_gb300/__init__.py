@@ -38,7 +38,9 @@ class swmd_options(ctypes.Structure):
                 ("max_vr", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("doc_begin", ctypes.c_int32), ("doc_end", ctypes.c_int32),
                 ("team_lanes", ctypes.c_int32), ("lanes_per_nz", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("tile_threads", ctypes.c_int32), ("nnz_per_lane", ctypes.c_int32),
+                ("tile_nnz", ctypes.c_int32), ("cost_split", ctypes.c_int32),
+                ("solver", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class swmd_corpus_info(ctypes.Structure):

@@ -133,6 +133,111 @@ Mapping choose_mapping(swmd_corpus *c, int vr, int path) {
     return m;
 }
 
+int build_tiles(swmd_corpus *c) {
+    const int threads = c->opt.tile_threads > 0 ? c->opt.tile_threads : 128;
+    const int npl = c->opt.nnz_per_lane > 0 ? c->opt.nnz_per_lane : 4;
+    if (threads != 64 && threads != 128 && threads != 256)
+        return set_error(SWMD_EINVAL, "tile_threads must be 64, 128 or 256");
+    if (c->tiles_dev && threads == c->tile_threads && npl == c->tile_npl) return SWMD_OK;
+    // tiles: consecutive documents (decreasing length) of one team size, at most
+    // threads / team size of them and at most `budget` nonzeros
+    std::vector<int> all;
+    std::vector<int> off, count;
+    for (int bi = 0; bi < kNumTileBudgets; ++bi) {
+        const int budget = kTileBudgets[bi];
+        off.push_back((int)all.size());
+        int n = 0, d = 0;
+        all.push_back(0);
+        while (d < c->Nl) {
+            int sum = 0, k = 0;
+            const int g = team_lanes_for(c->len_sorted[d], npl);
+            while (d + k < c->Nl && k < threads / g && team_lanes_for(c->len_sorted[d + k], npl) == g &&
+                   (k == 0 || sum + c->len_sorted[d + k] <= budget)) {
+                sum += c->len_sorted[d + k];
+                ++k;
+            }
+            d += k;
+            all.push_back(d);
+            ++n;
+        }
+        count.push_back(n);
+    }
+    int *dev = nullptr;
+    int64_t bytes = 0;
+    int rc = dev_alloc(&dev, all.size(), &bytes);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpy(dev, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dev);
+        return cuda_fail(e, "copy tiles");
+    }
+    if (c->tiles_dev) {
+        cudaDeviceSynchronize();   // no launch may still read the old sets
+        cudaFree(c->tiles_dev);
+    }
+    c->tiles_dev = dev;
+    c->tile_off = off;
+    c->tile_count = count;
+    c->tile_threads = threads;
+    c->tile_npl = npl;
+    return SWMD_OK;
+}
+
+int build_tasks(swmd_corpus *c) {
+    std::vector<int4> all;
+    for (int npl = 1; npl <= 8; ++npl) {
+        c->task_off[npl] = (int)all.size();
+        int d = 0, n = 0;
+        while (d < c->Nl) {
+            const int g = reg_team_lanes(c->len_sorted[d], npl);
+            int k = 0;
+            while (d + k < c->Nl && k < 32 / g && reg_team_lanes(c->len_sorted[d + k], npl) == g) ++k;
+            all.push_back(make_int4(d, g, k, 0));
+            d += k;
+            ++n;
+        }
+        c->task_count[npl] = n;
+    }
+    int64_t bytes = 0;
+    int rc = dev_alloc(&c->tasks_dev, std::max<size_t>(all.size(), 1), &bytes);
+    if (rc) return rc;
+    c->base_bytes += bytes;
+    if (!all.empty()) {
+        cudaError_t e = cudaMemcpy(c->tasks_dev, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "copy tasks");
+    }
+    return SWMD_OK;
+}
+
+int run_resident(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kprec, cudaStream_t st) {
+    const int solver = c->opt.solver;
+    const int npl = regs_rows_per_lane(m.vrp);
+    if (c->tasks_dev && npl > 0 && (solver == 0 || solver == 1)) {
+        TaskSet ts{c->tasks_dev + c->task_off[npl], c->task_count[npl], npl,
+                   c->Nl > 0 ? c->len_sorted[0] : 0};
+        SWMD_CK(launch_resident_regs(ra, m.vrp, kprec, ts, c->sms, st));
+        return SWMD_OK;
+    }
+    if (c->tiles_dev && tiled_supported(m.vrp, kprec) && solver != 3) {
+        // the largest nonzero budget that fits the requested size, or ~110 KB of
+        // shared memory (two blocks per SM) when none is requested
+        const int kb = (int)kprec_bytes(kprec);
+        int pick = 0;
+        for (int i = 0; i < kNumTileBudgets; ++i) {
+            const bool fits = c->opt.tile_nnz > 0
+                                  ? kTileBudgets[i] <= c->opt.tile_nnz
+                                  : tiled_smem_bytes(m.vrp, kb, kTileBudgets[i]) <= 110 * 1024;
+            if (fits && tiled_smem_bytes(m.vrp, kb, kTileBudgets[i]) <= 220 * 1024) pick = i;
+        }
+        TileSet ts{c->tiles_dev + c->tile_off[pick], c->tile_count[pick], kTileBudgets[pick],
+                   c->tile_threads, c->tile_npl};
+        SWMD_CK(launch_resident_tiled(ra, m.vrp, kprec, ts, c->sms, st));
+        return SWMD_OK;
+    }
+    SWMD_CK(launch_resident(ra, m, kprec, c->sms, st));
+    return SWMD_OK;
+}
+
 static int launch_sequence(swmd_corpus *c, Slot &s, Mapping m, int t, int path, int kprec,
                            int shift, cudaStream_t st) {
     CostArgs ca{};
@@ -144,6 +249,7 @@ static int launch_sequence(swmd_corpus *c, Slot &s, Mapping m, int t, int path, 
     ca.qp = s.qp;
     ca.V = c->V;
     ca.shift = shift;
+    ca.split = c->opt.cost_split;
     ca.KT = s.KT;
     ca.KMT = s.KMT;
     SWMD_CK(launch_cost(ca, m.vrp, kprec, st));
@@ -163,8 +269,7 @@ static int launch_sequence(swmd_corpus *c, Slot &s, Mapping m, int t, int path, 
     if (path == SWMD_PATH_RESIDENT) {
         ResidentArgs ra{ia, t};
         ra.it.first = 1;
-        SWMD_CK(launch_resident(ra, m, kprec, c->sms, st));
-        return SWMD_OK;
+        return run_resident(c, ra, m, kprec, st);
     }
     for (int it = 0; it < t; ++it) {
         ia.first = it == 0;
@@ -431,6 +536,8 @@ int swmd_create_corpus(int32_t V, int32_t N, int64_t nnz, const int64_t *row_ptr
     if (Nl > 0 && (ce = cudaMemcpy(c->doc_orig, order.data(), sizeof(int32_t) * (size_t)Nl,
                                    cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(cuda_fail(ce, "copy document order"));
+    if ((rc = build_tiles(c))) return bail(rc);
+    if ((rc = build_tasks(c))) return bail(rc);
     if ((rc = alloc_slot(c, c->main, opt.max_vr, opt.k_precision, opt.path == SWMD_PATH_PLAIN)))
         return bail(rc);
     *out = c;
@@ -449,6 +556,8 @@ void swmd_destroy_corpus(swmd_corpus *c) {
         dev_free(c->doc_ptr);
         dev_free(c->nz);
         dev_free(c->doc_orig);
+        dev_free(c->tiles_dev);
+        dev_free(c->tasks_dev);
         if (c->stream) cudaStreamDestroy(c->stream);
     }
     delete c;
@@ -479,7 +588,15 @@ int swmd_corpus_set_options(swmd_corpus *c, const swmd_options *opt) {
     c->opt.column_shift = opt->column_shift;
     c->opt.team_lanes = opt->team_lanes;
     c->opt.lanes_per_nz = opt->lanes_per_nz;
-    return SWMD_OK;
+    c->opt.tile_threads = opt->tile_threads;
+    c->opt.nnz_per_lane = opt->nnz_per_lane;
+    c->opt.tile_nnz = opt->tile_nnz;
+    c->opt.cost_split = opt->cost_split;
+    c->opt.solver = opt->solver;
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    DeviceGuard guard(c->device);
+    return build_tiles(c);
 }
 
 static int check_query_args(swmd_corpus *c, int vr, float lambda, int t) {
@@ -575,6 +692,7 @@ int swmd_step_cost(swmd_corpus *c, const int32_t *d_ids, const float *d_r, int32
     ca.qp = s.qp;
     ca.V = c->V;
     ca.shift = c->opt.column_shift ? 1 : 0;
+    ca.split = c->opt.cost_split;
     ca.KT = s.KT;
     ca.KMT = s.KMT;
     SWMD_CK(launch_cost(ca, m.vrp, c->opt.k_precision, st));
@@ -641,8 +759,7 @@ int swmd_step_resident(swmd_corpus *c, int32_t v_r, int32_t max_iter, double *d_
     const Mapping m = choose_mapping(c, v_r, SWMD_PATH_RESIDENT);
     ResidentArgs ra{iter_args(c, s), max_iter};
     ra.it.out = d_out;
-    SWMD_CK(launch_resident(ra, m, c->opt.k_precision, c->sms, st));
-    return SWMD_OK;
+    return run_resident(c, ra, m, c->opt.k_precision, st);
 }
 
 int swmd_get_mapping(swmd_corpus *c, int32_t v_r, int32_t path, int32_t *out3) {

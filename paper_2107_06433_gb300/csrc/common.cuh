@@ -66,6 +66,7 @@ struct CostArgs {
     const QParams *qp;
     int V;
     int shift;
+    int split;     // threads per word in the row kernel (1, 2, 4)
     void *KT;
     void *KMT;
 };
@@ -97,6 +98,47 @@ cudaError_t launch_spmm(const IterArgs &a, Mapping m, int kprec, int sms, cudaSt
 cudaError_t launch_final(const IterArgs &a, Mapping m, int kprec, int sms, cudaStream_t s);
 cudaError_t launch_resident(const ResidentArgs &a, Mapping m, int kprec, int sms,
                             cudaStream_t s);
+// Documents packed into tiles of at most `nt` nonzeros (at most 64 documents,
+// consecutive in the internal order): tiles[0..n_tiles] are document offsets.
+struct TileSet {
+    const int *tiles;
+    int n_tiles;
+    int nt;        // nonzeros staged per block
+    int threads;   // threads per block
+    int npl;       // nonzeros per lane and pass (team size rule)
+};
+// Lanes of the team that owns a document of `len` nonzeros in the tiled resident
+// solver: the power of two in [4, 32] that gives about `npl` nonzeros per lane and
+// pass.  A function of the document alone, so a document's arithmetic (and
+// result) does not depend on which documents share its tile, batch or GPU.
+__host__ __device__ inline int team_lanes_for(int len, int npl) {
+    int g = 4;
+    while (g < 32 && g * npl < len) g *= 2;
+    return g;
+}
+// Team size of the register-resident solver: the power of two in [1, 32] that
+// covers `len` nonzeros with at most `npl` per lane (longer documents use 32
+// lanes and re-read their excess rows).  A function of the document alone.
+__host__ __device__ inline int reg_team_lanes(int len, int npl) {
+    int g = 1;
+    while (g < 32 && g * npl < len) g *= 2;
+    return g;
+}
+// Warp tasks of the register-resident solver: (first document, team size,
+// documents) -- consecutive documents of one team size, 32 / team size at most.
+struct TaskSet {
+    const int4 *tasks;
+    int n_tasks;
+    int npl;
+    int max_len;   // longest document (sizes the per-warp overflow buffer)
+};
+int regs_rows_per_lane(int vrp);
+cudaError_t launch_resident_regs(const ResidentArgs &a, int vrp, int kprec, const TaskSet &ts,
+                                 int sms, cudaStream_t s);
+size_t tiled_smem_bytes(int vrp, int kbytes, int nt);
+bool tiled_supported(int vrp, int kprec);
+cudaError_t launch_resident_tiled(const ResidentArgs &a, int vrp, int kprec, const TileSet &ts,
+                                  int sms, cudaStream_t s);
 bool mapping_supported(Mapping m);
 int vrp_for(int vr, int q);
 

@@ -77,6 +77,16 @@ struct swmd_corpus {
     std::vector<int> len_sorted;   // document lengths in internal order (host)
     double mean_len = 0;
 
+    // tile sets of the resident solver, one per nonzero budget (kTileBudgets)
+    int *tiles_dev = nullptr;
+    std::vector<int> tile_off;     // offset of each set in tiles_dev
+    std::vector<int> tile_count;   // tiles in each set
+    int tile_threads = 0, tile_npl = 0;   // geometry the sets were built for
+    // warp tasks of the register-resident solver, one list per rows-per-lane value
+    int4 *tasks_dev = nullptr;
+    int task_off[9] = {0};         // indexed by rows per lane (1..8)
+    int task_count[9] = {0};
+
     swmd::Slot main;               // workspace of the single-query path
     int64_t base_bytes = 0;
 
@@ -96,5 +106,15 @@ int enqueue_query(swmd_corpus *c, Slot &s, const int *d_ids, const float *d_r, i
                   float lambda, int t, double *d_out, int *d_status, cudaStream_t st,
                   bool allow_graph);
 int status_to_code(int st);
+// Launches the all-iterations solver: the shared-memory tiled kernel when the
+// query's layout allows it, else the register-only resident walk.
+int run_resident(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kprec, cudaStream_t st);
+constexpr int kTileBudgets[] = {64, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048};
+constexpr int kNumTileBudgets = 10;
+// (Re)builds the resident solver's tile sets for the corpus's current
+// tile_threads / nnz_per_lane (allocates: only at creation or on an option change).
+int build_tiles(swmd_corpus *c);
+// Builds the register-resident solver's warp task lists (at corpus creation).
+int build_tasks(swmd_corpus *c);
 
 }  // namespace swmd

@@ -130,6 +130,143 @@ __global__ void __launch_bounds__(kCostThreads) k_cost(CostArgs a) {
     }
 }
 
+// Query blocks of up to 32 words: the whole transposed query block Q^T[d4][VRP]
+// sits in shared memory (loaded once per persistent block).  TS adjacent threads
+// own one word and take its embedding row's float4 chunks in turn (chunk i goes
+// to thread i mod TS, so the TS threads read consecutive 16-byte pieces), with 4
+// chunks per thread in flight (register double buffer); the main loop has no
+// barrier.  The TS partial sums are combined with shuffles at the end.
+template <int VRP, int TS, class KT_t>
+__global__ void __launch_bounds__(kCostThreads) k_cost_rows(CostArgs a) {
+    static_assert(VRP % 4 == 0 && VRP <= 32, "VRP");
+    static_assert(TS == 1 || TS == 2 || TS == 4, "TS");
+    constexpr int PF = 4;   // float4 chunks per thread in flight
+    extern __shared__ __align__(16) float sQ[];   // sQ[dim * VRP + k] = E[q_k][dim], 0 for k >= v_r
+    const int vr = a.qp->vr;
+    const float lam = a.qp->lambda;
+    const int d4 = a.d4;
+    for (int i = threadIdx.x; i < d4 * VRP; i += kCostThreads) {
+        const int k = i / d4, dim = i - k * d4;
+        float val = 0.f;
+        if (k < vr) {
+            const int qid = __ldg(a.q_ids + k);
+            if (qid >= 0 && qid < a.V) val = __ldg(a.E + (size_t)qid * d4 + dim);
+        }
+        sQ[dim * VRP + k] = val;
+    }
+    __syncthreads();
+    const int n4 = d4 / 4;
+    const int t = threadIdx.x % TS;
+    KT_t *KT = reinterpret_cast<KT_t *>(a.KT);
+    KT_t *KMT = reinterpret_cast<KT_t *>(a.KMT);
+    const long per_block = kCostThreads / TS;
+    // every thread of a TS-group runs the same trip count (shuffles need the whole warp)
+    for (long base = (long)blockIdx.x * per_block; base < a.Vu; base += (long)gridDim.x * per_block) {
+        const long wi = base + threadIdx.x / TS;
+        const bool active = wi < a.Vu;
+        const float4 *row =
+            reinterpret_cast<const float4 *>(a.E + (size_t)(active ? __ldg(a.used + wi) : 0) * d4);
+        unsigned long long acc[VRP / 2];
+#pragma unroll
+        for (int i = 0; i < VRP / 2; ++i) acc[i] = 0ull;
+        float4 buf[PF];
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            const int ch = j * TS + t;
+            buf[j] = ch < n4 ? __ldg(row + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int c0 = 0; c0 < n4; c0 += PF * TS) {
+            float4 nxt[PF];
+#pragma unroll
+            for (int j = 0; j < PF; ++j) {
+                const int ch = c0 + (PF + j) * TS + t;
+                nxt[j] = ch < n4 ? __ldg(row + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int j = 0; j < PF; ++j) {
+                const int ch = c0 + j * TS + t;
+                if (ch < n4) {
+                    const float ev[4] = {buf[j].x, buf[j].y, buf[j].z, buf[j].w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const unsigned long long e2 = pack2(ev[e], ev[e]);
+                        const float4 *qrow = reinterpret_cast<const float4 *>(sQ + (4 * ch + e) * VRP);
+#pragma unroll
+                        for (int c = 0; c < VRP / 4; ++c) {
+                            const float4 qv = qrow[c];
+                            acc[2 * c] = sqdiff_acc2(pack2(qv.x, qv.y), e2, acc[2 * c]);
+                            acc[2 * c + 1] = sqdiff_acc2(pack2(qv.z, qv.w), e2, acc[2 * c + 1]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < PF; ++j) buf[j] = nxt[j];
+        }
+        float m[VRP];
+#pragma unroll
+        for (int i = 0; i < VRP / 2; ++i) {
+            float x, y;
+            unpack2(acc[i], x, y);
+#pragma unroll
+            for (int o = 1; o < TS; o <<= 1) {
+                x += __shfl_xor_sync(0xffffffffu, x, o);
+                y += __shfl_xor_sync(0xffffffffu, y, o);
+            }
+            m[2 * i] = sqrtf(x);
+            m[2 * i + 1] = sqrtf(y);
+        }
+        if (!active) continue;
+        float mn = INFINITY;
+#pragma unroll
+        for (int k = 0; k < VRP; ++k)
+            if (k < vr) mn = fminf(mn, m[k]);
+        const float sh = (a.shift && mn < INFINITY) ? mn : 0.f;
+#pragma unroll
+        for (int c = 0; c < VRP / 4; ++c) {
+            if (c % TS != t) continue;
+            float kv[4], kmv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int k = 4 * c + j;
+                const float kk = (k < vr) ? expf(-lam * (m[k] - sh)) : 0.f;
+                kv[j] = kk;
+                kmv[j] = kk * m[k];
+            }
+            KIO<KT_t>::store4(KT, wi * (VRP / 4) + c, make_float4(kv[0], kv[1], kv[2], kv[3]));
+            KIO<KT_t>::store4(KMT, wi * (VRP / 4) + c, make_float4(kmv[0], kmv[1], kmv[2], kmv[3]));
+        }
+    }
+}
+
+template <int VRP, int TS, class KT_t>
+cudaError_t run_rows(const CostArgs &a, cudaStream_t s) {
+    auto kern = k_cost_rows<VRP, TS, KT_t>;
+    const size_t smem = (size_t)a.d4 * VRP * sizeof(float);
+    static size_t configured = 0;
+    static int per_sm = 0;
+    static size_t per_sm_smem = 0;
+    if (smem > 48 * 1024 && configured < smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    if (per_sm <= 0 || per_sm_smem != smem) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCostThreads, smem) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        per_sm_smem = smem;
+    }
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long per_block = kCostThreads / TS;
+    long blocks = (a.Vu + per_block - 1) / per_block;
+    if (blocks > (long)sms * per_sm) blocks = (long)sms * per_sm;
+    if (blocks > 0) kern<<<(unsigned)blocks, kCostThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int KPT, int T, class KT_t>
 cudaError_t run(const CostArgs &a, cudaStream_t s) {
     const int words_per_block = kCostThreads / T;
@@ -140,6 +277,19 @@ cudaError_t run(const CostArgs &a, cudaStream_t s) {
 
 template <class KT_t>
 cudaError_t dispatch(const CostArgs &a, int vrp, cudaStream_t s) {
+    if (vrp <= 32 && (size_t)a.d4 * vrp * sizeof(float) <= 100 * 1024) {
+        const int ts = a.split == 1 || a.split == 4 ? a.split : 2;
+        switch (vrp * 10 + ts) {
+#define SWMD_ROWS(V)                                      \
+    case V * 10 + 1: return run_rows<V, 1, KT_t>(a, s); \
+    case V * 10 + 2: return run_rows<V, 2, KT_t>(a, s); \
+    case V * 10 + 4: return run_rows<V, 4, KT_t>(a, s);
+            SWMD_ROWS(4) SWMD_ROWS(8) SWMD_ROWS(12) SWMD_ROWS(16) SWMD_ROWS(20) SWMD_ROWS(24)
+            SWMD_ROWS(28) SWMD_ROWS(32)
+#undef SWMD_ROWS
+            default: break;
+        }
+    }
     switch (vrp) {
 #define SWMD_COST_T1(V) \
     case V: return run<V, 1, KT_t>(a, s);

@@ -117,6 +117,7 @@ extern "C" int swmd_query_noalloc(swmd_corpus *c, const int32_t *d_ids, const fl
     ca.qp = qp;
     ca.V = c->V;
     ca.shift = c->opt.column_shift ? 1 : 0;
+    ca.split = c->opt.cost_split;
     ca.KT = KT;
     ca.KMT = KMT;
     SWMD_CK(launch_cost(ca, m.vrp, kprec, st));
@@ -132,6 +133,5 @@ extern "C" int swmd_query_noalloc(swmd_corpus *c, const int32_t *d_ids, const fl
     ia.N = c->Nl;
     ia.first = 1;
     ResidentArgs ra{ia, max_iter};
-    SWMD_CK(launch_resident(ra, m, kprec, c->sms, st));
-    return SWMD_OK;
+    return run_resident(c, ra, m, kprec, st);
 }

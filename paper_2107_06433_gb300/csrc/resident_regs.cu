@@ -1,0 +1,363 @@
+// a3 x t + a4 in one launch with each document's K^T rows held in registers.
+//
+// Every column of c is an independent problem in Algorithm 1, and one x-update of
+// document j only touches the rows K^T[w] of its own words: with A_j the
+// len_j x v_r matrix of those rows, an iteration is s = A_j u, tau = c_j ./ s,
+// acc = A_j^T tau, u = r ./ acc (the fused SDDMM_SpMM of Section III-C).  Here A_j
+// is spread over a team of G lanes (lane p holds rows p, p + G, ... -- up to NPL
+// of them -- in registers) and stays there for all t iterations, so an iteration
+// is register FMAs plus one team reduction of acc.  The reduction goes through a
+// per-warp shared-memory transpose: every lane stores its partial acc, lane p
+// sums the entries k = p, p + G, ... over the team, divides r_k by it, and
+// publishes u_k; the team then reads the new u back.  The final step (Algorithm 1
+// last line) reloads the same positions with the KM^T rows.
+//
+// Documents longer than 32 * NPL use a whole warp; their remaining K^T rows are
+// staged once into a per-warp shared-memory buffer (sized from the corpus's
+// longest document, up to `ovf_cap` rows; any rows beyond that are read from L2
+// each iteration).  Teams are formed from documents of one team size, so a
+// document's arithmetic depends on its own length only.
+#include "walk.cuh"
+
+namespace swmd {
+namespace {
+
+constexpr int kRegThreads = 128;
+constexpr int kWarps = kRegThreads / 32;
+
+template <int VRP, int NPL, class KT_t>
+__global__ void __launch_bounds__(kRegThreads) k_resident_regs(ResidentArgs ra, const int4 *tasks,
+                                                               int n_tasks, int ovf_cap) {
+    constexpr int C = VRP / 4;
+    const IterArgs &a = ra.it;
+    // per warp: 32 partial accumulators of VRP floats, then the teams' new u
+    __shared__ __align__(16) float s_acc[kWarps][32 * VRP];
+    __shared__ __align__(16) float s_u[kWarps][32 * VRP];
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int vr = a.qp->vr;
+    const float u0 = a.qp->u0;
+    int *const status = a.qp->status;
+    double *const out = a.out ? a.out : a.qp->out;
+    const KT_t *KT = reinterpret_cast<const KT_t *>(a.KT);
+    const KT_t *KMT = reinterpret_cast<const KT_t *>(a.KMT);
+    float *wacc = s_acc[warp];
+    float *wu = s_u[warp];
+    // per-warp overflow rows (VRP floats each) and their counts
+    extern __shared__ __align__(16) float s_ovf[];
+    float *wrow = s_ovf + (size_t)warp * ovf_cap * (VRP + 1);
+    float *wc = wrow + (size_t)ovf_cap * VRP;
+
+    const long gwarp = ((long)blockIdx.x * kRegThreads + threadIdx.x) >> 5;
+    const long nwarps = ((long)gridDim.x * kRegThreads) >> 5;
+    for (long task = gwarp; task < n_tasks; task += nwarps) {
+        const int4 tk = __ldg(tasks + task);   // first document, team size, documents
+        const int d0 = tk.x, G = tk.y, nd = tk.z;
+        const int team = lane / G;
+        const int p = lane - team * G;
+        const bool has = team < nd;
+        const int doc = d0 + team;
+        int beg = 0, len = 0;
+        if (has) {
+            beg = __ldg(a.doc_ptr + doc);
+            len = __ldg(a.doc_ptr + doc + 1) - beg;
+        }
+        // overflow rows (documents longer than G * NPL, which have G = 32 and one
+        // document per warp): the first ovf_cap of them go to shared memory once
+        int extra = len > G * NPL ? (len - G * NPL + G - 1) / G : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) extra = max(extra, __shfl_xor_sync(kFull, extra, o));
+        int n_ovf = 0;   // rows held in shared memory (whole warp agrees)
+        if (extra > 0) {
+            const int n_all = __shfl_sync(kFull, len, 0) - 32 * NPL;
+            const int beg0 = __shfl_sync(kFull, beg, 0);
+            n_ovf = n_all < ovf_cap ? n_all : ovf_cap;
+            for (int i = lane; i < n_ovf * C; i += 32) {
+                const int row = i / C, c = i - row * C;
+                const int2 e = __ldg(a.nz + beg0 + 32 * NPL + row);
+                reinterpret_cast<float4 *>(wrow)[i] = KIO<KT_t>::load4(KT, (long)e.x * C + c);
+                if (c == 0) wc[row] = __int_as_float(e.y);
+            }
+            __syncwarp();
+        }
+
+        float rows[NPL][VRP];
+        float cv[NPL];
+        int wid[NPL];
+#pragma unroll
+        for (int j = 0; j < NPL; ++j) {
+            const int idx = p + G * j;
+            const bool valid = idx < len;
+            int2 e = make_int2(0, 0);
+            if (valid) e = __ldg(a.nz + beg + idx);
+            wid[j] = e.x;
+            cv[j] = valid ? __int_as_float(e.y) : 0.f;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float4 t = valid ? KIO<KT_t>::load4(KT, (long)e.x * C + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+                rows[j][4 * c] = t.x; rows[j][4 * c + 1] = t.y; rows[j][4 * c + 2] = t.z; rows[j][4 * c + 3] = t.w;
+            }
+        }
+        float uu[VRP];
+#pragma unroll
+        for (int k = 0; k < VRP; ++k) uu[k] = (has && k < vr) ? u0 : 0.f;
+
+        for (int it = 0; it < ra.t; ++it) {
+            float acc[VRP];
+#pragma unroll
+            for (int k = 0; k < VRP; ++k) acc[k] = 0.f;
+            bool tiny_any = false;
+#pragma unroll
+            for (int j = 0; j < NPL; ++j) {
+                float d4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int k = 0; k < VRP; ++k) d4[k & 3] = fmaf(rows[j][k], uu[k], d4[k & 3]);
+                const float dot = (d4[0] + d4[1]) + (d4[2] + d4[3]);
+                const bool valid = cv[j] > 0.f;
+                tiny_any |= valid && !(dot >= 0x1p-100f);
+                const float tau = valid ? __fdividef(cv[j], dot) : 0.f;
+#pragma unroll
+                for (int k = 0; k < VRP; ++k) acc[k] = fmaf(tau, rows[j][k], acc[k]);
+            }
+            for (int x = 0; x < extra; ++x) {
+                const int idx = p + G * (NPL + x);
+                const int o = idx - 32 * NPL;   // row in the overflow list (G == 32 here)
+                const bool valid = idx < len;
+                float kr[VRP];
+                float cval;
+                if (o < n_ovf) {
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        const float4 t = reinterpret_cast<const float4 *>(wrow + (size_t)o * VRP)[c];
+                        kr[4 * c] = t.x; kr[4 * c + 1] = t.y; kr[4 * c + 2] = t.z; kr[4 * c + 3] = t.w;
+                    }
+                    cval = wc[o];
+                } else {
+                    int2 e = make_int2(0, 0);
+                    if (valid) e = __ldg(a.nz + beg + idx);
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        const float4 t = KIO<KT_t>::load4(KT, (long)e.x * C + c);
+                        kr[4 * c] = t.x; kr[4 * c + 1] = t.y; kr[4 * c + 2] = t.z; kr[4 * c + 3] = t.w;
+                    }
+                    cval = __int_as_float(e.y);
+                }
+                float d4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int k = 0; k < VRP; ++k) d4[k & 3] = fmaf(kr[k], uu[k], d4[k & 3]);
+                const float dot = (d4[0] + d4[1]) + (d4[2] + d4[3]);
+                tiny_any |= valid && !(dot >= 0x1p-100f);
+                const float tau = valid ? __fdividef(cval, dot) : 0.f;
+#pragma unroll
+                for (int k = 0; k < VRP; ++k) acc[k] = fmaf(tau, kr[k], acc[k]);
+            }
+            if (__any_sync(kFull, tiny_any)) {
+                SWMD_COLD_PATH();
+                // some K^T u fell below 2^-100: redo this lane's accumulation with
+                // the affected denominators in FP64
+#pragma unroll
+                for (int k = 0; k < VRP; ++k) acc[k] = 0.f;
+#pragma unroll
+                for (int j = 0; j < NPL; ++j) {
+                    float d4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int k = 0; k < VRP; ++k) d4[k & 3] = fmaf(rows[j][k], uu[k], d4[k & 3]);
+                    const float dot = (d4[0] + d4[1]) + (d4[2] + d4[3]);
+                    const bool valid = cv[j] > 0.f;
+                    float tau = valid ? __fdividef(cv[j], dot) : 0.f;
+                    if (valid && !(dot >= 0x1p-100f)) {
+                        double s = 0.0;
+#pragma unroll
+                        for (int k = 0; k < VRP; ++k) s = fma((double)rows[j][k], (double)uu[k], s);
+                        tau = s > 0.0 ? (float)((double)cv[j] / s) : 0.f;
+                        atomicOr(status, s > 0.0 ? ST_GUARD : ST_NUMERIC);
+                    }
+#pragma unroll
+                    for (int k = 0; k < VRP; ++k) acc[k] = fmaf(tau, rows[j][k], acc[k]);
+                }
+                for (int x = 0; x < extra; ++x) {
+                    const int idx = p + G * (NPL + x);
+                    const bool valid = idx < len;
+                    int2 e = make_int2(0, 0);
+                    if (valid) e = __ldg(a.nz + beg + idx);
+                    float kr[VRP];
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        const float4 t = KIO<KT_t>::load4(KT, (long)e.x * C + c);
+                        kr[4 * c] = t.x; kr[4 * c + 1] = t.y; kr[4 * c + 2] = t.z; kr[4 * c + 3] = t.w;
+                    }
+                    double s = 0.0;
+#pragma unroll
+                    for (int k = 0; k < VRP; ++k) s = fma((double)kr[k], (double)uu[k], s);
+                    float tau = 0.f;
+                    if (valid) {
+                        tau = s > 0.0 ? (float)((double)__int_as_float(e.y) / s) : 0.f;
+                        if (!(s > 0.0)) atomicOr(status, ST_NUMERIC);
+                    }
+#pragma unroll
+                    for (int k = 0; k < VRP; ++k) acc[k] = fmaf(tau, kr[k], acc[k]);
+                }
+            }
+            // team reduction of acc through the per-warp transpose buffer
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+                reinterpret_cast<float4 *>(wacc + lane * VRP)[c] =
+                    make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
+            __syncwarp();
+            bool bad = false;
+            for (int k = p; k < VRP; k += G) {
+                float s = 0.f;
+                for (int g = 0; g < G; ++g) s += wacc[(team * G + g) * VRP + k];
+                const float rk = (has && k < vr) ? __ldg(a.r + k) : 0.f;
+                const float nu = rk > 0.f ? __fdividef(rk, s) : 0.f;
+                bad |= !(nu < INFINITY);
+                wu[team * VRP + k] = nu;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float4 t = reinterpret_cast<const float4 *>(wu + team * VRP)[c];
+                uu[4 * c] = t.x; uu[4 * c + 1] = t.y; uu[4 * c + 2] = t.z; uu[4 * c + 3] = t.w;
+            }
+            if (bad) atomicOr(status, ST_NUMERIC);
+        }
+
+        // final step: s = K^T[w].u and m = KM^T[w].u per nonzero, WMD = sum c m / s
+        double dist = 0.0;
+#pragma unroll
+        for (int j = 0; j < NPL; ++j) {
+            float d4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < VRP; ++k) d4[k & 3] = fmaf(rows[j][k], uu[k], d4[k & 3]);
+            const float dot = (d4[0] + d4[1]) + (d4[2] + d4[3]);
+            const bool valid = cv[j] > 0.f;
+            float m4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float4 t = valid ? KIO<KT_t>::load4(KMT, (long)wid[j] * C + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+                m4[0] = fmaf(t.x, uu[4 * c], m4[0]);
+                m4[1] = fmaf(t.y, uu[4 * c + 1], m4[1]);
+                m4[2] = fmaf(t.z, uu[4 * c + 2], m4[2]);
+                m4[3] = fmaf(t.w, uu[4 * c + 3], m4[3]);
+            }
+            const float dm = (m4[0] + m4[1]) + (m4[2] + m4[3]);
+            if (valid) {
+                if (dot >= 0x1p-100f) {
+                    dist += (double)(cv[j] * (dm / dot));
+                } else {
+                    SWMD_COLD_PATH();
+                    double s = 0.0, m = 0.0;
+#pragma unroll
+                    for (int k = 0; k < VRP; ++k) s = fma((double)rows[j][k], (double)uu[k], s);
+                    for (int c = 0; c < C; ++c) {
+                        const float4 t = KIO<KT_t>::load4(KMT, (long)wid[j] * C + c);
+                        m = fma((double)t.x, (double)uu[4 * c], m);
+                        m = fma((double)t.y, (double)uu[4 * c + 1], m);
+                        m = fma((double)t.z, (double)uu[4 * c + 2], m);
+                        m = fma((double)t.w, (double)uu[4 * c + 3], m);
+                    }
+                    dist += (double)cv[j] * (m / s);
+                    atomicOr(status, s > 0.0 ? ST_GUARD : ST_NUMERIC);
+                }
+            }
+        }
+        for (int x = 0; x < extra; ++x) {
+            const int idx = p + G * (NPL + x);
+            const bool valid = idx < len;
+            int2 e = make_int2(0, 0);
+            if (valid) e = __ldg(a.nz + beg + idx);
+            float d4[4] = {0.f, 0.f, 0.f, 0.f}, m4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float4 t = KIO<KT_t>::load4(KT, (long)e.x * C + c);
+                const float4 m = KIO<KT_t>::load4(KMT, (long)e.x * C + c);
+                d4[0] = fmaf(t.x, uu[4 * c], d4[0]); d4[1] = fmaf(t.y, uu[4 * c + 1], d4[1]);
+                d4[2] = fmaf(t.z, uu[4 * c + 2], d4[2]); d4[3] = fmaf(t.w, uu[4 * c + 3], d4[3]);
+                m4[0] = fmaf(m.x, uu[4 * c], m4[0]); m4[1] = fmaf(m.y, uu[4 * c + 1], m4[1]);
+                m4[2] = fmaf(m.z, uu[4 * c + 2], m4[2]); m4[3] = fmaf(m.w, uu[4 * c + 3], m4[3]);
+            }
+            const float dot = (d4[0] + d4[1]) + (d4[2] + d4[3]);
+            const float dm = (m4[0] + m4[1]) + (m4[2] + m4[3]);
+            if (valid) {
+                if (dot >= 0x1p-100f) {
+                    dist += (double)(__int_as_float(e.y) * (dm / dot));
+                } else {
+                    SWMD_COLD_PATH();
+                    atomicOr(status, ST_NUMERIC);
+                    dist += (double)(__int_as_float(e.y) * (dm / dot));
+                }
+            }
+        }
+        for (int o = 1; o < G; o <<= 1) dist += __shfl_xor_sync(kFull, dist, o);
+        if (has && p == 0) {
+            if (!(fabs(dist) < INFINITY)) atomicOr(status, ST_NUMERIC);
+            out[__ldg(a.doc_orig + doc)] = dist;
+        }
+        __syncwarp();   // the next task reuses the warp's shared buffers
+    }
+}
+
+template <int VRP, int NPL, class KT_t>
+cudaError_t run_regs(const ResidentArgs &a, const TaskSet &ts, int sms, cudaStream_t s) {
+    auto kern = k_resident_regs<VRP, NPL, KT_t>;
+    // overflow buffer: rows beyond 32 * NPL of the longest document, at most 40 KB per warp
+    int ovf = ts.max_len - 32 * NPL;
+    const int cap_rows = (40 * 1024) / ((VRP + 1) * 4);
+    if (ovf < 0) ovf = 0;
+    if (ovf > cap_rows) ovf = cap_rows;
+    ovf = (ovf + 3) / 4 * 4;   // keeps every warp's buffer 16-byte aligned
+    const size_t smem = (size_t)kWarps * ovf * (VRP + 1) * sizeof(float);
+    static size_t configured = 0;
+    static int per_sm = 0;
+    static size_t per_sm_smem = (size_t)-1;
+    if (smem > 48 * 1024 - sizeof(float) * 2 * kWarps * 32 * VRP && configured < smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    if (per_sm <= 0 || per_sm_smem != smem) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRegThreads, smem) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        per_sm_smem = smem;
+    }
+    long blocks = ((long)ts.n_tasks + kWarps - 1) / kWarps;
+    if (blocks > (long)sms * per_sm) blocks = (long)sms * per_sm;
+    if (blocks > 0) kern<<<(unsigned)blocks, kRegThreads, smem, s>>>(a, ts.tasks, ts.n_tasks, ovf);
+    return cudaGetLastError();
+}
+
+template <class KT_t>
+cudaError_t dispatch_regs(const ResidentArgs &a, int vrp, const TaskSet &ts, int sms, cudaStream_t s) {
+    switch (vrp * 100 + ts.npl) {
+#define SWMD_R(V, N) \
+    case V * 100 + N: return run_regs<V, N, KT_t>(a, ts, sms, s);
+        SWMD_R(4, 8) SWMD_R(8, 8) SWMD_R(12, 4) SWMD_R(16, 4) SWMD_R(20, 4) SWMD_R(24, 2)
+        SWMD_R(28, 2) SWMD_R(32, 2) SWMD_R(12, 8) SWMD_R(16, 2) SWMD_R(20, 2) SWMD_R(20, 3)
+        SWMD_R(24, 3) SWMD_R(32, 1) SWMD_R(24, 4)
+#undef SWMD_R
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+int regs_rows_per_lane(int vrp) {
+    if (vrp <= 8) return 8;
+    if (vrp <= 20) return 4;
+    if (vrp <= 32) return 2;
+    return 0;   // not supported: the shared-memory tiled solver takes over
+}
+
+cudaError_t launch_resident_regs(const ResidentArgs &a, int vrp, int kprec, const TaskSet &ts,
+                                 int sms, cudaStream_t s) {
+    switch (kprec) {
+        case 0: return dispatch_regs<float>(a, vrp, ts, sms, s);
+        case 1: return dispatch_regs<__nv_bfloat16>(a, vrp, ts, sms, s);
+        case 2: return dispatch_regs<__half>(a, vrp, ts, sms, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace swmd

@@ -28,6 +28,12 @@ namespace swmd {
 
 enum class Kind { Fused, Sddmm, Spmm, Final };
 
+// The FP64 guard of K^T u runs only when some lane's FP32 dot fell below
+// 2^-100.  The empty volatile asm at its entry keeps the compiler from turning
+// the branch into predicated code evaluated on every nonzero: FP64 throughput is
+// a small fraction of FP32 on this GPU.
+#define SWMD_COLD_PATH() asm volatile("" ::: "memory")
+
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWalkThreads = 256;
 
@@ -137,6 +143,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(IterArgs a) {
                 const bool tiny = valid && !(dot >= 0x1p-100f);
                 double dot64 = 0.0, dm64 = 0.0;
                 if (__any_sync(kFull, tiny)) {
+                    SWMD_COLD_PATH();
 #pragma unroll
                     for (int s = 0; s < S; ++s) dot64 = fma((double)kr[s], (double)uu[s], dot64);
 #pragma unroll
@@ -286,6 +293,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_resident(ResidentArgs ra) {
                 const bool tiny = valid && !(dot >= 0x1p-100f);
                 float tau = valid ? cval / dot : 0.f;
                 if (__any_sync(kFull, tiny)) {
+                    SWMD_COLD_PATH();
                     double dot64 = 0.0;
 #pragma unroll
                     for (int s = 0; s < S; ++s) dot64 = fma((double)kr[s], (double)uu[s], dot64);
@@ -344,6 +352,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_resident(ResidentArgs ra) {
             const bool tiny = valid && !(dot >= 0x1p-100f);
             double contrib = valid ? (double)(cval * (dm / dot)) : 0.0;
             if (__any_sync(kFull, tiny)) {
+                    SWMD_COLD_PATH();
                 double dot64 = 0.0, dm64 = 0.0;
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
