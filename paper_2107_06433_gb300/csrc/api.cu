@@ -215,7 +215,11 @@ int run_resident(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kprec, c
     if (c->tasks_dev && npl > 0 && (solver == 0 || solver == 1)) {
         TaskSet ts{c->tasks_dev + c->task_off[npl], c->task_count[npl], npl,
                    c->Nl > 0 ? c->len_sorted[0] : 0};
-        SWMD_CK(launch_resident_regs(ra, m.vrp, kprec, ts, c->sms, st));
+        cudaError_t e = launch_resident_regs(ra, m.vrp, kprec, ts, c->sms, st);
+        if (e != cudaSuccess)
+            return set_error(e == cudaErrorMemoryAllocation ? SWMD_ENOMEM : SWMD_ECUDA,
+                             "register-resident solver (VRP %d, %d rows per lane, longest document %d): %s",
+                             m.vrp, npl, ts.max_len, cudaGetErrorString(e));
         return SWMD_OK;
     }
     if (c->tiles_dev && tiled_supported(m.vrp, kprec) && solver != 3) {

@@ -254,7 +254,7 @@ cudaError_t run_rows(const CostArgs &a, cudaStream_t s) {
     if (per_sm <= 0 || per_sm_smem != smem) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCostThreads, smem) != cudaSuccess ||
             per_sm < 1)
-            per_sm = 1;
+            { (void)cudaGetLastError(); per_sm = 1; }
         per_sm_smem = smem;
     }
     int sms = 0, dev = 0;

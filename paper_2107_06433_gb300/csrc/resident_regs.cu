@@ -25,206 +25,89 @@ namespace {
 constexpr int kRegThreads = 128;
 constexpr int kWarps = kRegThreads / 32;
 
-template <int VRP, int NPL, class KT_t>
-__global__ void __launch_bounds__(kRegThreads) k_resident_regs(ResidentArgs ra, const int4 *tasks,
-                                                               int n_tasks, int ovf_cap) {
-    constexpr int C = VRP / 4;
-    const IterArgs &a = ra.it;
-    // per warp: 32 partial accumulators of VRP floats, then the teams' new u
-    __shared__ __align__(16) float s_acc[kWarps][32 * VRP];
-    __shared__ __align__(16) float s_u[kWarps][32 * VRP];
+// Floats per team in the per-warp transpose buffer: G rows of VRP plus padding
+// that shifts consecutive teams by G banks (conflict-free reads for G >= 4).
+template <int VRP, int G>
+__host__ __device__ constexpr int team_stride() {
+    return G * VRP + ((G >= 4) ? ((G - (G * VRP) % 32) % 32 + 32) % 32 : 0);
+}
 
-    const int warp = threadIdx.x >> 5;
-    const int lane = threadIdx.x & 31;
+template <int VRP, int NPL, int G, class KT_t>
+__device__ __forceinline__ void regs_task(const IterArgs &a, int t, int4 tk, int lane, float *wacc,
+                                          float *wrow, float *wc, int ovf_cap) {
+    constexpr int C = VRP / 4;
+    constexpr int TS = team_stride<VRP, G>();
+    constexpr int KS = (VRP + G - 1) / G;   // entries of u each lane finishes
     const int vr = a.qp->vr;
     const float u0 = a.qp->u0;
     int *const status = a.qp->status;
     double *const out = a.out ? a.out : a.qp->out;
     const KT_t *KT = reinterpret_cast<const KT_t *>(a.KT);
     const KT_t *KMT = reinterpret_cast<const KT_t *>(a.KMT);
-    float *wacc = s_acc[warp];
-    float *wu = s_u[warp];
-    // per-warp overflow rows (VRP floats each) and their counts
-    extern __shared__ __align__(16) float s_ovf[];
-    float *wrow = s_ovf + (size_t)warp * ovf_cap * (VRP + 1);
-    float *wc = wrow + (size_t)ovf_cap * VRP;
 
-    const long gwarp = ((long)blockIdx.x * kRegThreads + threadIdx.x) >> 5;
-    const long nwarps = ((long)gridDim.x * kRegThreads) >> 5;
-    for (long task = gwarp; task < n_tasks; task += nwarps) {
-        const int4 tk = __ldg(tasks + task);   // first document, team size, documents
-        const int d0 = tk.x, G = tk.y, nd = tk.z;
-        const int team = lane / G;
-        const int p = lane - team * G;
-        const bool has = team < nd;
-        const int doc = d0 + team;
-        int beg = 0, len = 0;
-        if (has) {
-            beg = __ldg(a.doc_ptr + doc);
-            len = __ldg(a.doc_ptr + doc + 1) - beg;
-        }
-        // overflow rows (documents longer than G * NPL, which have G = 32 and one
-        // document per warp): the first ovf_cap of them go to shared memory once
-        int extra = len > G * NPL ? (len - G * NPL + G - 1) / G : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) extra = max(extra, __shfl_xor_sync(kFull, extra, o));
-        int n_ovf = 0;   // rows held in shared memory (whole warp agrees)
+    const int d0 = tk.x, nd = tk.z;
+    const int team = lane / G;
+    const int p = lane - team * G;
+    const bool has = team < nd;
+    const int doc = d0 + team;
+    int beg = 0, len = 0;
+    if (has) {
+        beg = __ldg(a.doc_ptr + doc);
+        len = __ldg(a.doc_ptr + doc + 1) - beg;
+    }
+    float *tacc = wacc + team * TS;   // this team's G partial accumulators
+
+    // overflow rows (documents longer than G * NPL exist only with G = 32, one
+    // document per warp): the first ovf_cap go to shared memory once
+    int extra = 0, n_ovf = 0;
+    if (G == 32) {
+        extra = len > 32 * NPL ? (len - 32 * NPL + 31) / 32 : 0;
         if (extra > 0) {
-            const int n_all = __shfl_sync(kFull, len, 0) - 32 * NPL;
-            const int beg0 = __shfl_sync(kFull, beg, 0);
+            const int n_all = len - 32 * NPL;
             n_ovf = n_all < ovf_cap ? n_all : ovf_cap;
             for (int i = lane; i < n_ovf * C; i += 32) {
                 const int row = i / C, c = i - row * C;
-                const int2 e = __ldg(a.nz + beg0 + 32 * NPL + row);
+                const int2 e = __ldg(a.nz + beg + 32 * NPL + row);
                 reinterpret_cast<float4 *>(wrow)[i] = KIO<KT_t>::load4(KT, (long)e.x * C + c);
                 if (c == 0) wc[row] = __int_as_float(e.y);
             }
             __syncwarp();
         }
+    }
 
-        float rows[NPL][VRP];
-        float cv[NPL];
-        int wid[NPL];
+    float rows[NPL][VRP];
+    float cv[NPL];
+    int wid[NPL];
 #pragma unroll
-        for (int j = 0; j < NPL; ++j) {
-            const int idx = p + G * j;
-            const bool valid = idx < len;
-            int2 e = make_int2(0, 0);
-            if (valid) e = __ldg(a.nz + beg + idx);
-            wid[j] = e.x;
-            cv[j] = valid ? __int_as_float(e.y) : 0.f;
+    for (int j = 0; j < NPL; ++j) {
+        const int idx = p + G * j;
+        const bool valid = idx < len;
+        int2 e = make_int2(0, 0);
+        if (valid) e = __ldg(a.nz + beg + idx);
+        wid[j] = e.x;
+        cv[j] = valid ? __int_as_float(e.y) : 0.f;
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const float4 t = valid ? KIO<KT_t>::load4(KT, (long)e.x * C + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-                rows[j][4 * c] = t.x; rows[j][4 * c + 1] = t.y; rows[j][4 * c + 2] = t.z; rows[j][4 * c + 3] = t.w;
-            }
+        for (int c = 0; c < C; ++c) {
+            const float4 v = valid ? KIO<KT_t>::load4(KT, (long)e.x * C + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            rows[j][4 * c] = v.x; rows[j][4 * c + 1] = v.y; rows[j][4 * c + 2] = v.z; rows[j][4 * c + 3] = v.w;
         }
-        float uu[VRP];
+    }
+    // r for the entries of u this lane finishes (k = p + G i)
+    float rk[KS];
 #pragma unroll
-        for (int k = 0; k < VRP; ++k) uu[k] = (has && k < vr) ? u0 : 0.f;
+    for (int i = 0; i < KS; ++i) {
+        const int k = p + G * i;
+        rk[i] = (has && k < VRP && k < vr) ? __ldg(a.r + k) : 0.f;
+    }
+    float uu[VRP];
+#pragma unroll
+    for (int k = 0; k < VRP; ++k) uu[k] = (has && k < vr) ? u0 : 0.f;
 
-        for (int it = 0; it < ra.t; ++it) {
-            float acc[VRP];
+    for (int it = 0; it < t; ++it) {
+        float acc[VRP];
 #pragma unroll
-            for (int k = 0; k < VRP; ++k) acc[k] = 0.f;
-            bool tiny_any = false;
-#pragma unroll
-            for (int j = 0; j < NPL; ++j) {
-                float d4[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                for (int k = 0; k < VRP; ++k) d4[k & 3] = fmaf(rows[j][k], uu[k], d4[k & 3]);
-                const float dot = (d4[0] + d4[1]) + (d4[2] + d4[3]);
-                const bool valid = cv[j] > 0.f;
-                tiny_any |= valid && !(dot >= 0x1p-100f);
-                const float tau = valid ? __fdividef(cv[j], dot) : 0.f;
-#pragma unroll
-                for (int k = 0; k < VRP; ++k) acc[k] = fmaf(tau, rows[j][k], acc[k]);
-            }
-            for (int x = 0; x < extra; ++x) {
-                const int idx = p + G * (NPL + x);
-                const int o = idx - 32 * NPL;   // row in the overflow list (G == 32 here)
-                const bool valid = idx < len;
-                float kr[VRP];
-                float cval;
-                if (o < n_ovf) {
-#pragma unroll
-                    for (int c = 0; c < C; ++c) {
-                        const float4 t = reinterpret_cast<const float4 *>(wrow + (size_t)o * VRP)[c];
-                        kr[4 * c] = t.x; kr[4 * c + 1] = t.y; kr[4 * c + 2] = t.z; kr[4 * c + 3] = t.w;
-                    }
-                    cval = wc[o];
-                } else {
-                    int2 e = make_int2(0, 0);
-                    if (valid) e = __ldg(a.nz + beg + idx);
-#pragma unroll
-                    for (int c = 0; c < C; ++c) {
-                        const float4 t = KIO<KT_t>::load4(KT, (long)e.x * C + c);
-                        kr[4 * c] = t.x; kr[4 * c + 1] = t.y; kr[4 * c + 2] = t.z; kr[4 * c + 3] = t.w;
-                    }
-                    cval = __int_as_float(e.y);
-                }
-                float d4[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                for (int k = 0; k < VRP; ++k) d4[k & 3] = fmaf(kr[k], uu[k], d4[k & 3]);
-                const float dot = (d4[0] + d4[1]) + (d4[2] + d4[3]);
-                tiny_any |= valid && !(dot >= 0x1p-100f);
-                const float tau = valid ? __fdividef(cval, dot) : 0.f;
-#pragma unroll
-                for (int k = 0; k < VRP; ++k) acc[k] = fmaf(tau, kr[k], acc[k]);
-            }
-            if (__any_sync(kFull, tiny_any)) {
-                SWMD_COLD_PATH();
-                // some K^T u fell below 2^-100: redo this lane's accumulation with
-                // the affected denominators in FP64
-#pragma unroll
-                for (int k = 0; k < VRP; ++k) acc[k] = 0.f;
-#pragma unroll
-                for (int j = 0; j < NPL; ++j) {
-                    float d4[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                    for (int k = 0; k < VRP; ++k) d4[k & 3] = fmaf(rows[j][k], uu[k], d4[k & 3]);
-                    const float dot = (d4[0] + d4[1]) + (d4[2] + d4[3]);
-                    const bool valid = cv[j] > 0.f;
-                    float tau = valid ? __fdividef(cv[j], dot) : 0.f;
-                    if (valid && !(dot >= 0x1p-100f)) {
-                        double s = 0.0;
-#pragma unroll
-                        for (int k = 0; k < VRP; ++k) s = fma((double)rows[j][k], (double)uu[k], s);
-                        tau = s > 0.0 ? (float)((double)cv[j] / s) : 0.f;
-                        atomicOr(status, s > 0.0 ? ST_GUARD : ST_NUMERIC);
-                    }
-#pragma unroll
-                    for (int k = 0; k < VRP; ++k) acc[k] = fmaf(tau, rows[j][k], acc[k]);
-                }
-                for (int x = 0; x < extra; ++x) {
-                    const int idx = p + G * (NPL + x);
-                    const bool valid = idx < len;
-                    int2 e = make_int2(0, 0);
-                    if (valid) e = __ldg(a.nz + beg + idx);
-                    float kr[VRP];
-#pragma unroll
-                    for (int c = 0; c < C; ++c) {
-                        const float4 t = KIO<KT_t>::load4(KT, (long)e.x * C + c);
-                        kr[4 * c] = t.x; kr[4 * c + 1] = t.y; kr[4 * c + 2] = t.z; kr[4 * c + 3] = t.w;
-                    }
-                    double s = 0.0;
-#pragma unroll
-                    for (int k = 0; k < VRP; ++k) s = fma((double)kr[k], (double)uu[k], s);
-                    float tau = 0.f;
-                    if (valid) {
-                        tau = s > 0.0 ? (float)((double)__int_as_float(e.y) / s) : 0.f;
-                        if (!(s > 0.0)) atomicOr(status, ST_NUMERIC);
-                    }
-#pragma unroll
-                    for (int k = 0; k < VRP; ++k) acc[k] = fmaf(tau, kr[k], acc[k]);
-                }
-            }
-            // team reduction of acc through the per-warp transpose buffer
-#pragma unroll
-            for (int c = 0; c < C; ++c)
-                reinterpret_cast<float4 *>(wacc + lane * VRP)[c] =
-                    make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
-            __syncwarp();
-            bool bad = false;
-            for (int k = p; k < VRP; k += G) {
-                float s = 0.f;
-                for (int g = 0; g < G; ++g) s += wacc[(team * G + g) * VRP + k];
-                const float rk = (has && k < vr) ? __ldg(a.r + k) : 0.f;
-                const float nu = rk > 0.f ? __fdividef(rk, s) : 0.f;
-                bad |= !(nu < INFINITY);
-                wu[team * VRP + k] = nu;
-            }
-            __syncwarp();
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const float4 t = reinterpret_cast<const float4 *>(wu + team * VRP)[c];
-                uu[4 * c] = t.x; uu[4 * c + 1] = t.y; uu[4 * c + 2] = t.z; uu[4 * c + 3] = t.w;
-            }
-            if (bad) atomicOr(status, ST_NUMERIC);
-        }
-
-        // final step: s = K^T[w].u and m = KM^T[w].u per nonzero, WMD = sum c m / s
-        double dist = 0.0;
+        for (int k = 0; k < VRP; ++k) acc[k] = 0.f;
+        bool tiny_any = false;
 #pragma unroll
         for (int j = 0; j < NPL; ++j) {
             float d4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -232,69 +115,231 @@ __global__ void __launch_bounds__(kRegThreads) k_resident_regs(ResidentArgs ra, 
             for (int k = 0; k < VRP; ++k) d4[k & 3] = fmaf(rows[j][k], uu[k], d4[k & 3]);
             const float dot = (d4[0] + d4[1]) + (d4[2] + d4[3]);
             const bool valid = cv[j] > 0.f;
-            float m4[4] = {0.f, 0.f, 0.f, 0.f};
+            tiny_any |= valid && !(dot >= 0x1p-100f);
+            const float tau = valid ? __fdividef(cv[j], dot) : 0.f;
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const float4 t = valid ? KIO<KT_t>::load4(KMT, (long)wid[j] * C + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-                m4[0] = fmaf(t.x, uu[4 * c], m4[0]);
-                m4[1] = fmaf(t.y, uu[4 * c + 1], m4[1]);
-                m4[2] = fmaf(t.z, uu[4 * c + 2], m4[2]);
-                m4[3] = fmaf(t.w, uu[4 * c + 3], m4[3]);
-            }
-            const float dm = (m4[0] + m4[1]) + (m4[2] + m4[3]);
-            if (valid) {
-                if (dot >= 0x1p-100f) {
-                    dist += (double)(cv[j] * (dm / dot));
-                } else {
-                    SWMD_COLD_PATH();
-                    double s = 0.0, m = 0.0;
-#pragma unroll
-                    for (int k = 0; k < VRP; ++k) s = fma((double)rows[j][k], (double)uu[k], s);
-                    for (int c = 0; c < C; ++c) {
-                        const float4 t = KIO<KT_t>::load4(KMT, (long)wid[j] * C + c);
-                        m = fma((double)t.x, (double)uu[4 * c], m);
-                        m = fma((double)t.y, (double)uu[4 * c + 1], m);
-                        m = fma((double)t.z, (double)uu[4 * c + 2], m);
-                        m = fma((double)t.w, (double)uu[4 * c + 3], m);
-                    }
-                    dist += (double)cv[j] * (m / s);
-                    atomicOr(status, s > 0.0 ? ST_GUARD : ST_NUMERIC);
-                }
-            }
+            for (int k = 0; k < VRP; ++k) acc[k] = fmaf(tau, rows[j][k], acc[k]);
         }
         for (int x = 0; x < extra; ++x) {
             const int idx = p + G * (NPL + x);
+            const int o = idx - 32 * NPL;
             const bool valid = idx < len;
-            int2 e = make_int2(0, 0);
-            if (valid) e = __ldg(a.nz + beg + idx);
-            float d4[4] = {0.f, 0.f, 0.f, 0.f}, m4[4] = {0.f, 0.f, 0.f, 0.f};
+            float kr[VRP];
+            float cval;
+            if (o < n_ovf) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const float4 v = reinterpret_cast<const float4 *>(wrow + (size_t)o * VRP)[c];
+                    kr[4 * c] = v.x; kr[4 * c + 1] = v.y; kr[4 * c + 2] = v.z; kr[4 * c + 3] = v.w;
+                }
+                cval = wc[o];
+            } else {
+                int2 e = make_int2(0, 0);
+                if (valid) e = __ldg(a.nz + beg + idx);
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const float4 v = KIO<KT_t>::load4(KT, (long)e.x * C + c);
+                    kr[4 * c] = v.x; kr[4 * c + 1] = v.y; kr[4 * c + 2] = v.z; kr[4 * c + 3] = v.w;
+                }
+                cval = __int_as_float(e.y);
+            }
+            float d4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < VRP; ++k) d4[k & 3] = fmaf(kr[k], uu[k], d4[k & 3]);
+            const float dot = (d4[0] + d4[1]) + (d4[2] + d4[3]);
+            tiny_any |= valid && !(dot >= 0x1p-100f);
+            const float tau = valid ? __fdividef(cval, dot) : 0.f;
+#pragma unroll
+            for (int k = 0; k < VRP; ++k) acc[k] = fmaf(tau, kr[k], acc[k]);
+        }
+        if (__any_sync(kFull, tiny_any)) {
+            SWMD_COLD_PATH();
+            // some K^T u fell below 2^-100: redo this lane's accumulation with the
+            // affected denominators in FP64 (rows held in registers; an overflow
+            // row always comes with a full-warp team and is re-derived the same way)
+#pragma unroll
+            for (int k = 0; k < VRP; ++k) acc[k] = 0.f;
+#pragma unroll
+            for (int j = 0; j < NPL; ++j) {
+                float d4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int k = 0; k < VRP; ++k) d4[k & 3] = fmaf(rows[j][k], uu[k], d4[k & 3]);
+                const float dot = (d4[0] + d4[1]) + (d4[2] + d4[3]);
+                const bool valid = cv[j] > 0.f;
+                float tau = valid ? __fdividef(cv[j], dot) : 0.f;
+                if (valid && !(dot >= 0x1p-100f)) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int k = 0; k < VRP; ++k) s = fma((double)rows[j][k], (double)uu[k], s);
+                    tau = s > 0.0 ? (float)((double)cv[j] / s) : 0.f;
+                    atomicOr(status, s > 0.0 ? ST_GUARD : ST_NUMERIC);
+                }
+#pragma unroll
+                for (int k = 0; k < VRP; ++k) acc[k] = fmaf(tau, rows[j][k], acc[k]);
+            }
+            for (int x = 0; x < extra; ++x) {
+                const int idx = p + G * (NPL + x);
+                const bool valid = idx < len;
+                int2 e = make_int2(0, 0);
+                if (valid) e = __ldg(a.nz + beg + idx);
+                float kr[VRP];
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const float4 v = KIO<KT_t>::load4(KT, (long)e.x * C + c);
+                    kr[4 * c] = v.x; kr[4 * c + 1] = v.y; kr[4 * c + 2] = v.z; kr[4 * c + 3] = v.w;
+                }
+                double s = 0.0;
+#pragma unroll
+                for (int k = 0; k < VRP; ++k) s = fma((double)kr[k], (double)uu[k], s);
+                float tau = 0.f;
+                if (valid) {
+                    tau = s > 0.0 ? (float)((double)__int_as_float(e.y) / s) : 0.f;
+                    if (!(s > 0.0)) atomicOr(status, ST_NUMERIC);
+                }
+#pragma unroll
+                for (int k = 0; k < VRP; ++k) acc[k] = fmaf(tau, kr[k], acc[k]);
+            }
+        }
+        bool bad = false;
+        if constexpr (G == 1) {
+#pragma unroll
+            for (int k = 0; k < VRP; ++k) {
+                const float nu = rk[k] > 0.f ? __fdividef(rk[k], acc[k]) : 0.f;
+                bad |= !(nu < INFINITY);
+                uu[k] = nu;
+            }
+        } else {
+            // team reduction of acc: store the partials, finish entries k = p + G i,
+            // publish them in place of the first partial row, read the new u back
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+                reinterpret_cast<float4 *>(tacc + p * VRP)[c] =
+                    make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
+            __syncwarp();
+            float nu[KS];
+#pragma unroll
+            for (int i = 0; i < KS; ++i) {
+                const int k = p + G * i;
+                float s = 0.f;
+                if (k < VRP) {
+#pragma unroll
+                    for (int g = 0; g < G; ++g) s += tacc[g * VRP + k];
+                }
+                nu[i] = rk[i] > 0.f ? __fdividef(rk[i], s) : 0.f;
+                bad |= !(nu[i] < INFINITY);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < KS; ++i) {
+                const int k = p + G * i;
+                if (k < VRP) tacc[k] = nu[i];
+            }
+            __syncwarp();
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                const float4 t = KIO<KT_t>::load4(KT, (long)e.x * C + c);
-                const float4 m = KIO<KT_t>::load4(KMT, (long)e.x * C + c);
-                d4[0] = fmaf(t.x, uu[4 * c], d4[0]); d4[1] = fmaf(t.y, uu[4 * c + 1], d4[1]);
-                d4[2] = fmaf(t.z, uu[4 * c + 2], d4[2]); d4[3] = fmaf(t.w, uu[4 * c + 3], d4[3]);
-                m4[0] = fmaf(m.x, uu[4 * c], m4[0]); m4[1] = fmaf(m.y, uu[4 * c + 1], m4[1]);
-                m4[2] = fmaf(m.z, uu[4 * c + 2], m4[2]); m4[3] = fmaf(m.w, uu[4 * c + 3], m4[3]);
+                const float4 v = reinterpret_cast<const float4 *>(tacc)[c];
+                uu[4 * c] = v.x; uu[4 * c + 1] = v.y; uu[4 * c + 2] = v.z; uu[4 * c + 3] = v.w;
             }
-            const float dot = (d4[0] + d4[1]) + (d4[2] + d4[3]);
-            const float dm = (m4[0] + m4[1]) + (m4[2] + m4[3]);
-            if (valid) {
-                if (dot >= 0x1p-100f) {
-                    dist += (double)(__int_as_float(e.y) * (dm / dot));
-                } else {
-                    SWMD_COLD_PATH();
-                    atomicOr(status, ST_NUMERIC);
-                    dist += (double)(__int_as_float(e.y) * (dm / dot));
+            __syncwarp();
+        }
+        if (bad) atomicOr(status, ST_NUMERIC);
+    }
+
+    // final step: s = K^T[w].u and m = KM^T[w].u per nonzero, WMD = sum c m / s
+    double dist = 0.0;
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) {
+        float d4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < VRP; ++k) d4[k & 3] = fmaf(rows[j][k], uu[k], d4[k & 3]);
+        const float dot = (d4[0] + d4[1]) + (d4[2] + d4[3]);
+        const bool valid = cv[j] > 0.f;
+        float m4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const float4 v = valid ? KIO<KT_t>::load4(KMT, (long)wid[j] * C + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            m4[0] = fmaf(v.x, uu[4 * c], m4[0]);
+            m4[1] = fmaf(v.y, uu[4 * c + 1], m4[1]);
+            m4[2] = fmaf(v.z, uu[4 * c + 2], m4[2]);
+            m4[3] = fmaf(v.w, uu[4 * c + 3], m4[3]);
+        }
+        const float dm = (m4[0] + m4[1]) + (m4[2] + m4[3]);
+        if (valid) {
+            if (dot >= 0x1p-100f) {
+                dist += (double)(cv[j] * (dm / dot));
+            } else {
+                SWMD_COLD_PATH();
+                double s = 0.0, m = 0.0;
+#pragma unroll
+                for (int k = 0; k < VRP; ++k) s = fma((double)rows[j][k], (double)uu[k], s);
+                for (int c = 0; c < C; ++c) {
+                    const float4 v = KIO<KT_t>::load4(KMT, (long)wid[j] * C + c);
+                    m = fma((double)v.x, (double)uu[4 * c], m);
+                    m = fma((double)v.y, (double)uu[4 * c + 1], m);
+                    m = fma((double)v.z, (double)uu[4 * c + 2], m);
+                    m = fma((double)v.w, (double)uu[4 * c + 3], m);
                 }
+                dist += (double)cv[j] * (m / s);
+                atomicOr(status, s > 0.0 ? ST_GUARD : ST_NUMERIC);
             }
         }
-        for (int o = 1; o < G; o <<= 1) dist += __shfl_xor_sync(kFull, dist, o);
-        if (has && p == 0) {
-            if (!(fabs(dist) < INFINITY)) atomicOr(status, ST_NUMERIC);
-            out[__ldg(a.doc_orig + doc)] = dist;
+    }
+    for (int x = 0; x < extra; ++x) {
+        const int idx = p + G * (NPL + x);
+        const bool valid = idx < len;
+        int2 e = make_int2(0, 0);
+        if (valid) e = __ldg(a.nz + beg + idx);
+        float d4[4] = {0.f, 0.f, 0.f, 0.f}, m4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const float4 v = KIO<KT_t>::load4(KT, (long)e.x * C + c);
+            const float4 m = KIO<KT_t>::load4(KMT, (long)e.x * C + c);
+            d4[0] = fmaf(v.x, uu[4 * c], d4[0]); d4[1] = fmaf(v.y, uu[4 * c + 1], d4[1]);
+            d4[2] = fmaf(v.z, uu[4 * c + 2], d4[2]); d4[3] = fmaf(v.w, uu[4 * c + 3], d4[3]);
+            m4[0] = fmaf(m.x, uu[4 * c], m4[0]); m4[1] = fmaf(m.y, uu[4 * c + 1], m4[1]);
+            m4[2] = fmaf(m.z, uu[4 * c + 2], m4[2]); m4[3] = fmaf(m.w, uu[4 * c + 3], m4[3]);
         }
-        __syncwarp();   // the next task reuses the warp's shared buffers
+        const float dot = (d4[0] + d4[1]) + (d4[2] + d4[3]);
+        const float dm = (m4[0] + m4[1]) + (m4[2] + m4[3]);
+        if (valid) {
+            if (!(dot >= 0x1p-100f)) atomicOr(status, ST_NUMERIC);
+            dist += (double)(__int_as_float(e.y) * (dm / dot));
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) dist += __shfl_xor_sync(kFull, dist, o);
+    if (has && p == 0) {
+        if (!(fabs(dist) < INFINITY)) atomicOr(status, ST_NUMERIC);
+        out[__ldg(a.doc_orig + doc)] = dist;
+    }
+    __syncwarp();   // the next task reuses the warp's shared buffers
+}
+
+template <int VRP, int NPL, class KT_t>
+__global__ void __launch_bounds__(kRegThreads) k_resident_regs(ResidentArgs ra, const int4 *tasks,
+                                                               int n_tasks, int ovf_cap) {
+    const IterArgs &a = ra.it;
+    // per warp: the transpose buffer (32 partial rows of VRP plus team padding)
+    constexpr int WACC = 32 * VRP + 32 * 32;
+    __shared__ __align__(16) float s_acc[kWarps][WACC];
+    extern __shared__ __align__(16) float s_ovf[];   // per warp: overflow rows, then their counts
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    float *wacc = s_acc[warp];
+    float *wrow = s_ovf + (size_t)warp * ovf_cap * (VRP + 1);
+    float *wc = wrow + (size_t)ovf_cap * VRP;
+    const long gwarp = ((long)blockIdx.x * kRegThreads + threadIdx.x) >> 5;
+    const long nwarps = ((long)gridDim.x * kRegThreads) >> 5;
+    for (long task = gwarp; task < n_tasks; task += nwarps) {
+        const int4 tk = __ldg(tasks + task);   // first document, team size, documents
+        switch (tk.y) {
+            case 1: regs_task<VRP, NPL, 1, KT_t>(a, ra.t, tk, lane, wacc, wrow, wc, ovf_cap); break;
+            case 2: regs_task<VRP, NPL, 2, KT_t>(a, ra.t, tk, lane, wacc, wrow, wc, ovf_cap); break;
+            case 4: regs_task<VRP, NPL, 4, KT_t>(a, ra.t, tk, lane, wacc, wrow, wc, ovf_cap); break;
+            case 8: regs_task<VRP, NPL, 8, KT_t>(a, ra.t, tk, lane, wacc, wrow, wc, ovf_cap); break;
+            case 16: regs_task<VRP, NPL, 16, KT_t>(a, ra.t, tk, lane, wacc, wrow, wc, ovf_cap); break;
+            default: regs_task<VRP, NPL, 32, KT_t>(a, ra.t, tk, lane, wacc, wrow, wc, ovf_cap); break;
+        }
     }
 }
 
@@ -311,15 +356,17 @@ cudaError_t run_regs(const ResidentArgs &a, const TaskSet &ts, int sms, cudaStre
     static size_t configured = 0;
     static int per_sm = 0;
     static size_t per_sm_smem = (size_t)-1;
-    if (smem > 48 * 1024 - sizeof(float) * 2 * kWarps * 32 * VRP && configured < smem) {
+    if (configured < smem) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = smem;
     }
     if (per_sm <= 0 || per_sm_smem != smem) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRegThreads, smem) != cudaSuccess ||
-            per_sm < 1)
+            per_sm < 1) {
+            (void)cudaGetLastError();
             per_sm = 1;
+        }
         per_sm_smem = smem;
     }
     long blocks = ((long)ts.n_tasks + kWarps - 1) / kWarps;

@@ -300,7 +300,7 @@ cudaError_t run_tiled(const ResidentArgs &a, const TileSet &ts, int sms, cudaStr
     if (per_sm <= 0 || per_sm_key != key) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ts.threads, smem) != cudaSuccess ||
             per_sm < 1)
-            per_sm = 1;
+            { (void)cudaGetLastError(); per_sm = 1; }
         per_sm_key = key;
     }
     int blocks = sms * per_sm;

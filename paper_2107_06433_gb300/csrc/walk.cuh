@@ -394,8 +394,10 @@ int walk_blocks(K kernel, int &per_sm_cache, long N, int G, int sms) {
     if (per_sm_cache <= 0) {
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWalkThreads, 0) !=
-                cudaSuccess || per_sm < 1)
+                cudaSuccess || per_sm < 1) {
+            (void)cudaGetLastError();
             per_sm = 1;
+        }
         per_sm_cache = per_sm;
     }
     const long need = (N * G + kWalkThreads - 1) / kWalkThreads;
