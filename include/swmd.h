@@ -85,8 +85,9 @@ typedef struct swmd_options {
     int32_t lanes_per_nz;  /* per-iteration paths: 0 = autotuned, else lanes sharing one
                               nonzero's dot (power of 2) */
     int32_t tile_threads;  /* resident path: threads per block (64, 128 or 256; 0 = 128) */
-    int32_t nnz_per_lane;  /* resident path: target nonzeros per lane and pass; a document of
-                              n nonzeros gets about n / nnz_per_lane lanes (0 = 4) */
+    int32_t nnz_per_lane;  /* resident path: nonzeros (rows of K^T) per lane and pass; a
+                              document of n nonzeros gets about n / nnz_per_lane lanes
+                              (0 = chosen from the query size) */
     int32_t tile_nnz;      /* resident path: nonzeros staged per block (0 = as many as fit
                               in about 100 KB of shared memory) */
     int32_t cost_split;    /* cost kernel: threads sharing one word's embedding row
@@ -204,7 +205,9 @@ SWMD_API int swmd_query_noalloc(swmd_corpus *corpus, const int32_t *d_ids, const
 /* ------------------------------------------------------------------ the steps */
 /* The steps of swmd_query_device, one call each, for timing and testing; they
  * share the corpus's workspace and must be called in this order for one query.
- * All are asynchronous on `stream`.
+ * All are asynchronous on `stream`.  swmd_step_cost lays K^T out for the
+ * corpus's current path (swmd_get_mapping); the later steps of the same query
+ * walk that layout whatever their own path.
  *
  * a0 (device part) + a1, cost matrix and kernel (Algorithm 1 first line; Table I
  * "M = cdist(...)", "K = exp(-M*lamb)"; Section III-C "K.*M"): copies the
@@ -238,9 +241,11 @@ SWMD_API int swmd_step_final(swmd_corpus *corpus, int32_t v_r, int32_t t0, doubl
 SWMD_API int swmd_step_resident(swmd_corpus *corpus, int32_t v_r, int32_t max_iter,
                                 double *d_out, void *stream);
 
-/* The lane mapping the corpus uses for a query of v_r words on `path`:
- * out[0] = VRP (v_r padded), out[1] = lanes sharing one nonzero (Q), out[2] =
- * nonzeros in flight per document (P); a team of Q*P lanes owns a document. */
+/* The layout and lane mapping the corpus uses for a query of v_r words on `path`:
+ * out[0] = VRP (v_r padded: the row length of K^T, KM^T and u), out[1] = Q,
+ * out[2] = P.  P > 0: P sub-teams of Q lanes own a document, each sub-team one
+ * nonzero at a time.  P = 0: a team of Q = VRP / 4 lanes owns a document, each
+ * lane one float4 slice of every row (the per-iteration paths' default). */
 SWMD_API int swmd_get_mapping(swmd_corpus *corpus, int32_t v_r, int32_t path, int32_t *out3);
 
 /* Copies a workspace array to host memory for inspection (tests):

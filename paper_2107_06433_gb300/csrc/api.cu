@@ -107,30 +107,61 @@ void free_slot(Slot &s) {
     s = Slot{};
 }
 
-// Lane mapping of the walk for a query of vr words.  P (nonzeros in flight per
-// document) follows the mean document length; Q (lanes per nonzero) keeps the
-// per-lane slice S = VRP / Q at or below 32 registers.
-Mapping choose_mapping(swmd_corpus *c, int vr, int path) {
+static bool pow2_times4(int v) { return v >= 4 && v <= 128 && ((v / 4) & (v / 4 - 1)) == 0 && v % 4 == 0; }
+
+// Padding VRP of the K^T / KM^T / u layout for a query of vr words on `path`:
+// the per-iteration paths use 4 x a power of two (a team of VRP / 4 lanes, one
+// float4 slice each); the resident solvers keep the tight padding.
+int layout_vrp(swmd_corpus *c, int vr, int path) {
     const int tl = c->opt.team_lanes, lq = c->opt.lanes_per_nz;
     if (tl > 0 && lq > 0 && tl % lq == 0) {
         Mapping m{vrp_for(vr, lq), lq, tl / lq};
+        if (mapping_supported(m)) return m.vrp;
+    }
+    if (path == SWMD_PATH_FUSED || path == SWMD_PATH_PLAIN) {
+        int v = 4;
+        while (v < vr) v *= 2;
+        return v;
+    }
+    return vrp_for(vr, vr <= 32 ? 1 : (vr <= 64 ? 2 : 4));
+}
+
+// Kernel mapping for walking a layout of padding vrp: p = 0 selects the
+// lanes-over-k walk (VRP / 4 lanes per document); otherwise P sub-teams of Q lanes.
+Mapping walk_mapping(swmd_corpus *c, int vrp, int path) {
+    const int tl = c->opt.team_lanes, lq = c->opt.lanes_per_nz;
+    if (tl > 0 && lq > 0 && tl % lq == 0) {
+        Mapping m{vrp, lq, tl / lq};
         if (mapping_supported(m)) return m;
     }
-    auto key = std::make_tuple(vr, path, c->opt.k_precision);
-    auto it = c->tuned.find(key);
-    if (it != c->tuned.end()) return it->second;
-    int q = vr <= 32 ? 1 : (vr <= 64 ? 2 : 4);
-    int p = c->mean_len >= 24.0 ? 8 : 4;
-    Mapping m{vrp_for(vr, q), q, p};
-    if (!mapping_supported(m)) m.p = 4;
-    if (!mapping_supported(m)) {
-        // fall back to the smallest supported layout of this width
-        for (int qq = 1; qq <= 8; qq *= 2) {
-            Mapping t{vrp_for(vr, qq), qq, 4};
-            if (mapping_supported(t)) return t;
-        }
+    (void)path;
+    if (pow2_times4(vrp)) return Mapping{vrp, vrp / 4, 0};
+    const int p = c->mean_len >= 24.0 ? 8 : 4;
+    for (int q = 1; q <= 8; q *= 2) {
+        Mapping m{vrp, q, p};
+        if (mapping_supported(m)) return m;
+        m.p = 4;
+        if (mapping_supported(m)) return m;
     }
-    return m;
+    return Mapping{vrp, 1, 4};
+}
+
+Mapping choose_mapping(swmd_corpus *c, int vr, int path) {
+    return walk_mapping(c, layout_vrp(c, vr, path), path);
+}
+
+// per-iteration launches of one mapping (lanes-over-k walk when m.p == 0)
+static cudaError_t iter_fused(const IterArgs &ia, Mapping m, int kprec, int sms, cudaStream_t st) {
+    return m.p == 0 ? launch_fused2(ia, m.vrp, kprec, sms, st) : launch_fused(ia, m, kprec, sms, st);
+}
+static cudaError_t iter_sddmm(const IterArgs &ia, Mapping m, int kprec, int sms, cudaStream_t st) {
+    return m.p == 0 ? launch_sddmm2(ia, m.vrp, kprec, sms, st) : launch_sddmm(ia, m, kprec, sms, st);
+}
+static cudaError_t iter_spmm(const IterArgs &ia, Mapping m, int kprec, int sms, cudaStream_t st) {
+    return m.p == 0 ? launch_spmm2(ia, m.vrp, kprec, sms, st) : launch_spmm(ia, m, kprec, sms, st);
+}
+static cudaError_t iter_final(const IterArgs &ia, Mapping m, int kprec, int sms, cudaStream_t st) {
+    return m.p == 0 ? launch_final2(ia, m.vrp, kprec, sms, st) : launch_final(ia, m, kprec, sms, st);
 }
 
 int build_tiles(swmd_corpus *c) {
@@ -211,7 +242,7 @@ int build_tasks(swmd_corpus *c) {
 
 int run_resident(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kprec, cudaStream_t st) {
     const int solver = c->opt.solver;
-    const int npl = regs_rows_per_lane(m.vrp);
+    const int npl = regs_rows_per_lane(m.vrp, c->opt.nnz_per_lane);
     if (c->tasks_dev && npl > 0 && (solver == 0 || solver == 1)) {
         TaskSet ts{c->tasks_dev + c->task_off[npl], c->task_count[npl], npl,
                    c->Nl > 0 ? c->len_sorted[0] : 0};
@@ -278,15 +309,15 @@ static int launch_sequence(swmd_corpus *c, Slot &s, Mapping m, int t, int path, 
     for (int it = 0; it < t; ++it) {
         ia.first = it == 0;
         if (path == SWMD_PATH_PLAIN) {
-            SWMD_CK(launch_sddmm(ia, m, kprec, c->sms, st));
+            SWMD_CK(iter_sddmm(ia, m, kprec, c->sms, st));
             ia.first = 0;
-            SWMD_CK(launch_spmm(ia, m, kprec, c->sms, st));
+            SWMD_CK(iter_spmm(ia, m, kprec, c->sms, st));
         } else {
-            SWMD_CK(launch_fused(ia, m, kprec, c->sms, st));
+            SWMD_CK(iter_fused(ia, m, kprec, c->sms, st));
         }
     }
     ia.first = t == 0;
-    SWMD_CK(launch_final(ia, m, kprec, c->sms, st));
+    SWMD_CK(iter_final(ia, m, kprec, c->sms, st));
     return SWMD_OK;
 }
 
@@ -303,6 +334,8 @@ int enqueue_query(swmd_corpus *c, Slot &s, const int *d_ids, const float *d_r, i
         if (rc) return rc;
     }
     const Mapping m = choose_mapping(c, vr, path);
+    s.cur_vrp = m.vrp;
+    s.cur_vr = vr;
     SWMD_CK(launch_prep(s.qp, lambda, vr, c->V, d_ids, d_r, s.q_ids, s.r, s.vrp_cap, d_out,
                         d_status ? d_status : s.status, st));
     const int shift = c->opt.column_shift ? 1 : 0;
@@ -653,6 +686,12 @@ int swmd_query_device(swmd_corpus *c, const int32_t *d_ids, const float *d_r, in
 }
 
 // ---------------------------------------------------------------- the steps
+// VRP of the K^T layout the last swmd_step_cost / query wrote (v_r's default
+// layout for the corpus's path if none yet)
+static int slot_vrp(swmd_corpus *c, Slot &s, int v_r) {
+    return (s.cur_vrp > 0 && s.cur_vr == v_r) ? s.cur_vrp : layout_vrp(c, v_r, c->opt.path);
+}
+
 static IterArgs iter_args(swmd_corpus *c, Slot &s) {
     IterArgs ia{};
     ia.doc_ptr = c->doc_ptr;
@@ -685,6 +724,8 @@ int swmd_step_cost(swmd_corpus *c, const int32_t *d_ids, const float *d_r, int32
             return rc;
     }
     const Mapping m = choose_mapping(c, v_r, c->opt.path);
+    s.cur_vrp = m.vrp;
+    s.cur_vr = v_r;
     SWMD_CK(launch_prep(s.qp, lambda, v_r, c->V, d_ids, d_r, s.q_ids, s.r, s.vrp_cap, s.out,
                         d_status ? d_status : s.status, st));
     CostArgs ca{};
@@ -720,16 +761,16 @@ int swmd_step_iterate(swmd_corpus *c, int32_t v_r, int32_t n_iter, int32_t first
         for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
         c->graphs.clear();
     }
-    const Mapping m = choose_mapping(c, v_r, path);
+    const Mapping m = walk_mapping(c, slot_vrp(c, s, v_r), path);
     IterArgs ia = iter_args(c, s);
     for (int it = 0; it < n_iter; ++it) {
         ia.first = (first && it == 0) ? 1 : 0;
         if (path == SWMD_PATH_PLAIN) {
-            SWMD_CK(launch_sddmm(ia, m, c->opt.k_precision, c->sms, st));
+            SWMD_CK(iter_sddmm(ia, m, c->opt.k_precision, c->sms, st));
             ia.first = 0;
-            SWMD_CK(launch_spmm(ia, m, c->opt.k_precision, c->sms, st));
+            SWMD_CK(iter_spmm(ia, m, c->opt.k_precision, c->sms, st));
         } else {
-            SWMD_CK(launch_fused(ia, m, c->opt.k_precision, c->sms, st));
+            SWMD_CK(iter_fused(ia, m, c->opt.k_precision, c->sms, st));
         }
     }
     return SWMD_OK;
@@ -743,11 +784,11 @@ int swmd_step_final(swmd_corpus *c, int32_t v_r, int32_t t0, double *d_out, void
     DeviceGuard guard(c->device);
     cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
     Slot &s = c->main;
-    const Mapping m = choose_mapping(c, v_r, c->opt.path);
+    const Mapping m = walk_mapping(c, slot_vrp(c, s, v_r), c->opt.path);
     IterArgs ia = iter_args(c, s);
     ia.first = t0 ? 1 : 0;
     ia.out = d_out;
-    SWMD_CK(launch_final(ia, m, c->opt.k_precision, c->sms, st));
+    SWMD_CK(iter_final(ia, m, c->opt.k_precision, c->sms, st));
     return SWMD_OK;
 }
 
@@ -760,7 +801,8 @@ int swmd_step_resident(swmd_corpus *c, int32_t v_r, int32_t max_iter, double *d_
     DeviceGuard guard(c->device);
     cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
     Slot &s = c->main;
-    const Mapping m = choose_mapping(c, v_r, SWMD_PATH_RESIDENT);
+    const int vrp = slot_vrp(c, s, v_r);
+    const Mapping m = walk_mapping(c, vrp, SWMD_PATH_RESIDENT);
     ResidentArgs ra{iter_args(c, s), max_iter};
     ra.it.out = d_out;
     return run_resident(c, ra, m, c->opt.k_precision, st);
@@ -789,8 +831,7 @@ int swmd_debug_read(swmd_corpus *c, int32_t what, int32_t v_r, void *h_dst) {
         return SWMD_OK;
     }
     if (v_r < 1 || v_r > c->opt.max_vr) return set_error(SWMD_EINVAL, "swmd_debug_read: bad v_r");
-    const Mapping m = choose_mapping(c, v_r, c->opt.path);
-    const int vrp = m.vrp;
+    const int vrp = slot_vrp(c, s, v_r);
     float *dst = static_cast<float *>(h_dst);
     if (what == 0 || what == 1) {
         const size_t kb = kprec_bytes(s.kprec);

@@ -98,6 +98,11 @@ cudaError_t launch_spmm(const IterArgs &a, Mapping m, int kprec, int sms, cudaSt
 cudaError_t launch_final(const IterArgs &a, Mapping m, int kprec, int sms, cudaStream_t s);
 cudaError_t launch_resident(const ResidentArgs &a, Mapping m, int kprec, int sms,
                             cudaStream_t s);
+// Lanes-over-k walks (a team of VRP / 4 lanes per document; VRP in {4, 8, 16, 32, 64, 128}).
+cudaError_t launch_fused2(const IterArgs &a, int vrp, int kprec, int sms, cudaStream_t s);
+cudaError_t launch_sddmm2(const IterArgs &a, int vrp, int kprec, int sms, cudaStream_t s);
+cudaError_t launch_spmm2(const IterArgs &a, int vrp, int kprec, int sms, cudaStream_t s);
+cudaError_t launch_final2(const IterArgs &a, int vrp, int kprec, int sms, cudaStream_t s);
 // Documents packed into tiles of at most `nt` nonzeros (at most 64 documents,
 // consecutive in the internal order): tiles[0..n_tiles] are document offsets.
 struct TileSet {
@@ -132,7 +137,7 @@ struct TaskSet {
     int npl;
     int max_len;   // longest document (sizes the per-warp overflow buffer)
 };
-int regs_rows_per_lane(int vrp);
+int regs_rows_per_lane(int vrp, int want);
 cudaError_t launch_resident_regs(const ResidentArgs &a, int vrp, int kprec, const TaskSet &ts,
                                  int sms, cudaStream_t s);
 size_t tiled_smem_bytes(int vrp, int kbytes, int nt);

@@ -48,6 +48,8 @@ struct Slot {
     float *r_in = nullptr;
     int64_t bytes = 0;
     bool external = false;   // buffers managed by a server (never reallocated here)
+    int cur_vrp = 0;         // padding of the K^T layout the last query / cost step wrote
+    int cur_vr = 0;          // ... and the query size it was written for
 };
 
 // Key of a captured launch sequence: everything baked into the launches.
@@ -100,6 +102,8 @@ namespace swmd {
 int alloc_slot(swmd_corpus *c, Slot &s, int max_vr, int kprec, bool with_v);
 void free_slot(Slot &s);
 Mapping choose_mapping(swmd_corpus *c, int vr, int path);
+int layout_vrp(swmd_corpus *c, int vr, int path);
+Mapping walk_mapping(swmd_corpus *c, int vrp, int path);
 // Enqueues a whole query whose ids / r are already in device memory (d_ids,
 // d_r), writing the distances to d_out and the status to d_status.
 int enqueue_query(swmd_corpus *c, Slot &s, const int *d_ids, const float *d_r, int vr,

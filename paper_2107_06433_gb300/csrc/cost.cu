@@ -190,12 +190,13 @@ __global__ void __launch_bounds__(kCostThreads) k_cost_rows(CostArgs a) {
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const unsigned long long e2 = pack2(ev[e], ev[e]);
-                        const float4 *qrow = reinterpret_cast<const float4 *>(sQ + (4 * ch + e) * VRP);
+                        // query pairs read straight into 64-bit registers: no repacking
+                        const ulonglong2 *qrow = reinterpret_cast<const ulonglong2 *>(sQ + (4 * ch + e) * VRP);
 #pragma unroll
                         for (int c = 0; c < VRP / 4; ++c) {
-                            const float4 qv = qrow[c];
-                            acc[2 * c] = sqdiff_acc2(pack2(qv.x, qv.y), e2, acc[2 * c]);
-                            acc[2 * c + 1] = sqdiff_acc2(pack2(qv.z, qv.w), e2, acc[2 * c + 1]);
+                            const ulonglong2 qv = qrow[c];
+                            acc[2 * c] = sqdiff_acc2(qv.x, e2, acc[2 * c]);
+                            acc[2 * c + 1] = sqdiff_acc2(qv.y, e2, acc[2 * c + 1]);
                         }
                     }
                 }

@@ -390,11 +390,17 @@ cudaError_t dispatch_regs(const ResidentArgs &a, int vrp, const TaskSet &ts, int
 
 }  // namespace
 
-int regs_rows_per_lane(int vrp) {
-    if (vrp <= 8) return 8;
-    if (vrp <= 20) return 4;
-    if (vrp <= 32) return 2;
-    return 0;   // not supported: the shared-memory tiled solver takes over
+int regs_rows_per_lane(int vrp, int want) {
+    if (vrp > 32) return 0;   // not supported: the shared-memory tiled solver takes over
+    const int def = vrp <= 8 ? 8 : (vrp <= 20 ? 4 : 2);
+    if (want <= 0) return def;
+    // the (VRP, rows per lane) pairs compiled below
+    static const int ok[][2] = {{4, 8}, {8, 8}, {12, 4}, {16, 4}, {20, 4}, {24, 2}, {28, 2},
+                                {32, 2}, {12, 8}, {16, 2}, {20, 2}, {20, 3}, {24, 3}, {32, 1},
+                                {24, 4}};
+    for (auto &e : ok)
+        if (e[0] == vrp && e[1] == want) return want;
+    return def;
 }
 
 cudaError_t launch_resident_regs(const ResidentArgs &a, int vrp, int kprec, const TaskSet &ts,

@@ -1,5 +1,5 @@
 // a4: the final step of Algorithm 1 (SDDMM_SpMM type 2) and the distance.
-#include "walk.cuh"
+#include "walk2.cuh"
 
 namespace swmd {
 
@@ -29,6 +29,11 @@ int vrp_for(int vr, int q) {
     if (v > 32 && v % 8) v = (v + 7) / 8 * 8;
     if (v > 64 && v % 16) v = (v + 15) / 16 * 16;
     return v;
+}
+
+
+cudaError_t launch_final2(const IterArgs &a, int vrp, int kprec, int sms, cudaStream_t s) {
+    return dispatch_walk2_prec<Kind::Final>(a, vrp, kprec, sms, s);
 }
 
 }  // namespace swmd
