@@ -25,19 +25,18 @@ namespace {
 constexpr int kRegThreads = 128;
 constexpr int kWarps = kRegThreads / 32;
 
-// Floats per team in the per-warp transpose buffer: G rows of VRP plus padding
-// that shifts consecutive teams by G banks (conflict-free reads for G >= 4).
-template <int VRP, int G>
-__host__ __device__ constexpr int team_stride() {
-    return G * VRP + ((G >= 4) ? ((G - (G * VRP) % 32) % 32 + 32) % 32 : 0);
-}
+// Per-warp transpose buffer: lane l's partial row of acc starts at float 33 l
+// (a row stride of 33 = 1 mod 32 banks), so a team's rows sit at 33 * (lane of
+// its first member); storing one k across the warp, summing one column across a
+// team, publishing u and reading it back are all free of bank conflicts.
+constexpr int kRowStride = 33;
 
 template <int VRP, int NPL, int G, class KT_t>
 __device__ __forceinline__ void regs_task(const IterArgs &a, int t, int4 tk, int lane, float *wacc,
                                           float *wrow, float *wc, int ovf_cap) {
     constexpr int C = VRP / 4;
-    constexpr int TS = team_stride<VRP, G>();
     constexpr int KS = (VRP + G - 1) / G;   // entries of u each lane finishes
+    static_assert(VRP <= kRowStride, "row stride");
     const int vr = a.qp->vr;
     const float u0 = a.qp->u0;
     int *const status = a.qp->status;
@@ -55,7 +54,7 @@ __device__ __forceinline__ void regs_task(const IterArgs &a, int t, int4 tk, int
         beg = __ldg(a.doc_ptr + doc);
         len = __ldg(a.doc_ptr + doc + 1) - beg;
     }
-    float *tacc = wacc + team * TS;   // this team's G partial accumulators
+    float *tacc = wacc + team * G * kRowStride;   // this team's G partial accumulators
 
     // overflow rows (documents longer than G * NPL exist only with G = 32, one
     // document per warp): the first ovf_cap go to shared memory once
@@ -212,9 +211,7 @@ __device__ __forceinline__ void regs_task(const IterArgs &a, int t, int4 tk, int
             // team reduction of acc: store the partials, finish entries k = p + G i,
             // publish them in place of the first partial row, read the new u back
 #pragma unroll
-            for (int c = 0; c < C; ++c)
-                reinterpret_cast<float4 *>(tacc + p * VRP)[c] =
-                    make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
+            for (int k = 0; k < VRP; ++k) tacc[p * kRowStride + k] = acc[k];
             __syncwarp();
             float nu[KS];
 #pragma unroll
@@ -223,7 +220,7 @@ __device__ __forceinline__ void regs_task(const IterArgs &a, int t, int4 tk, int
                 float s = 0.f;
                 if (k < VRP) {
 #pragma unroll
-                    for (int g = 0; g < G; ++g) s += tacc[g * VRP + k];
+                    for (int g = 0; g < G; ++g) s += tacc[g * kRowStride + k];
                 }
                 nu[i] = rk[i] > 0.f ? __fdividef(rk[i], s) : 0.f;
                 bad |= !(nu[i] < INFINITY);
@@ -236,10 +233,7 @@ __device__ __forceinline__ void regs_task(const IterArgs &a, int t, int4 tk, int
             }
             __syncwarp();
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const float4 v = reinterpret_cast<const float4 *>(tacc)[c];
-                uu[4 * c] = v.x; uu[4 * c + 1] = v.y; uu[4 * c + 2] = v.z; uu[4 * c + 3] = v.w;
-            }
+            for (int k = 0; k < VRP; ++k) uu[k] = tacc[k];
             __syncwarp();
         }
         if (bad) atomicOr(status, ST_NUMERIC);
@@ -319,8 +313,8 @@ template <int VRP, int NPL, class KT_t>
 __global__ void __launch_bounds__(kRegThreads) k_resident_regs(ResidentArgs ra, const int4 *tasks,
                                                                int n_tasks, int ovf_cap) {
     const IterArgs &a = ra.it;
-    // per warp: the transpose buffer (32 partial rows of VRP plus team padding)
-    constexpr int WACC = 32 * VRP + 32 * 32;
+    // per warp: the transpose buffer (32 partial rows, stride kRowStride)
+    constexpr int WACC = 32 * kRowStride;
     __shared__ __align__(16) float s_acc[kWarps][WACC];
     extern __shared__ __align__(16) float s_ovf[];   // per warp: overflow rows, then their counts
     const int warp = threadIdx.x >> 5;
