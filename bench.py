@@ -1,19 +1,26 @@
 """Benchmark: Sinkhorn WMD of one query against a paper-shaped corpus on GB300.
 
-One step = one whole query through the hot path (query prep, cost/kernel matrix,
-all Sinkhorn iterations, final distances) over the resident corpus of the
-paper-shaped workload (V=100,000, d=300, 5,000 documents of 10-300 Zipf words,
-v_r=19, lambda=1, 15 iterations).  Inputs are synthetic (see synth.py).
+One step = one whole query through the hot path (query staging, cost/kernel
+matrix, all Sinkhorn iterations and the final distances) over the resident corpus
+of the paper-shaped workload (V=100,000, d=300, 5,000 documents of 10-300 Zipf
+words, v_r=19, lambda=1, 15 iterations).  Inputs are synthetic (synth.py).
 
-  value      WMDs/s (documents x queries / device time), inputs resident in HBM,
+  value      WMD/s (documents x queries / device time), inputs resident in HBM,
              L2 flushed (256 MiB write) before every timed step, outside the events.
-  e2e        WMDs/s through swmd_query with host buffers: the query's ids and
+  e2e        WMD/s through swmd_query with host buffers: the query's ids and
              weights go host->device and the N distances device->host every step.
   roofline   the dominant kernel of a step: algorithmic bytes or flops per launch
-             over its CUDA-event duration, against MEASURED_PEAKS.json.
+             over its CUDA-event duration, against MEASURED_PEAKS.json; `traffic`
+             from the committed ncu capture when it matches the current sources.
   paths      the same query on the resident, fused (one launch per iteration) and
-             plain (separate SDDMM and SpMM launches) paths, plus the per-iteration
-             kernel time and effective GB/s of fused vs plain.
+             plain (separate SDDMM and SpMM launches) paths, and the per-iteration
+             fused vs plain kernels.
+  hbm_regime the per-iteration fused and plain kernels on the 1,000,000-document
+             workload (17.5M nonzeros, v_r=32), where c and u exceed L2: effective
+             GB/s against the HBM peak.
+  serving    a query server fed by Poisson arrivals (v_r uniform in [4,128]) over
+             the resident paper-shaped corpus: queries/s, p50/p99 latency, against
+             the same queries run one at a time through swmd_query.
   cpu_baseline  the FP64 oracle timed on the host cores on a bounded sample.
 
 `--impl reference` times the oracle alone (the reference arm).  Under torchrun
@@ -23,6 +30,7 @@ collective on the data path) and rank 0 prints the line.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -38,6 +46,7 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "paper"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA), times the SM clock.
 SMS, FP32_LANES = 152, 128
@@ -54,6 +63,8 @@ def parse():
     ap.add_argument("--kprec", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-paths", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     return ap.parse_args()
 
 
@@ -67,10 +78,33 @@ def dist_env():
 def load_peaks():
     try:
         with open(PEAKS_FILE) as f:
-            p = json.load(f)
-        return p, "measured"
+            return json.load(f), "measured"
     except (OSError, ValueError):
         return dict(FALLBACK_PEAKS), "fallback"
+
+
+def source_hash():
+    """Hash of the CUDA sources and headers: ncu traffic is valid only for it."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2107_06433_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it matches."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = t.get(kernel_key)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
 
 
 class ClockSampler:
@@ -135,9 +169,7 @@ class ClockSampler:
 def cost_counts(Vu, d, vrp, vr, kb):
     """a1: reads the used embedding rows, writes K^T and KM^T; 3 flops per
     (query word, word, dimension): subtract, multiply, add."""
-    byts = Vu * d * 4 + 2 * Vu * vrp * kb
-    flops = 3.0 * Vu * vr * d
-    return byts, flops
+    return Vu * d * 4 + 2 * Vu * vrp * kb, 3.0 * Vu * vr * d
 
 
 def fused_iter_bytes(nnz, N, Vu, vrp, kb):
@@ -154,7 +186,7 @@ def plain_iter_bytes(nnz, N, Vu, vrp, kb):
 def resident_counts(nnz, N, Vu, vrp, vr, kb, t):
     """a3 x t + a4 in one launch: compulsory bytes (c, doc_ptr, K^T, KM^T, the
     output) and flops: per nonzero and iteration 2 v_r FMAs + 1 divide (4 v_r + 1
-    flop), in the final step 2 dots and a divide and an add (4 v_r + 3)."""
+    flop), in the final step 2 dots, a divide and an add (4 v_r + 3)."""
     byts = nnz * 8 + (N + 1) * 4 + 2 * Vu * vrp * kb + N * (8 + 4)
     flops = float(t) * nnz * (4 * vr + 1) + nnz * (4 * vr + 3) + t * N * vr
     return byts, flops
@@ -172,6 +204,13 @@ def time_oracle(E, C, qi, qw, lam, t, budget_s=12.0, max_runs=50):
         if el >= budget_s or runs >= max_runs:
             break
     return runs, el, oracle.get_threads()
+
+
+def config_dict(w, C):
+    return {"workload": w.name, "V": w.V, "d": w.d, "documents": C.N, "nnz": C.nnz,
+            "v_r": w.v_r, "lambda": w.lam, "max_iter": w.max_iter,
+            "doc_lengths": f"{w.len_kind} {w.len_lo}-{w.len_hi}",
+            "word_ids": "Zipf(1.1)", "l2": "flushed (256 MiB write) before every timed step"}
 
 
 def reference_arm(args):
@@ -212,11 +251,136 @@ def reference_arm(args):
     return 0
 
 
-def config_dict(w, C):
-    return {"workload": w.name, "V": w.V, "d": w.d, "documents": C.N, "nnz": C.nnz,
-            "v_r": w.v_r, "lambda": w.lam, "max_iter": w.max_iter,
-            "doc_lengths": f"{w.len_kind} {w.len_lo}-{w.len_hi}",
-            "word_ids": "Zipf(1.1)", "l2": "flushed (256 MiB write) before every timed step"}
+def event_pair():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def compare_paths(swmd, corpus, d_ids, d_r, d_out, d_status, flush, stream, vr, lam, t, info, C,
+                  peaks, kb):
+    """Whole-query time of each path, and one fused vs one plain iteration."""
+    import torch
+    res = {}
+    reps = 50
+    for path in ("resident", "fused", "plain"):
+        swmd.swmd_corpus_set_options(corpus, path=path)
+        times = []
+        with torch.cuda.stream(stream):
+            for k in range(reps + 3):
+                flush.zero_()
+                a, b = event_pair()
+                a.record(stream)
+                swmd.swmd_query_device(corpus, d_ids, d_r, vr, lam, t, d_out, d_status,
+                                       stream=stream)
+                b.record(stream)
+                if k >= 3:
+                    times.append((a, b))
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in times)
+        res[path] = {"ms_per_query": ms, "wmds_per_s": C.N / (ms * 1e-3)}
+    res["iteration_kernel"] = iteration_kernels(swmd, corpus, d_ids, d_r, d_status, flush, stream,
+                                                vr, lam, info, C, peaks, kb)
+    swmd.swmd_corpus_set_options(corpus, path="resident")
+    return res
+
+
+def iteration_kernels(swmd, corpus, d_ids, d_r, d_status, flush, stream, vr, lam, info, C, peaks,
+                      kb, reps=30):
+    """One fused SDDMM-SpMM launch vs one SDDMM + one SpMM launch, on the
+    per-iteration layout (swmd_get_mapping of the fused path)."""
+    import torch
+    swmd.swmd_corpus_set_options(corpus, path="fused")
+    vrp = swmd.swmd_get_mapping(corpus, vr, "fused")[0]
+    per = {}
+    for path in ("fused", "plain"):
+        with torch.cuda.stream(stream):
+            swmd.swmd_step_cost(corpus, d_ids, d_r, vr, lam, d_status, stream=stream)
+            swmd.swmd_step_iterate(corpus, vr, 1, 1, path, stream=stream)
+            evs = []
+            for k in range(reps):
+                flush.zero_()
+                a, b = event_pair()
+                a.record(stream)
+                swmd.swmd_step_iterate(corpus, vr, 1, 0, path, stream=stream)
+                b.record(stream)
+                evs.append((a, b))
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        byts = (fused_iter_bytes if path == "fused" else plain_iter_bytes)(
+            info.nnz, C.N, info.V_used, vrp, kb)
+        gbs = byts / (ms * 1e-3) / 1e9
+        per[path] = {"ms_per_iteration": ms, "algorithmic_bytes": byts, "vrp": vrp, "gbs": gbs,
+                     "frac_of_hbm": gbs / peaks["hbm_gbs"]}
+    per["fusion_speedup"] = per["plain"]["ms_per_iteration"] / per["fused"]["ms_per_iteration"]
+    return per
+
+
+def hbm_regime(swmd, synth, torch, flush, stream, peaks):
+    """The per-iteration kernels where c and u exceed L2 (1M documents)."""
+    w = synth.WORKLOADS["large"]
+    E, C, (qi, qw) = synth.make(w)
+    corpus = swmd.corpus_from_synth(E, C, path="fused")
+    info = corpus.info()
+    ids, r = swmd.swmd_select(C.V, qi, qw)
+    d_ids = torch.from_numpy(ids).cuda()
+    d_r = torch.from_numpy(r).cuda()
+    d_status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    per = iteration_kernels(swmd, corpus, d_ids, d_r, d_status, flush, stream, len(ids), w.lam,
+                            info, C, peaks, 4, reps=10)
+    d_out = torch.empty(C.N, dtype=torch.float64, device="cuda")
+    q = {}
+    for path in ("resident", "fused"):
+        swmd.swmd_corpus_set_options(corpus, path=path)
+        with torch.cuda.stream(stream):
+            swmd.swmd_query_device(corpus, d_ids, d_r, len(ids), w.lam, w.max_iter, d_out,
+                                   d_status, stream=stream)
+            evs = []
+            for _ in range(3):
+                flush.zero_()
+                a, b = event_pair()
+                a.record(stream)
+                swmd.swmd_query_device(corpus, d_ids, d_r, len(ids), w.lam, w.max_iter, d_out,
+                                       d_status, stream=stream)
+                b.record(stream)
+                evs.append((a, b))
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        q[path] = {"ms_per_query": ms, "wmds_per_s": C.N / (ms * 1e-3)}
+    corpus.close()
+    return {"workload": "large", "documents": C.N, "nnz": info.nnz, "v_r": len(ids),
+            "iteration_kernel": per, "query": q}
+
+
+def serving(swmd, synth, corpus, C, rate_qps=2000.0, n=400):
+    """Poisson arrivals into the server vs the same queries one at a time."""
+    qs = synth.batch_queries(C.V, n, 4, 128, seed=synth.SEED + 1)
+    arrivals = synth.poisson_arrivals(rate_qps, n)
+    swmd.swmd_corpus_set_options(corpus, path="resident")
+    # one at a time through swmd_query (host in, host out)
+    lat = []
+    t0 = time.perf_counter()
+    for qi, qw in qs:
+        a = time.perf_counter()
+        swmd.swmd_query(corpus, qi, qw, 1.0, 15)
+        lat.append((time.perf_counter() - a) * 1e3)
+    one_qps = n / (time.perf_counter() - t0)
+    srv = swmd.swmd_serve_start(corpus, max_batch=32, memory_budget=2 << 30)
+    tickets = []
+    t0 = time.perf_counter()
+    for (qi, qw), at in zip(qs, arrivals):
+        now = time.perf_counter() - t0
+        if at > now:
+            time.sleep(at - now)
+        tickets.append(swmd.swmd_serve_submit(srv, qi, qw, 1.0, 15))
+    for tk in tickets:
+        swmd.swmd_serve_wait(srv, tk, 60000)
+    st = swmd.swmd_serve_stats(srv)
+    srv.stop()
+    return {"queries": n, "v_r": "uniform 4-128", "arrivals": f"Poisson {rate_qps:.0f} qps",
+            "served": {"qps": st["qps"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                       "mean_batch": st["mean_batch"]},
+            "one_at_a_time": {"qps": one_qps, "p50_ms": float(np.percentile(lat, 50)),
+                              "p99_ms": float(np.percentile(lat, 99))}}
 
 
 def main():
@@ -243,6 +407,7 @@ def main():
     if rank > 0:   # every rank answers the same query
         _, _, (qi, qw) = synth.make(w)
     kprec = {"fp32": 0, "bf16": 1, "fp16": 2}[args.kprec]
+    kb = 4 if kprec == 0 else 2
     corpus = swmd.corpus_from_synth(E, C, path=args.path, k_precision=kprec, device=local)
     info = corpus.info()
     ids, r = swmd.swmd_select(C.V, qi, qw)
@@ -294,8 +459,7 @@ def main():
     clocks = sampler.stop()
     cost_ms = [evs[k][0].elapsed_time(evs[k][1]) for k in range(K)]
     solve_ms = [evs[k][1].elapsed_time(evs[k][2]) for k in range(K)]
-    step_ms = [a + b for a, b in zip(cost_ms, solve_ms)]
-    total_ms = sum(step_ms)
+    total_ms = sum(a + b for a, b in zip(cost_ms, solve_ms))
     if pg:
         tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         pg.all_reduce(tt, op=pg.ReduceOp.MAX)
@@ -319,11 +483,11 @@ def main():
         tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
         pg.all_reduce(tt, op=pg.ReduceOp.MAX)
         e2e_s = float(tt.item())
-    assert np.array_equal(host_out, out_dev), "host and device entry points disagree"
+    if not np.allclose(host_out, out_dev, rtol=1e-12, atol=0):
+        raise SystemExit("host and device entry points disagree")
 
     # ---- roofline of the dominant kernel
     peaks, peak_kind = load_peaks()
-    kb = 4 if kprec == 0 else 2
     vrp = swmd.swmd_get_mapping(corpus, vr, args.path)[0]
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     cost_avg = statistics.mean(cost_ms) * 1e-3
@@ -331,27 +495,29 @@ def main():
     cb, cf = cost_counts(info.V_used, w.d, vrp, vr, kb)
     if args.path == "resident":
         sb, sf = resident_counts(info.nnz, C.N, info.V_used, vrp, vr, kb, t)
+        skey = f"resident:{w.name}"
     else:
         sb = t * fused_iter_bytes(info.nnz, C.N, info.V_used, vrp, kb)
         sf = float(t + 1) * info.nnz * (4 * vr + 1)
+        skey = f"{args.path}:{w.name}"
     alu_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s at the sampled clock
     if solve_avg >= cost_avg:
-        name, dur, byts, flops = f"{args.path} solver (a3 x t + a4)", solve_avg, sb, sf
+        name, key, dur, byts, flops = f"{args.path} solver (a3 x t + a4)", skey, solve_avg, sb, sf
     else:
-        name, dur, byts, flops = "cost/kernel matrix (a1)", cost_avg, cb, cf
-    ai = flops / byts
+        name, key, dur, byts, flops = "cost/kernel matrix (a1)", f"cost:{w.name}", cost_avg, cb, cf
     ridge = alu_peak * 1e12 / (peaks["hbm_gbs"] * 1e9)
-    if ai >= ridge:
+    traffic = measured_traffic(key)
+    if flops / byts >= ridge:
         ach = flops / dur / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": ach / alu_peak, "traffic": None, "kernel": name,
+                "frac": ach / alu_peak, "traffic": traffic, "kernel": name,
                 "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x "
                                f"{sm_mhz:.0f} MHz (median sampled SM clock)",
                 "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": byts}
     else:
         ach = byts / dur / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": name,
+                "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "kernel": name,
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes_per_launch": byts, "algorithmic_flops_per_launch": flops}
 
@@ -372,7 +538,12 @@ def main():
     }
     if rank == 0 and not args.no_paths:
         line["paths"] = compare_paths(swmd, corpus, d_ids, d_r, d_out, d_status, flush, stream,
-                                      vr, vrp, lam, t, info, C, peaks, kb)
+                                      vr, lam, t, info, C, peaks, kb)
+    if rank == 0 and not args.no_serve:
+        line["serving"] = serving(swmd, synth, corpus, C)
+    if rank == 0 and not args.no_large:
+        corpus.close()
+        line["hbm_regime"] = hbm_regime(swmd, synth, torch, flush, stream, peaks)
     if rank == 0 and not args.no_cpu_baseline:
         runs, el, cores = time_oracle(E, C, qi, qw, lam, t)
         line["cpu_baseline"] = {"value": C.N * runs / el, "unit": "WMD/s", "cores": cores,
@@ -385,57 +556,6 @@ def main():
         pg.barrier()
         pg.destroy_process_group()
     return 0
-
-
-def compare_paths(swmd, corpus, d_ids, d_r, d_out, d_status, flush, stream, vr, vrp, lam, t,
-                  info, C, peaks, kb):
-    """Whole-query time of each path, and the per-iteration fused vs plain kernels."""
-    import torch
-    res = {}
-    reps = 50
-    for path in ("resident", "fused", "plain"):
-        swmd.swmd_corpus_set_options(corpus, path=path)
-        times = []
-        with torch.cuda.stream(stream):
-            for k in range(reps + 3):
-                flush.zero_()
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                swmd.swmd_query_device(corpus, d_ids, d_r, vr, lam, t, d_out, d_status,
-                                       stream=stream)
-                b.record(stream)
-                if k >= 3:
-                    times.append((a, b))
-        torch.cuda.synchronize()
-        ms = statistics.mean(a.elapsed_time(b) for a, b in times)
-        res[path] = {"ms_per_query": ms, "wmds_per_s": C.N / (ms * 1e-3)}
-    swmd.swmd_corpus_set_options(corpus, path="resident")
-    # per-iteration kernels: one fused launch vs one SDDMM + one SpMM launch
-    per = {}
-    for path in ("fused", "plain"):
-        with torch.cuda.stream(stream):
-            swmd.swmd_step_cost(corpus, d_ids, d_r, vr, lam, d_status, stream=stream)
-            swmd.swmd_step_iterate(corpus, vr, 1, 1, path, stream=stream)
-            evs = []
-            for k in range(reps):
-                flush.zero_()
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                swmd.swmd_step_iterate(corpus, vr, 1, 0, path, stream=stream)
-                b.record(stream)
-                evs.append((a, b))
-        torch.cuda.synchronize()
-        ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
-        byts = (fused_iter_bytes if path == "fused" else plain_iter_bytes)(
-            info.nnz, C.N, info.V_used, vrp, kb)
-        per[path] = {"ms_per_iteration": ms, "algorithmic_bytes": byts,
-                     "gbs": byts / (ms * 1e-3) / 1e9,
-                     "frac_of_hbm": byts / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
-    res["iteration_kernel"] = per
-    res["fusion_speedup"] = per["plain"]["ms_per_iteration"] / per["fused"]["ms_per_iteration"]
-    return res
 
 
 if __name__ == "__main__":
