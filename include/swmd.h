@@ -116,6 +116,19 @@ SWMD_API const char *swmd_last_error(void);
 SWMD_API int swmd_select(int32_t V, int32_t n, const int32_t *h_ids, const float *h_weights,
                 int32_t *h_out_ids, float *h_out_r, int32_t *out_vr);
 
+/* ------------------------------------------------------------------ multi-GPU */
+/* Document ranges for `parts` GPUs.  The columns of c are independent problems
+ * (Algorithm 1 never mixes them), so the corpus shards by contiguous document
+ * ranges with no exchange during a query; the ranges are balanced by nonzeros,
+ * the cross-GPU form of the equal-nnz split of Section III-D.
+ *   doc_nnz[N] (int64, host): nonzeros of each document (column counts of c).
+ *   out_bounds[parts+1] (int32, host): range g is [out_bounds[g], out_bounds[g+1]),
+ *   out_bounds[0] = 0, out_bounds[parts] = N, non-decreasing.
+ * Host-only (no CUDA call); SWMD_EINVAL for parts < 1 or a negative count.  Pass a
+ * range as swmd_options.doc_begin / doc_end when creating each GPU's corpus. */
+SWMD_API int swmd_partition_documents(int32_t N, const int64_t *doc_nnz, int32_t parts,
+                                      int32_t *out_bounds);
+
 /* ------------------------------------------------------------------ corpus */
 /* Section III-B1: c is a V x N sparse matrix passed as CSR, c[i, j] the
  * frequency of word i in target document j; vecs is the V x d embedding matrix.

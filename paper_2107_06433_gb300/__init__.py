@@ -84,6 +84,7 @@ _SIGS = {
     "swmd_step_final": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P, P]),
     "swmd_step_resident": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P, P]),
     "swmd_get_mapping": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P]),
+    "swmd_partition_documents": (ctypes.c_int, [ctypes.c_int32, P, ctypes.c_int32, P]),
     "swmd_query_noalloc": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.c_float, ctypes.c_int32,
                                           P, P, P]),
     "swmd_debug_read": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P]),
@@ -163,6 +164,15 @@ def swmd_select(V, ids, weights):
     _err(lib().swmd_select(V, n, pi, pw, out_ids.ctypes.data_as(P), out_r.ctypes.data_as(P),
                            ctypes.byref(vr)), "swmd_select")
     return out_ids[:vr.value].copy(), out_r[:vr.value].copy()
+
+
+def swmd_partition_documents(N, doc_nnz, parts):
+    """Contiguous document ranges for `parts` GPUs, balanced by nonzeros: int32[parts+1]."""
+    cnt, pc = _np(doc_nnz, np.int64)
+    out = np.empty(int(parts) + 1, np.int32)
+    _err(lib().swmd_partition_documents(int(N), pc, int(parts), out.ctypes.data_as(P)),
+         "swmd_partition_documents")
+    return out
 
 
 class Corpus:

@@ -427,6 +427,28 @@ int swmd_select(int32_t V, int32_t n, const int32_t *h_ids, const float *h_weigh
     return SWMD_OK;
 }
 
+int swmd_partition_documents(int32_t N, const int64_t *doc_nnz, int32_t parts,
+                             int32_t *out_bounds) {
+    if (N < 0 || parts < 1 || !out_bounds || (N > 0 && !doc_nnz))
+        return set_error(SWMD_EINVAL, "swmd_partition_documents: bad arguments");
+    std::vector<int64_t> pre((size_t)N + 1, 0);
+    for (int32_t j = 0; j < N; ++j) {
+        if (doc_nnz[j] < 0) return set_error(SWMD_EINVAL, "swmd_partition_documents: negative count");
+        pre[j + 1] = pre[j] + doc_nnz[j];
+    }
+    // boundary g: the first document whose prefix reaches g/parts of the nonzeros
+    out_bounds[0] = 0;
+    for (int32_t g = 1; g < parts; ++g) {
+        const long double target = (long double)pre[N] * g / parts;
+        int32_t j = (int32_t)(std::lower_bound(pre.begin(), pre.end(), (int64_t)(target + 0.5L)) - pre.begin());
+        if (j < out_bounds[g - 1]) j = out_bounds[g - 1];
+        if (j > N) j = N;
+        out_bounds[g] = j;
+    }
+    out_bounds[parts] = N;
+    return SWMD_OK;
+}
+
 int swmd_create_corpus(int32_t V, int32_t N, int64_t nnz, const int64_t *row_ptr,
                        const int32_t *doc_idx, const float *val, const float *emb, int32_t d,
                        const swmd_options *opt_in, swmd_corpus **out) {

@@ -15,6 +15,8 @@
 // columns k >= v_r are zero.  With column_shift, K[k,w] = exp(-lambda (M[k,w] -
 // min_k M[k,w])): a rescaling of column w of K that leaves every x-update and the
 // distance unchanged and keeps the largest entry of each column at 1.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace swmd {
@@ -40,6 +42,16 @@ __device__ __forceinline__ unsigned long long sqdiff_acc2(unsigned long long a,
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(a), "l"(e));
     asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(d) : "l"(t), "l"(c));
     return d;
+}
+
+// Column factor b_w of the stored K (an exact rescaling of column w, like the
+// shift): 1 except for FP16 storage, where b_w = 2^14 / max(1, max_k M[k,w]) lifts
+// the shifted column (largest entry 1) out of FP16's subnormal range while K b_w
+// and K.*M b_w stay below 2^14.
+template <class KT_t>
+__device__ __forceinline__ float storage_scale(float mmax) {
+    if constexpr (std::is_same<KT_t, __half>::value) return 16384.f / fmaxf(1.f, mmax);
+    return 1.f;
 }
 
 template <int KPT, int T, class KT_t>
@@ -102,14 +114,21 @@ __global__ void __launch_bounds__(kCostThreads) k_cost(CostArgs a) {
         m[2 * i] = sqrtf(x);
         m[2 * i + 1] = sqrtf(y);
     }
-    float mn = INFINITY;
+    float mn = INFINITY, mx = 0.f;
 #pragma unroll
     for (int kk = 0; kk < KPT; ++kk)
-        if (sub * KPT + kk < vr) mn = fminf(mn, m[kk]);
+        if (sub * KPT + kk < vr) {
+            mn = fminf(mn, m[kk]);
+            mx = fmaxf(mx, m[kk]);
+        }
 #pragma unroll
-    for (int o = 1; o < T; o <<= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    for (int o = 1; o < T; o <<= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
     if (!active) return;
     const float sh = (a.shift && mn < INFINITY) ? mn : 0.f;
+    const float bw = a.shift ? storage_scale<KT_t>(mx) : 1.f;
 
     KT_t *KT = reinterpret_cast<KT_t *>(a.KT);
     KT_t *KMT = reinterpret_cast<KT_t *>(a.KMT);
@@ -122,8 +141,8 @@ __global__ void __launch_bounds__(kCostThreads) k_cost(CostArgs a) {
             const int k = sub * KPT + 4 * c + j;
             const float mm = m[4 * c + j];
             const float kk = (k < vr) ? expf(-lam * (mm - sh)) : 0.f;
-            kv[j] = kk;
-            kmv[j] = kk * mm;
+            kv[j] = kk * bw;
+            kmv[j] = (kk * mm) * bw;
         }
         KIO<KT_t>::store4(KT, base4 + c, make_float4(kv[0], kv[1], kv[2], kv[3]));
         KIO<KT_t>::store4(KMT, base4 + c, make_float4(kmv[0], kmv[1], kmv[2], kmv[3]));
@@ -218,11 +237,15 @@ __global__ void __launch_bounds__(kCostThreads) k_cost_rows(CostArgs a) {
             m[2 * i + 1] = sqrtf(y);
         }
         if (!active) continue;
-        float mn = INFINITY;
+        float mn = INFINITY, mx = 0.f;
 #pragma unroll
         for (int k = 0; k < VRP; ++k)
-            if (k < vr) mn = fminf(mn, m[k]);
+            if (k < vr) {
+                mn = fminf(mn, m[k]);
+                mx = fmaxf(mx, m[k]);
+            }
         const float sh = (a.shift && mn < INFINITY) ? mn : 0.f;
+        const float bw = a.shift ? storage_scale<KT_t>(mx) : 1.f;
 #pragma unroll
         for (int c = 0; c < VRP / 4; ++c) {
             if (c % TS != t) continue;
@@ -231,8 +254,8 @@ __global__ void __launch_bounds__(kCostThreads) k_cost_rows(CostArgs a) {
             for (int j = 0; j < 4; ++j) {
                 const int k = 4 * c + j;
                 const float kk = (k < vr) ? expf(-lam * (m[k] - sh)) : 0.f;
-                kv[j] = kk;
-                kmv[j] = kk * m[k];
+                kv[j] = kk * bw;
+                kmv[j] = (kk * m[k]) * bw;
             }
             KIO<KT_t>::store4(KT, wi * (VRP / 4) + c, make_float4(kv[0], kv[1], kv[2], kv[3]));
             KIO<KT_t>::store4(KMT, wi * (VRP / 4) + c, make_float4(kmv[0], kmv[1], kmv[2], kmv[3]));
