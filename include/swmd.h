@@ -269,6 +269,28 @@ SWMD_API int swmd_get_mapping(swmd_corpus *corpus, int32_t v_r, int32_t path, in
  * h_dst must hold the stated number of elements.  Synchronous. */
 SWMD_API int swmd_debug_read(swmd_corpus *corpus, int32_t what, int32_t v_r, void *h_dst);
 
+/* ------------------------------------------------------------------ autotuning */
+typedef struct swmd_tune_result {
+    int32_t vrp;           /* layout tuned (VRP of the resident path for v_r) */
+    int32_t solver;        /* chosen resident solver (see swmd_options.solver) */
+    int32_t nnz_per_lane;  /* chosen rows of K^T per lane (register solver) */
+    int32_t cost_split;    /* chosen threads per word of the cost kernel */
+    float default_ms;      /* whole-query time with the settings before tuning */
+    float best_ms;         /* whole-query time with the chosen settings */
+    int32_t candidates;    /* configurations timed */
+    int32_t reserved;
+} swmd_tune_result;
+
+/* Times the resident-path kernels of this corpus for queries of v_r words over
+ * the candidate lane mappings (register solver rows per lane; shared-memory
+ * solver; threads per word of the cost kernel), each `reps` times (>= 1) with
+ * CUDA events on a query of v_r distinct words drawn from the corpus, and keeps
+ * the fastest for this layout: later queries with the same VRP and K precision
+ * use it unless swmd_options fixes the field.  Synchronous; allocates nothing
+ * beyond the corpus's workspace.  The paper has no counterpart (it tuned by hand
+ * for Xeon and PIUMA, Sections IV-V). */
+SWMD_API int swmd_autotune(swmd_corpus *corpus, int32_t v_r, int32_t reps, swmd_tune_result *out);
+
 /* ------------------------------------------------------------------ batch */
 /* Several queries at once (Section III-D notes that many source documents can
  * run together; the paper's multi-query experiment, Section V):

@@ -63,6 +63,13 @@ class swmd_serve_stats_t(ctypes.Structure):
                 ("batches", ctypes.c_int64)]
 
 
+class swmd_tune_result(ctypes.Structure):
+    _fields_ = [("vrp", ctypes.c_int32), ("solver", ctypes.c_int32),
+                ("nnz_per_lane", ctypes.c_int32), ("cost_split", ctypes.c_int32),
+                ("default_ms", ctypes.c_float), ("best_ms", ctypes.c_float),
+                ("candidates", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 _lib = None
 
 P = ctypes.c_void_p
@@ -89,6 +96,7 @@ _SIGS = {
                                           P, P, P]),
     "swmd_debug_read": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P]),
     "swmd_query_batch": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P, ctypes.c_int32, P]),
+    "swmd_autotune": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P]),
     "swmd_default_serve_config": (None, [P]),
     "swmd_serve_start": (ctypes.c_int, [P, P, P]),
     "swmd_serve_submit": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.c_float, ctypes.c_int32,
@@ -320,6 +328,15 @@ def swmd_query_batch(corpus: Corpus, queries, lambdas, max_iter: int) -> np.ndar
     _err(lib().swmd_query_batch(corpus.handle, n, q_ptr.ctypes.data_as(P), pids, pws, plam,
                                 int(max_iter), out.ctypes.data_as(P)), "swmd_query_batch")
     return out
+
+
+def swmd_autotune(corpus: Corpus, v_r: int, reps: int = 5) -> dict:
+    """Times the resident path's candidate mappings for queries of v_r words on this
+    corpus and keeps the fastest for that layout.  Returns the chosen settings."""
+    res = swmd_tune_result()
+    _err(lib().swmd_autotune(corpus.handle, int(v_r), int(reps), ctypes.byref(res)),
+         "swmd_autotune")
+    return {f: getattr(res, f) for f, _ in swmd_tune_result._fields_ if f != "reserved"}
 
 
 class Server:

@@ -77,7 +77,7 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     if force or todo or _stale(LIB, objs):
         tmp = LIB + ".%d.tmp" % os.getpid()
         cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fvisibility=hidden",
-               "-lpthread"]
+               "-lpthread", "-Xlinker", "--no-undefined"]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
             raise RuntimeError("link failed:\n" + p.stderr[-6000:])

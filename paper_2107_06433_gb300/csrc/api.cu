@@ -240,13 +240,24 @@ int build_tasks(swmd_corpus *c) {
     return SWMD_OK;
 }
 
-int run_resident(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kprec, cudaStream_t st) {
-    const int solver = c->opt.solver;
-    const int npl = regs_rows_per_lane(m.vrp, c->opt.nnz_per_lane);
+void resident_settings(swmd_corpus *c, int vrp, int kprec, int *solver, int *npl_want, int *split) {
+    int s = 0, n = 0, cs = 0;
+    auto it = c->tuned_resident.find(std::make_pair(vrp, kprec));
+    if (it != c->tuned_resident.end()) std::tie(s, n, cs) = it->second;
+    *solver = c->opt.solver ? c->opt.solver : s;
+    *npl_want = c->opt.nnz_per_lane ? c->opt.nnz_per_lane : n;
+    *split = c->opt.cost_split ? c->opt.cost_split : cs;
+}
+
+int run_resident_batch(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kprec, int nq,
+                       const ResidentArgs *d_batch, cudaStream_t st) {
+    int solver = 0, npl_want = 0, split = 0;
+    resident_settings(c, m.vrp, kprec, &solver, &npl_want, &split);
+    const int npl = regs_rows_per_lane(m.vrp, npl_want);
     if (c->tasks_dev && npl > 0 && (solver == 0 || solver == 1)) {
         TaskSet ts{c->tasks_dev + c->task_off[npl], c->task_count[npl], npl,
                    c->Nl > 0 ? c->len_sorted[0] : 0};
-        cudaError_t e = launch_resident_regs(ra, m.vrp, kprec, ts, c->sms, st);
+        cudaError_t e = launch_resident_regs(ra, m.vrp, kprec, ts, c->sms, st, nq, d_batch);
         if (e != cudaSuccess)
             return set_error(e == cudaErrorMemoryAllocation ? SWMD_ENOMEM : SWMD_ECUDA,
                              "register-resident solver (VRP %d, %d rows per lane, longest document %d): %s",
@@ -266,11 +277,17 @@ int run_resident(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kprec, c
         }
         TileSet ts{c->tiles_dev + c->tile_off[pick], c->tile_count[pick], kTileBudgets[pick],
                    c->tile_threads, c->tile_npl};
-        SWMD_CK(launch_resident_tiled(ra, m.vrp, kprec, ts, c->sms, st));
+        SWMD_CK(launch_resident_tiled(ra, m.vrp, kprec, ts, c->sms, st, nq, d_batch));
         return SWMD_OK;
     }
+    if (nq != 1 || d_batch)
+        return set_error(SWMD_EINVAL, "no batched resident solver for VRP %d with these options", m.vrp);
     SWMD_CK(launch_resident(ra, m, kprec, c->sms, st));
     return SWMD_OK;
+}
+
+int run_resident(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kprec, cudaStream_t st) {
+    return run_resident_batch(c, ra, m, kprec, 1, nullptr, st);
 }
 
 static int launch_sequence(swmd_corpus *c, Slot &s, Mapping m, int t, int path, int kprec,
@@ -284,7 +301,11 @@ static int launch_sequence(swmd_corpus *c, Slot &s, Mapping m, int t, int path, 
     ca.qp = s.qp;
     ca.V = c->V;
     ca.shift = shift;
-    ca.split = c->opt.cost_split;
+    {
+        int s_ = 0, n_ = 0, cs_ = 0;
+        resident_settings(c, m.vrp, kprec, &s_, &n_, &cs_);
+        ca.split = cs_;
+    }
     ca.KT = s.KT;
     ca.KMT = s.KMT;
     SWMD_CK(launch_cost(ca, m.vrp, kprec, st));
@@ -610,6 +631,7 @@ void swmd_destroy_corpus(swmd_corpus *c) {
         if (c->stream) cudaStreamSynchronize(c->stream);
         for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
         free_slot(c->main);
+        dev_free(c->batch_ws);
         dev_free(c->E);
         dev_free(c->used);
         dev_free(c->doc_ptr);
@@ -759,7 +781,11 @@ int swmd_step_cost(swmd_corpus *c, const int32_t *d_ids, const float *d_r, int32
     ca.qp = s.qp;
     ca.V = c->V;
     ca.shift = c->opt.column_shift ? 1 : 0;
-    ca.split = c->opt.cost_split;
+    {
+        int s_ = 0, n_ = 0, cs_ = 0;
+        resident_settings(c, m.vrp, c->opt.k_precision, &s_, &n_, &cs_);
+        ca.split = cs_;
+    }
     ca.KT = s.KT;
     ca.KMT = s.KMT;
     SWMD_CK(launch_cost(ca, m.vrp, c->opt.k_precision, st));

@@ -86,6 +86,24 @@ struct Mapping {
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_cost(const CostArgs &a, int vrp, int kprec, cudaStream_t s);
+// Batched forms: grid row y runs query y with d_batch[y] (device array); `shape`
+// supplies the fields shared by the batch (corpus arrays, sizes).
+cudaError_t launch_cost_batch(const CostArgs &shape, int vrp, int kprec, int nq,
+                              const CostArgs *d_batch, cudaStream_t s);
+struct PrepArgs {
+    QParams *qp;
+    const int *src_ids;
+    const float *src_r;
+    int *q_ids;
+    float *r;
+    double *out;
+    int *status;
+    float lambda;
+    int vr;
+    int vrp_cap;
+    int pad;
+};
+cudaError_t launch_prep_batch(const PrepArgs *d_args, int nq, int V, cudaStream_t s);
 // Writes the parameter block of a query and copies / validates its ids and
 // weights into the slot (zero padded to vrp_cap).  src_ids / src_r may be NULL
 // to leave that array as it is.
@@ -139,11 +157,13 @@ struct TaskSet {
 };
 int regs_rows_per_lane(int vrp, int want);
 cudaError_t launch_resident_regs(const ResidentArgs &a, int vrp, int kprec, const TaskSet &ts,
-                                 int sms, cudaStream_t s);
+                                 int sms, cudaStream_t s, int nq = 1,
+                                 const ResidentArgs *d_batch = nullptr);
 size_t tiled_smem_bytes(int vrp, int kbytes, int nt);
 bool tiled_supported(int vrp, int kprec);
 cudaError_t launch_resident_tiled(const ResidentArgs &a, int vrp, int kprec, const TileSet &ts,
-                                  int sms, cudaStream_t s);
+                                  int sms, cudaStream_t s, int nq = 1,
+                                  const ResidentArgs *d_batch = nullptr);
 bool mapping_supported(Mapping m);
 int vrp_for(int vr, int q);
 

@@ -90,10 +90,14 @@ struct swmd_corpus {
     int task_count[9] = {0};
 
     swmd::Slot main;               // workspace of the single-query path
+    void *batch_ws = nullptr;      // workspace of swmd_query_batch (grown on demand)
+    size_t batch_ws_bytes = 0;
     int64_t base_bytes = 0;
 
     std::map<swmd::GraphKey, cudaGraphExec_t> graphs;
     std::map<std::tuple<int, int, int>, swmd::Mapping> tuned;  // (vr bucket, path, kprec)
+    // autotuned resident-path settings per (VRP, K precision): solver, rows per lane, cost split
+    std::map<std::pair<int, int>, std::tuple<int, int, int>> tuned_resident;
     std::mutex mu;                 // serialises use of `main` and the graph cache
 };
 
@@ -113,6 +117,10 @@ int status_to_code(int st);
 // Launches the all-iterations solver: the shared-memory tiled kernel when the
 // query's layout allows it, else the register-only resident walk.
 int run_resident(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kprec, cudaStream_t st);
+// The same for nq queries of one layout in one launch (d_batch: device array of
+// their arguments; `shape` is any one of them).
+int run_resident_batch(swmd_corpus *c, const ResidentArgs &shape, Mapping m, int kprec, int nq,
+                       const ResidentArgs *d_batch, cudaStream_t st);
 constexpr int kTileBudgets[] = {64, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048};
 constexpr int kNumTileBudgets = 10;
 // (Re)builds the resident solver's tile sets for the corpus's current
@@ -120,5 +128,7 @@ constexpr int kNumTileBudgets = 10;
 int build_tiles(swmd_corpus *c);
 // Builds the register-resident solver's warp task lists (at corpus creation).
 int build_tasks(swmd_corpus *c);
+// Effective resident settings for a layout: explicit options, else autotuned, else defaults.
+void resident_settings(swmd_corpus *c, int vrp, int kprec, int *solver, int *npl_want, int *split);
 
 }  // namespace swmd

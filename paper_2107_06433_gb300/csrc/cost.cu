@@ -55,7 +55,9 @@ __device__ __forceinline__ float storage_scale(float mmax) {
 }
 
 template <int KPT, int T, class KT_t>
-__global__ void __launch_bounds__(kCostThreads) k_cost(CostArgs a) {
+__global__ void __launch_bounds__(kCostThreads) k_cost(CostArgs a0, const CostArgs *batch) {
+    // one query per grid row when batched (batch[blockIdx.y]), else the argument
+    const CostArgs a = batch ? batch[blockIdx.y] : a0;
     constexpr int VRP = KPT * T;
     constexpr int ROW = KPT + 4;  // padded slice: T slices of a stage row in distinct banks
     static_assert(KPT % 4 == 0, "KPT must be a multiple of 4");
@@ -156,7 +158,8 @@ __global__ void __launch_bounds__(kCostThreads) k_cost(CostArgs a) {
 // chunks per thread in flight (register double buffer); the main loop has no
 // barrier.  The TS partial sums are combined with shuffles at the end.
 template <int VRP, int TS, class KT_t>
-__global__ void __launch_bounds__(kCostThreads) k_cost_rows(CostArgs a) {
+__global__ void __launch_bounds__(kCostThreads) k_cost_rows(CostArgs a0, const CostArgs *batch) {
+    const CostArgs a = batch ? batch[blockIdx.y] : a0;
     static_assert(VRP % 4 == 0 && VRP <= 32, "VRP");
     static_assert(TS == 1 || TS == 2 || TS == 4, "TS");
     constexpr int PF = 4;   // float4 chunks per thread in flight
@@ -264,7 +267,7 @@ __global__ void __launch_bounds__(kCostThreads) k_cost_rows(CostArgs a) {
 }
 
 template <int VRP, int TS, class KT_t>
-cudaError_t run_rows(const CostArgs &a, cudaStream_t s) {
+cudaError_t run_rows(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *batch) {
     auto kern = k_cost_rows<VRP, TS, KT_t>;
     const size_t smem = (size_t)a.d4 * VRP * sizeof(float);
     static size_t configured = 0;
@@ -286,28 +289,31 @@ cudaError_t run_rows(const CostArgs &a, cudaStream_t s) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long per_block = kCostThreads / TS;
     long blocks = (a.Vu + per_block - 1) / per_block;
-    if (blocks > (long)sms * per_sm) blocks = (long)sms * per_sm;
-    if (blocks > 0) kern<<<(unsigned)blocks, kCostThreads, smem, s>>>(a);
+    long cap = ((long)sms * per_sm + nq - 1) / nq;   // resident blocks shared by the queries
+    if (cap < 1) cap = 1;
+    if (blocks > cap) blocks = cap;
+    if (blocks > 0) kern<<<dim3((unsigned)blocks, (unsigned)nq), kCostThreads, smem, s>>>(a, batch);
     return cudaGetLastError();
 }
 
 template <int KPT, int T, class KT_t>
-cudaError_t run(const CostArgs &a, cudaStream_t s) {
+cudaError_t run(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *batch) {
     const int words_per_block = kCostThreads / T;
     const long blocks = (a.Vu + words_per_block - 1) / words_per_block;
-    if (blocks > 0) k_cost<KPT, T, KT_t><<<(unsigned)blocks, kCostThreads, 0, s>>>(a);
+    if (blocks > 0)
+        k_cost<KPT, T, KT_t><<<dim3((unsigned)blocks, (unsigned)nq), kCostThreads, 0, s>>>(a, batch);
     return cudaGetLastError();
 }
 
 template <class KT_t>
-cudaError_t dispatch(const CostArgs &a, int vrp, cudaStream_t s) {
+cudaError_t dispatch(const CostArgs &a, int vrp, cudaStream_t s, int nq, const CostArgs *batch) {
     if (vrp <= 32 && (size_t)a.d4 * vrp * sizeof(float) <= 100 * 1024) {
         const int ts = a.split == 1 || a.split == 4 ? a.split : 2;
         switch (vrp * 10 + ts) {
 #define SWMD_ROWS(V)                                      \
-    case V * 10 + 1: return run_rows<V, 1, KT_t>(a, s); \
-    case V * 10 + 2: return run_rows<V, 2, KT_t>(a, s); \
-    case V * 10 + 4: return run_rows<V, 4, KT_t>(a, s);
+    case V * 10 + 1: return run_rows<V, 1, KT_t>(a, s, nq, batch); \
+    case V * 10 + 2: return run_rows<V, 2, KT_t>(a, s, nq, batch); \
+    case V * 10 + 4: return run_rows<V, 4, KT_t>(a, s, nq, batch);
             SWMD_ROWS(4) SWMD_ROWS(8) SWMD_ROWS(12) SWMD_ROWS(16) SWMD_ROWS(20) SWMD_ROWS(24)
             SWMD_ROWS(28) SWMD_ROWS(32)
 #undef SWMD_ROWS
@@ -316,18 +322,18 @@ cudaError_t dispatch(const CostArgs &a, int vrp, cudaStream_t s) {
     }
     switch (vrp) {
 #define SWMD_COST_T1(V) \
-    case V: return run<V, 1, KT_t>(a, s);
+    case V: return run<V, 1, KT_t>(a, s, nq, batch);
         SWMD_COST_T1(4) SWMD_COST_T1(8) SWMD_COST_T1(12) SWMD_COST_T1(16)
         SWMD_COST_T1(20) SWMD_COST_T1(24) SWMD_COST_T1(28) SWMD_COST_T1(32)
 #undef SWMD_COST_T1
-        case 40: return run<20, 2, KT_t>(a, s);
-        case 48: return run<24, 2, KT_t>(a, s);
-        case 56: return run<28, 2, KT_t>(a, s);
-        case 64: return run<32, 2, KT_t>(a, s);
-        case 80: return run<20, 4, KT_t>(a, s);
-        case 96: return run<24, 4, KT_t>(a, s);
-        case 112: return run<28, 4, KT_t>(a, s);
-        case 128: return run<32, 4, KT_t>(a, s);
+        case 40: return run<20, 2, KT_t>(a, s, nq, batch);
+        case 48: return run<24, 2, KT_t>(a, s, nq, batch);
+        case 56: return run<28, 2, KT_t>(a, s, nq, batch);
+        case 64: return run<32, 2, KT_t>(a, s, nq, batch);
+        case 80: return run<20, 4, KT_t>(a, s, nq, batch);
+        case 96: return run<24, 4, KT_t>(a, s, nq, batch);
+        case 112: return run<28, 4, KT_t>(a, s, nq, batch);
+        case 128: return run<32, 4, KT_t>(a, s, nq, batch);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -370,7 +376,41 @@ __global__ void k_prep(QParams *qp, float lambda, int vr, int V, const int *src_
     }
 }
 
+// One block per query of a batch: the same work as k_prep for query blockIdx.x.
+__global__ void k_prep_batch(const PrepArgs *args, int V) {
+    const PrepArgs p = args[blockIdx.x];
+    if (threadIdx.x == 0) {
+        QParams q;
+        q.lambda = p.lambda;
+        q.vr = p.vr;
+        q.u0 = (float)p.vr;
+        q.pad = 0;
+        q.out = p.out;
+        q.status = p.status;
+        *p.qp = q;
+        *p.status = 0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < p.vrp_cap; k += blockDim.x) {
+        int id = 0;
+        float w = 0.f;
+        if (k < p.vr) {
+            id = p.src_ids[k];
+            w = p.src_r[k];
+            if (id < 0 || id >= V) atomicOr(p.status, ST_BAD_ID);
+            if (!(w > 0.f) || !(w < INFINITY)) atomicOr(p.status, ST_BAD_R);
+        }
+        p.q_ids[k] = id;
+        p.r[k] = w;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_prep_batch(const PrepArgs *d_args, int nq, int V, cudaStream_t s) {
+    if (nq > 0) k_prep_batch<<<nq, 128, 0, s>>>(d_args, V);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_prep(QParams *qp, float lambda, int vr, int V, const int *src_ids,
                         const float *src_r, int *q_ids, float *r, int vrp_cap, double *out,
@@ -380,10 +420,15 @@ cudaError_t launch_prep(QParams *qp, float lambda, int vr, int V, const int *src
 }
 
 cudaError_t launch_cost(const CostArgs &a, int vrp, int kprec, cudaStream_t s) {
+    return launch_cost_batch(a, vrp, kprec, 1, nullptr, s);
+}
+
+cudaError_t launch_cost_batch(const CostArgs &shape, int vrp, int kprec, int nq,
+                              const CostArgs *d_batch, cudaStream_t s) {
     switch (kprec) {
-        case 0: return dispatch<float>(a, vrp, s);
-        case 1: return dispatch<__nv_bfloat16>(a, vrp, s);
-        case 2: return dispatch<__half>(a, vrp, s);
+        case 0: return dispatch<float>(shape, vrp, s, nq, d_batch);
+        case 1: return dispatch<__nv_bfloat16>(shape, vrp, s, nq, d_batch);
+        case 2: return dispatch<__half>(shape, vrp, s, nq, d_batch);
         default: return cudaErrorInvalidValue;
     }
 }

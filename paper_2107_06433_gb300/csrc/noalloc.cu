@@ -117,7 +117,11 @@ extern "C" int swmd_query_noalloc(swmd_corpus *c, const int32_t *d_ids, const fl
     ca.qp = qp;
     ca.V = c->V;
     ca.shift = c->opt.column_shift ? 1 : 0;
-    ca.split = c->opt.cost_split;
+    {
+        int s_ = 0, n_ = 0, cs_ = 0;
+        resident_settings(c, m.vrp, kprec, &s_, &n_, &cs_);
+        ca.split = cs_;
+    }
     ca.KT = KT;
     ca.KMT = KMT;
     SWMD_CK(launch_cost(ca, m.vrp, kprec, st));

@@ -310,8 +310,10 @@ __device__ __forceinline__ void regs_task(const IterArgs &a, int t, int4 tk, int
 }
 
 template <int VRP, int NPL, class KT_t>
-__global__ void __launch_bounds__(kRegThreads) k_resident_regs(ResidentArgs ra, const int4 *tasks,
-                                                               int n_tasks, int ovf_cap) {
+__global__ void __launch_bounds__(kRegThreads) k_resident_regs(ResidentArgs ra0, const ResidentArgs *batch,
+                                                               const int4 *tasks, int n_tasks, int ovf_cap) {
+    // one query per grid row when batched (batch[blockIdx.y]), else the argument
+    const ResidentArgs ra = batch ? batch[blockIdx.y] : ra0;
     const IterArgs &a = ra.it;
     // per warp: the transpose buffer (32 partial rows, stride kRowStride)
     constexpr int WACC = 32 * kRowStride;
@@ -338,7 +340,8 @@ __global__ void __launch_bounds__(kRegThreads) k_resident_regs(ResidentArgs ra, 
 }
 
 template <int VRP, int NPL, class KT_t>
-cudaError_t run_regs(const ResidentArgs &a, const TaskSet &ts, int sms, cudaStream_t s) {
+cudaError_t run_regs(const ResidentArgs &a, const TaskSet &ts, int sms, cudaStream_t s, int nq,
+                     const ResidentArgs *batch) {
     auto kern = k_resident_regs<VRP, NPL, KT_t>;
     // overflow buffer: rows beyond 32 * NPL of the longest document, at most 40 KB per warp
     int ovf = ts.max_len - 32 * NPL;
@@ -364,16 +367,22 @@ cudaError_t run_regs(const ResidentArgs &a, const TaskSet &ts, int sms, cudaStre
         per_sm_smem = smem;
     }
     long blocks = ((long)ts.n_tasks + kWarps - 1) / kWarps;
-    if (blocks > (long)sms * per_sm) blocks = (long)sms * per_sm;
-    if (blocks > 0) kern<<<(unsigned)blocks, kRegThreads, smem, s>>>(a, ts.tasks, ts.n_tasks, ovf);
+    long cap = ((long)sms * per_sm * 2 + nq - 1) / nq;   // resident blocks shared by the queries
+    if (cap < 1) cap = 1;
+    if (nq == 1) cap = (long)sms * per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks > 0)
+        kern<<<dim3((unsigned)blocks, (unsigned)nq), kRegThreads, smem, s>>>(a, batch, ts.tasks,
+                                                                           ts.n_tasks, ovf);
     return cudaGetLastError();
 }
 
 template <class KT_t>
-cudaError_t dispatch_regs(const ResidentArgs &a, int vrp, const TaskSet &ts, int sms, cudaStream_t s) {
+cudaError_t dispatch_regs(const ResidentArgs &a, int vrp, const TaskSet &ts, int sms, cudaStream_t s,
+                          int nq, const ResidentArgs *batch) {
     switch (vrp * 100 + ts.npl) {
 #define SWMD_R(V, N) \
-    case V * 100 + N: return run_regs<V, N, KT_t>(a, ts, sms, s);
+    case V * 100 + N: return run_regs<V, N, KT_t>(a, ts, sms, s, nq, batch);
         SWMD_R(4, 8) SWMD_R(8, 8) SWMD_R(12, 4) SWMD_R(16, 4) SWMD_R(20, 4) SWMD_R(24, 2)
         SWMD_R(28, 2) SWMD_R(32, 2) SWMD_R(12, 8) SWMD_R(16, 2) SWMD_R(20, 2) SWMD_R(20, 3)
         SWMD_R(24, 3) SWMD_R(32, 1) SWMD_R(24, 4)
@@ -398,11 +407,11 @@ int regs_rows_per_lane(int vrp, int want) {
 }
 
 cudaError_t launch_resident_regs(const ResidentArgs &a, int vrp, int kprec, const TaskSet &ts,
-                                 int sms, cudaStream_t s) {
+                                 int sms, cudaStream_t s, int nq, const ResidentArgs *batch) {
     switch (kprec) {
-        case 0: return dispatch_regs<float>(a, vrp, ts, sms, s);
-        case 1: return dispatch_regs<__nv_bfloat16>(a, vrp, ts, sms, s);
-        case 2: return dispatch_regs<__half>(a, vrp, ts, sms, s);
+        case 0: return dispatch_regs<float>(a, vrp, ts, sms, s, nq, batch);
+        case 1: return dispatch_regs<__nv_bfloat16>(a, vrp, ts, sms, s, nq, batch);
+        case 2: return dispatch_regs<__half>(a, vrp, ts, sms, s, nq, batch);
         default: return cudaErrorInvalidValue;
     }
 }

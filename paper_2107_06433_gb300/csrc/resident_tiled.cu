@@ -52,8 +52,11 @@ template <> __device__ __forceinline__ float4 ld4<__half>(const __half *p, int i
 }
 
 template <int VRP, int Q, class KT_t>
-__global__ void __launch_bounds__(kTileThreads) k_resident_tiled(ResidentArgs ra, const int *tiles,
-                                                                 int n_tiles, int NT, int npl) {
+__global__ void __launch_bounds__(kTileThreads) k_resident_tiled(ResidentArgs ra0, const ResidentArgs *batch,
+                                                                 const int *tiles, int n_tiles, int NT,
+                                                                 int npl) {
+    // one query per grid row when batched (batch[blockIdx.y]), else the argument
+    const ResidentArgs ra = batch ? batch[blockIdx.y] : ra0;
     constexpr int S = VRP / Q;
     constexpr int C = S / 4;
     constexpr int ROWB = VRP * (int)sizeof(KT_t);          // bytes of one row
@@ -282,7 +285,8 @@ __global__ void __launch_bounds__(kTileThreads) k_resident_tiled(ResidentArgs ra
 }
 
 template <int VRP, int Q, class KT_t>
-cudaError_t run_tiled(const ResidentArgs &a, const TileSet &ts, int sms, cudaStream_t s) {
+cudaError_t run_tiled(const ResidentArgs &a, const TileSet &ts, int sms, cudaStream_t s, int nq,
+                      const ResidentArgs *batch) {
     auto kern = k_resident_tiled<VRP, Q, KT_t>;
     const size_t smem = tiled_smem_bytes(VRP, (int)sizeof(KT_t), ts.nt);
     static int configured_smem = 0;
@@ -303,27 +307,30 @@ cudaError_t run_tiled(const ResidentArgs &a, const TileSet &ts, int sms, cudaStr
             { (void)cudaGetLastError(); per_sm = 1; }
         per_sm_key = key;
     }
-    int blocks = sms * per_sm;
+    int blocks = nq == 1 ? sms * per_sm : (sms * per_sm * 2 + nq - 1) / nq;
+    if (blocks < 1) blocks = 1;
     if (blocks > ts.n_tiles) blocks = ts.n_tiles;
-    if (blocks > 0) kern<<<blocks, ts.threads, smem, s>>>(a, ts.tiles, ts.n_tiles, ts.nt, ts.npl);
+    if (blocks > 0)
+        kern<<<dim3(blocks, nq), ts.threads, smem, s>>>(a, batch, ts.tiles, ts.n_tiles, ts.nt, ts.npl);
     return cudaGetLastError();
 }
 
 template <class KT_t>
-cudaError_t dispatch_tiled(const ResidentArgs &a, int vrp, const TileSet &ts, int sms, cudaStream_t s) {
+cudaError_t dispatch_tiled(const ResidentArgs &a, int vrp, const TileSet &ts, int sms, cudaStream_t s,
+                           int nq, const ResidentArgs *batch) {
     switch (vrp) {
 #define SWMD_T1(V) \
-    case V: return run_tiled<V, 1, KT_t>(a, ts, sms, s);
+    case V: return run_tiled<V, 1, KT_t>(a, ts, sms, s, nq, batch);
         SWMD_T1(4) SWMD_T1(8) SWMD_T1(12) SWMD_T1(16) SWMD_T1(20) SWMD_T1(24) SWMD_T1(28) SWMD_T1(32)
 #undef SWMD_T1
-        case 40: return run_tiled<40, 2, KT_t>(a, ts, sms, s);
-        case 48: return run_tiled<48, 2, KT_t>(a, ts, sms, s);
-        case 56: return run_tiled<56, 2, KT_t>(a, ts, sms, s);
-        case 64: return run_tiled<64, 2, KT_t>(a, ts, sms, s);
-        case 80: return run_tiled<80, 4, KT_t>(a, ts, sms, s);
-        case 96: return run_tiled<96, 4, KT_t>(a, ts, sms, s);
-        case 112: return run_tiled<112, 4, KT_t>(a, ts, sms, s);
-        case 128: return run_tiled<128, 4, KT_t>(a, ts, sms, s);
+        case 40: return run_tiled<40, 2, KT_t>(a, ts, sms, s, nq, batch);
+        case 48: return run_tiled<48, 2, KT_t>(a, ts, sms, s, nq, batch);
+        case 56: return run_tiled<56, 2, KT_t>(a, ts, sms, s, nq, batch);
+        case 64: return run_tiled<64, 2, KT_t>(a, ts, sms, s, nq, batch);
+        case 80: return run_tiled<80, 4, KT_t>(a, ts, sms, s, nq, batch);
+        case 96: return run_tiled<96, 4, KT_t>(a, ts, sms, s, nq, batch);
+        case 112: return run_tiled<112, 4, KT_t>(a, ts, sms, s, nq, batch);
+        case 128: return run_tiled<128, 4, KT_t>(a, ts, sms, s, nq, batch);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -342,11 +349,11 @@ bool tiled_supported(int vrp, int kprec) {
 }
 
 cudaError_t launch_resident_tiled(const ResidentArgs &a, int vrp, int kprec, const TileSet &ts,
-                                  int sms, cudaStream_t s) {
+                                  int sms, cudaStream_t s, int nq, const ResidentArgs *batch) {
     switch (kprec) {
-        case 0: return dispatch_tiled<float>(a, vrp, ts, sms, s);
-        case 1: return dispatch_tiled<__nv_bfloat16>(a, vrp, ts, sms, s);
-        case 2: return dispatch_tiled<__half>(a, vrp, ts, sms, s);
+        case 0: return dispatch_tiled<float>(a, vrp, ts, sms, s, nq, batch);
+        case 1: return dispatch_tiled<__nv_bfloat16>(a, vrp, ts, sms, s, nq, batch);
+        case 2: return dispatch_tiled<__half>(a, vrp, ts, sms, s, nq, batch);
         default: return cudaErrorInvalidValue;
     }
 }

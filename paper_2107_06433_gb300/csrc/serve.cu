@@ -14,6 +14,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <memory>
 #include <thread>
 #include <unordered_map>
@@ -310,40 +311,171 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
     std::lock_guard<std::mutex> lk(c->mu);
     DeviceGuard guard(c->device);
     cudaStream_t st = c->stream;
-    int32_t *d_ids = nullptr;
-    float *d_r = nullptr;
-    double *d_out = nullptr;
-    int *d_status = nullptr;
-    int rc = SWMD_OK;
-    std::vector<int> h_status((size_t)n_queries, 0);
-    auto cleanup = [&]() {
-        cudaStreamSynchronize(st);
-        cudaFree(d_ids); cudaFree(d_r); cudaFree(d_out); cudaFree(d_status);
-    };
-    cudaError_t e = cudaMalloc(&d_ids, sizeof(int32_t) * std::max<size_t>(ids.size(), 1));
-    if (e == cudaSuccess) e = cudaMalloc(&d_r, sizeof(float) * std::max<size_t>(rs.size(), 1));
-    if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(double) * (size_t)n_queries * c->Nl);
-    if (e == cudaSuccess) e = cudaMalloc(&d_status, sizeof(int) * (size_t)n_queries);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ids, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_r, rs.data(), sizeof(float) * rs.size(), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) {
-        cleanup();
-        return cuda_fail(e, "swmd_query_batch staging");
-    }
-    for (int32_t i = 0; i < n_queries && rc == SWMD_OK; ++i)
-        rc = enqueue_query(c, c->main, d_ids + off[i], d_r + off[i], vrs[i], h_lambdas[i], max_iter,
-                           d_out + (size_t)i * c->Nl, d_status + i, st, true);
-    if (rc == SWMD_OK) {
-        e = cudaMemcpyAsync(h_out, d_out, sizeof(double) * (size_t)n_queries * c->Nl, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess)
+    const int kprec = c->opt.k_precision;
+    const size_t kb = kprec_bytes(kprec);
+
+    if (c->opt.path != SWMD_PATH_RESIDENT) {
+        // per-iteration paths: the queries run one after another on the corpus's slot
+        int32_t *d_ids = nullptr;
+        float *d_r = nullptr;
+        double *d_out = nullptr;
+        int *d_status = nullptr;
+        int rc = SWMD_OK;
+        std::vector<int> h_status((size_t)n_queries, 0);
+        cudaError_t e = cudaMalloc(&d_ids, sizeof(int32_t) * ids.size());
+        if (e == cudaSuccess) e = cudaMalloc(&d_r, sizeof(float) * rs.size());
+        if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(double) * (size_t)n_queries * c->Nl);
+        if (e == cudaSuccess) e = cudaMalloc(&d_status, sizeof(int) * (size_t)n_queries);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_ids, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_r, rs.data(), sizeof(float) * rs.size(), cudaMemcpyHostToDevice, st);
+        for (int32_t i = 0; e == cudaSuccess && i < n_queries && rc == SWMD_OK; ++i)
+            rc = enqueue_query(c, c->main, d_ids + off[i], d_r + off[i], vrs[i], h_lambdas[i], max_iter,
+                               d_out + (size_t)i * c->Nl, d_status + i, st, true);
+        if (e == cudaSuccess && rc == SWMD_OK)
+            e = cudaMemcpyAsync(h_out, d_out, sizeof(double) * (size_t)n_queries * c->Nl, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && rc == SWMD_OK)
             e = cudaMemcpyAsync(h_status.data(), d_status, sizeof(int) * (size_t)n_queries, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) rc = cuda_fail(e, "swmd_query_batch");
+        cudaError_t e2 = cudaStreamSynchronize(st);
+        cudaFree(d_ids); cudaFree(d_r); cudaFree(d_out); cudaFree(d_status);
+        if (rc) return rc;
+        if (e != cudaSuccess || e2 != cudaSuccess) return cuda_fail(e != cudaSuccess ? e : e2, "swmd_query_batch");
+        int all = 0;
+        for (int x : h_status) all |= x;
+        return status_to_code(all);
     }
-    cleanup();
-    if (rc) return rc;
+
+    // ---- resident path: one batched launch per kernel and layout group
+    std::vector<int> vrp((size_t)n_queries);
+    std::map<int, std::vector<int>> groups;   // layout VRP -> queries
+    for (int32_t i = 0; i < n_queries; ++i) {
+        vrp[i] = layout_vrp(c, vrs[i], SWMD_PATH_RESIDENT);
+        groups[vrp[i]].push_back(i);
+    }
+    auto up = [](size_t n) { return (n + 255) & ~size_t(255); };
+    // device workspace: per query K^T, KM^T, parameter block, ids, r, status; then
+    // the outputs, the staged query arrays and the argument arrays
+    std::vector<size_t> kt_off((size_t)n_queries);
+    size_t bytes = 0;
+    for (int32_t i = 0; i < n_queries; ++i) {
+        kt_off[i] = bytes;
+        bytes += 2 * up((size_t)c->Vu * vrp[i] * kb) + up(sizeof(QParams)) + 2 * up(sizeof(float) * vrp[i]) + 256;
+    }
+    const size_t o_out = bytes;
+    bytes += up(sizeof(double) * (size_t)n_queries * c->Nl);
+    const size_t o_ids = bytes;
+    bytes += up(sizeof(int32_t) * ids.size());
+    const size_t o_r = bytes;
+    bytes += up(sizeof(float) * rs.size());
+    const size_t o_prep = bytes;
+    bytes += up(sizeof(PrepArgs) * n_queries);
+    const size_t o_cost = bytes;
+    bytes += up(sizeof(CostArgs) * n_queries);
+    const size_t o_res = bytes;
+    bytes += up(sizeof(ResidentArgs) * n_queries);
+    if (c->batch_ws_bytes < bytes) {
+        if (c->batch_ws) {
+            cudaStreamSynchronize(st);
+            cudaFree(c->batch_ws);
+            c->batch_ws = nullptr;
+            c->batch_ws_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&c->batch_ws, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "swmd_query_batch: workspace");
+        c->batch_ws_bytes = bytes;
+    }
+    char *ws = static_cast<char *>(c->batch_ws);
+    std::vector<PrepArgs> prep((size_t)n_queries);
+    std::vector<CostArgs> cost((size_t)n_queries);
+    std::vector<ResidentArgs> res((size_t)n_queries);
+    std::vector<int *> status_ptr((size_t)n_queries);
+    for (int32_t i = 0; i < n_queries; ++i) {
+        char *b = ws + kt_off[i];
+        void *KT = b;
+        void *KMT = b + up((size_t)c->Vu * vrp[i] * kb);
+        QParams *qp = reinterpret_cast<QParams *>(b + 2 * up((size_t)c->Vu * vrp[i] * kb));
+        int *q_ids = reinterpret_cast<int *>(reinterpret_cast<char *>(qp) + up(sizeof(QParams)));
+        float *r = reinterpret_cast<float *>(reinterpret_cast<char *>(q_ids) + up(sizeof(float) * vrp[i]));
+        int *status = reinterpret_cast<int *>(reinterpret_cast<char *>(r) + up(sizeof(float) * vrp[i]));
+        double *out = reinterpret_cast<double *>(ws + o_out) + (size_t)i * c->Nl;
+        status_ptr[i] = status;
+        PrepArgs &p = prep[i];
+        p.qp = qp;
+        p.src_ids = reinterpret_cast<const int *>(ws + o_ids) + off[i];
+        p.src_r = reinterpret_cast<const float *>(ws + o_r) + off[i];
+        p.q_ids = q_ids;
+        p.r = r;
+        p.out = out;
+        p.status = status;
+        p.lambda = h_lambdas[i];
+        p.vr = vrs[i];
+        p.vrp_cap = vrp[i];
+        p.pad = 0;
+        CostArgs &ca = cost[i];
+        ca = CostArgs{};
+        ca.E = c->E;
+        ca.d4 = c->d4;
+        ca.used = c->used;
+        ca.Vu = c->Vu;
+        ca.q_ids = q_ids;
+        ca.qp = qp;
+        ca.V = c->V;
+        ca.shift = c->opt.column_shift ? 1 : 0;
+        {
+            int s_ = 0, n_ = 0, cs_ = 0;
+            resident_settings(c, vrp[i], kprec, &s_, &n_, &cs_);
+            ca.split = cs_;
+        }
+        ca.KT = KT;
+        ca.KMT = KMT;
+        IterArgs ia{};
+        ia.doc_ptr = c->doc_ptr;
+        ia.nz = c->nz;
+        ia.KT = KT;
+        ia.KMT = KMT;
+        ia.r = r;
+        ia.doc_orig = c->doc_orig;
+        ia.qp = qp;
+        ia.doc0 = 0;
+        ia.N = c->Nl;
+        ia.first = 1;
+        res[i] = ResidentArgs{ia, max_iter};
+    }
+    // group-contiguous copies of the argument arrays (grid row y of a group's
+    // launch reads element y of its slice)
+    std::vector<CostArgs> cost_g;
+    std::vector<ResidentArgs> res_g;
+    std::vector<std::pair<int, size_t>> gstart;   // (vrp, first index in the grouped arrays)
+    for (auto &g : groups) {
+        gstart.emplace_back(g.first, cost_g.size());
+        for (int i : g.second) {
+            cost_g.push_back(cost[i]);
+            res_g.push_back(res[i]);
+        }
+    }
+    SWMD_CK(cudaMemcpyAsync(ws + o_ids, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice, st));
+    SWMD_CK(cudaMemcpyAsync(ws + o_r, rs.data(), sizeof(float) * rs.size(), cudaMemcpyHostToDevice, st));
+    SWMD_CK(cudaMemcpyAsync(ws + o_prep, prep.data(), sizeof(PrepArgs) * prep.size(), cudaMemcpyHostToDevice, st));
+    SWMD_CK(cudaMemcpyAsync(ws + o_cost, cost_g.data(), sizeof(CostArgs) * cost_g.size(), cudaMemcpyHostToDevice, st));
+    SWMD_CK(cudaMemcpyAsync(ws + o_res, res_g.data(), sizeof(ResidentArgs) * res_g.size(), cudaMemcpyHostToDevice, st));
+    SWMD_CK(launch_prep_batch(reinterpret_cast<const PrepArgs *>(ws + o_prep), n_queries, c->V, st));
+    for (size_t gi = 0; gi < gstart.size(); ++gi) {
+        const int v = gstart[gi].first;
+        const size_t g0 = gstart[gi].second;
+        const int ng = (int)groups[v].size();
+        const Mapping m = walk_mapping(c, v, SWMD_PATH_RESIDENT);
+        SWMD_CK(launch_cost_batch(cost_g[g0], v, kprec, ng,
+                                  reinterpret_cast<const CostArgs *>(ws + o_cost) + g0, st));
+        int rc = run_resident_batch(c, res_g[g0], m, kprec, ng,
+                                    reinterpret_cast<const ResidentArgs *>(ws + o_res) + g0, st);
+        if (rc) return rc;
+    }
+    std::vector<int> h_status((size_t)n_queries, 0);
+    SWMD_CK(cudaMemcpyAsync(h_out, ws + o_out, sizeof(double) * (size_t)n_queries * c->Nl, cudaMemcpyDeviceToHost, st));
+    for (int32_t i = 0; i < n_queries; ++i)
+        SWMD_CK(cudaMemcpyAsync(&h_status[i], status_ptr[i], sizeof(int), cudaMemcpyDeviceToHost, st));
+    SWMD_CK(cudaStreamSynchronize(st));
     int all = 0;
-    for (int s : h_status) all |= s;
+    for (int x : h_status) all |= x;
     return status_to_code(all);
 }
 

@@ -1,0 +1,163 @@
+// Autotuning of the resident path's lane mappings for one query size.
+//
+// The resident path is one cost launch (the dense Q^T-vs-vocabulary distance
+// block and K = exp(-lambda M), the M and K steps of Algorithm 1) followed by
+// one solver launch that runs every Sinkhorn iteration (Algorithms 2 and 3 fused
+// per document, Section III-C).  Which solver and lane mapping is fastest depends
+// on the corpus's length mix and on v_r, so it is measured here on the corpus
+// itself instead of fixed by hand (the paper picks its mappings by hand for each
+// machine, Sections IV-V).
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <set>
+#include <tuple>
+#include <vector>
+
+#include "corpus.h"
+
+using namespace swmd;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+constexpr float kTuneLambda = 10.0f;
+constexpr int kTuneIters = 15;
+
+// splitmix64: a fixed, platform-independent generator for the timing query
+uint64_t splitmix(uint64_t &x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Median time in ms of `reps` whole queries (prep, cost, solver) after one
+// untimed run; a negative value when the configuration cannot launch.
+float time_query(swmd_corpus *c, Slot &s, int vr, int reps, cudaStream_t st, cudaEvent_t e0,
+                 cudaEvent_t e1) {
+    if (enqueue_query(c, s, s.q_in, s.r_in, vr, kTuneLambda, kTuneIters, s.out, s.status, st, false))
+        return -1.0f;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return -1.0f;
+    std::vector<float> ms;
+    for (int i = 0; i < reps; ++i) {
+        cudaEventRecord(e0, st);
+        if (enqueue_query(c, s, s.q_in, s.r_in, vr, kTuneLambda, kTuneIters, s.out, s.status, st,
+                          false))
+            return -1.0f;
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0f;
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms.push_back(t);
+    }
+    std::sort(ms.begin(), ms.end());
+    return ms[ms.size() / 2];
+}
+
+}  // namespace
+
+int swmd_autotune(swmd_corpus *c, int32_t v_r, int32_t reps, swmd_tune_result *out) {
+    if (!c || !out) return set_error(SWMD_EINVAL, "swmd_autotune: NULL argument");
+    if (reps < 1) return set_error(SWMD_EINVAL, "swmd_autotune: reps must be >= 1");
+    if (c->opt.path != SWMD_PATH_RESIDENT)
+        return set_error(SWMD_EINVAL, "swmd_autotune tunes the resident path; the corpus uses path %d",
+                         c->opt.path);
+    if (v_r < 1 || v_r > c->opt.max_vr || v_r > c->V)
+        return set_error(SWMD_EINVAL, "swmd_autotune: v_r %d outside [1, min(max_vr %d, V %d)]", v_r,
+                         c->opt.max_vr, c->V);
+    std::memset(out, 0, sizeof(*out));
+    if (c->Nl == 0) return SWMD_OK;
+
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard guard(c->device);
+    Slot &s = c->main;
+    cudaStream_t st = c->stream;
+
+    // the timing query: v_r distinct ids, uniform weights
+    std::vector<int32_t> ids;
+    std::vector<float> r((size_t)v_r, 1.0f / (float)v_r);
+    if ((int64_t)v_r * 2 > c->V) {
+        for (int i = 0; i < v_r; ++i) ids.push_back(i);
+    } else {
+        std::set<int32_t> seen;
+        uint64_t x = 0x2107064330ull + (uint64_t)v_r;
+        while ((int)ids.size() < v_r) {
+            const int32_t w = (int32_t)(splitmix(x) % (uint64_t)c->V);
+            if (seen.insert(w).second) ids.push_back(w);
+        }
+    }
+    SWMD_CK(cudaMemcpyAsync(s.q_in, ids.data(), sizeof(int32_t) * v_r, cudaMemcpyHostToDevice, st));
+    SWMD_CK(cudaMemcpyAsync(s.r_in, r.data(), sizeof(float) * v_r, cudaMemcpyHostToDevice, st));
+
+    const int vrp = layout_vrp(c, v_r, SWMD_PATH_RESIDENT);
+    const int kprec = c->opt.k_precision;
+    const auto key = std::make_pair(vrp, kprec);
+
+    // time with every tunable field free; the caller's fixed fields are put back after
+    const int fix_solver = c->opt.solver, fix_npl = c->opt.nnz_per_lane, fix_split = c->opt.cost_split;
+    c->opt.solver = c->opt.nnz_per_lane = c->opt.cost_split = 0;
+    c->tuned_resident.erase(key);
+
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+
+    auto timed = [&](std::tuple<int, int, int> cfg) {
+        c->tuned_resident[key] = cfg;
+        const float ms = time_query(c, s, v_r, reps, st, e0, e1);
+        cudaGetLastError();   // a configuration that cannot launch leaves no sticky error
+        ++out->candidates;
+        return ms;
+    };
+
+    std::tuple<int, int, int> best{0, 0, 0};
+    float best_ms = timed(best);
+    out->default_ms = best_ms;
+    std::vector<std::tuple<int, int, int>> cands;
+    if (regs_rows_per_lane(vrp, 0) > 0)
+        for (int npl : {1, 2, 3, 4, 8})
+            if (regs_rows_per_lane(vrp, npl) == npl) cands.emplace_back(1, npl, 0);
+    if (tiled_supported(vrp, kprec)) cands.emplace_back(2, 0, 0);
+    for (auto &cfg : cands) {
+        const float ms = timed(cfg);
+        if (ms > 0.0f && (best_ms <= 0.0f || ms < best_ms)) best_ms = ms, best = cfg;
+    }
+    if (vrp <= 32) {   // threads per word of the row-wise cost kernel
+        for (int split : {1, 2, 4}) {
+            auto cfg = std::make_tuple(std::get<0>(best), std::get<1>(best), split);
+            const float ms = timed(cfg);
+            if (ms > 0.0f && (best_ms <= 0.0f || ms < best_ms)) best_ms = ms, best = cfg;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+
+    c->tuned_resident[key] = best;
+    c->opt.solver = fix_solver;
+    c->opt.nnz_per_lane = fix_npl;
+    c->opt.cost_split = fix_split;
+    // captured graphs hold the kernels of the settings they were captured with
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+
+    if (best_ms <= 0.0f) return set_error(SWMD_ECUDA, "swmd_autotune: no configuration ran for v_r %d", v_r);
+    out->vrp = vrp;
+    out->solver = std::get<0>(best);
+    out->nnz_per_lane = std::get<1>(best);
+    out->cost_split = std::get<2>(best);
+    out->best_ms = best_ms;
+    return SWMD_OK;
+}

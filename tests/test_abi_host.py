@@ -30,8 +30,14 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("swmd_create_corpus", "swmd_destroy_corpus", "swmd_query",
                      "swmd_query_batch", "swmd_serve_start", "swmd_serve_submit",
-                     "swmd_serve_wait", "swmd_serve_stats", "swmd_serve_stop", "swmd_last_error"):
+                     "swmd_serve_wait", "swmd_serve_stats", "swmd_serve_stop", "swmd_last_error",
+                     "swmd_autotune", "swmd_query_noalloc"):
         assert required in names
+
+
+def test_binding_covers_every_declared_function():
+    missing = [n for n in declared_functions() if n not in swmd._SIGS]
+    assert not missing, missing
 
 
 def test_library_exports_every_declared_symbol(lib):

@@ -315,3 +315,38 @@ def test_served_results_equal_alone_bitwise(paper):
     st = swmd.swmd_serve_stats(srv)
     assert st["completed"] == len(qs) and st["p99_ms"] >= st["p50_ms"] > 0
     srv.stop()
+
+
+def test_batch_spanning_every_layout_equals_alone_bitwise(paper):
+    """40 queries of 1..128 words (every resident layout, register and shared-memory
+    solvers) in one call: each equals its own single query bit for bit."""
+    E, C, _ = paper
+    corpus = swmd.corpus_from_synth(E, C)
+    qs = synth.batch_queries(C.V, 40, 1, 128, seed=77)
+    batch = swmd.swmd_query_batch(corpus, qs, 1.0, 15)
+    for i, (qi, qw) in enumerate(qs):
+        np.testing.assert_array_equal(batch[i], swmd.swmd_query(corpus, qi, qw, 1.0, 15))
+
+
+@pytest.mark.parametrize("vr", [5, 19, 32, 64])
+def test_autotune_then_query_matches_oracle(paper, vr):
+    E, C, _ = paper
+    corpus = swmd.corpus_from_synth(E, C)
+    res = swmd.swmd_autotune(corpus, vr, 3)
+    assert res["candidates"] >= 2 and res["best_ms"] > 0
+    assert res["best_ms"] <= res["default_ms"] * 1.0001
+    assert res["solver"] in (0, 1, 2) and res["vrp"] >= vr
+    qi, qw = synth.query(np.random.default_rng(vr), C.V, vr)
+    got = swmd.swmd_query(corpus, qi, qw, 1.0, 15)
+    assert rel_err(got, oracle_wmd(E, C, qi, qw, 1.0, 15)) <= RTOL
+    # the tuned settings serve batches too, bit for bit
+    qs = [(qi, qw), synth.query(np.random.default_rng(vr + 1), C.V, vr)]
+    batch = swmd.swmd_query_batch(corpus, qs, 1.0, 15)
+    np.testing.assert_array_equal(batch[0], got)
+
+
+def test_autotune_rejects_per_iteration_paths(paper):
+    E, C, _ = paper
+    corpus = swmd.corpus_from_synth(E, C, path="fused")
+    with pytest.raises(swmd.SwmdError):
+        swmd.swmd_autotune(corpus, 8, 1)
