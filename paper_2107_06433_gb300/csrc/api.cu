@@ -86,7 +86,8 @@ int alloc_slot(swmd_corpus *c, Slot &s, int max_vr, int kprec, bool with_v) {
     if ((rc = dev_alloc(&kmt, (size_t)std::max(c->Vu, 1) * vrp * kb, &s.bytes))) return rc;
     s.KMT = kmt;
     if ((rc = dev_alloc(&s.u, (size_t)std::max(c->Nl, 1) * vrp, &s.bytes))) return rc;
-    if (with_v && (rc = dev_alloc(&s.v, (size_t)std::max<int64_t>(c->nnz, 1), &s.bytes))) return rc;
+    if (with_v && (rc = dev_alloc(&s.v, (size_t)std::max<int64_t>(std::max(c->nnz, c->slice_total), 1), &s.bytes)))
+        return rc;
     if ((rc = dev_alloc(&s.q_ids, vrp, &s.bytes))) return rc;
     if ((rc = dev_alloc(&s.r, vrp, &s.bytes))) return rc;
     if ((rc = dev_alloc(&s.qp, 1, &s.bytes))) return rc;
@@ -152,16 +153,16 @@ Mapping choose_mapping(swmd_corpus *c, int vr, int path) {
 
 // per-iteration launches of one mapping (lanes-over-k walk when m.p == 0)
 static cudaError_t iter_fused(const IterArgs &ia, Mapping m, int kprec, int sms, cudaStream_t st) {
-    return m.p == 0 ? launch_fused2(ia, m.vrp, kprec, sms, st) : launch_fused(ia, m, kprec, sms, st);
+    return m.p == 0 ? launch_fused3(ia, m.vrp, kprec, sms, st) : launch_fused(ia, m, kprec, sms, st);
 }
 static cudaError_t iter_sddmm(const IterArgs &ia, Mapping m, int kprec, int sms, cudaStream_t st) {
-    return m.p == 0 ? launch_sddmm2(ia, m.vrp, kprec, sms, st) : launch_sddmm(ia, m, kprec, sms, st);
+    return m.p == 0 ? launch_sddmm3(ia, m.vrp, kprec, sms, st) : launch_sddmm(ia, m, kprec, sms, st);
 }
 static cudaError_t iter_spmm(const IterArgs &ia, Mapping m, int kprec, int sms, cudaStream_t st) {
-    return m.p == 0 ? launch_spmm2(ia, m.vrp, kprec, sms, st) : launch_spmm(ia, m, kprec, sms, st);
+    return m.p == 0 ? launch_spmm3(ia, m.vrp, kprec, sms, st) : launch_spmm(ia, m, kprec, sms, st);
 }
 static cudaError_t iter_final(const IterArgs &ia, Mapping m, int kprec, int sms, cudaStream_t st) {
-    return m.p == 0 ? launch_final2(ia, m.vrp, kprec, sms, st) : launch_final(ia, m, kprec, sms, st);
+    return m.p == 0 ? launch_final3(ia, m.vrp, kprec, sms, st) : launch_final(ia, m, kprec, sms, st);
 }
 
 int build_tiles(swmd_corpus *c) {
@@ -322,6 +323,9 @@ static int launch_sequence(swmd_corpus *c, Slot &s, Mapping m, int t, int path, 
     ia.qp = s.qp;
     ia.doc0 = 0;
     ia.N = c->Nl;
+    ia.slice_ptr = c->slice_ptr;
+    ia.slice_nz = c->slice_nz;
+    ia.n_slices = c->n_slices;
     if (path == SWMD_PATH_RESIDENT) {
         ResidentArgs ra{ia, t};
         ra.it.first = 1;
@@ -552,8 +556,27 @@ int swmd_create_corpus(int32_t V, int32_t N, int64_t nnz, const int64_t *row_ptr
             nzh[(size_t)dptr[i] + fill[i]++] = t;
         }
 
+    // ---- the sliced copy: slices of 32 consecutive documents, entry (i, t) at
+    // slice_ptr[s] + 32 i + t, padded with (0, c = 0) to the slice's longest document
+    const int n_slices = (Nl + kSliceDocs - 1) / kSliceDocs;
+    std::vector<int32_t> sptr((size_t)n_slices + 1, 0);
+    for (int s = 0; s < n_slices; ++s) {
+        const int64_t next = (int64_t)sptr[s] + (int64_t)kSliceDocs * (dptr[s * kSliceDocs + 1] - dptr[s * kSliceDocs]);
+        if (next > INT32_MAX) return set_error(SWMD_EINVAL, "swmd_create_corpus: too many nonzeros");
+        sptr[s + 1] = (int32_t)next;
+    }
+    const int64_t slice_total = sptr[n_slices];
+    std::vector<int2> snz((size_t)std::max<int64_t>(slice_total, 1), make_int2(0, 0));
+    for (int i = 0; i < Nl; ++i) {
+        const int s = i / kSliceDocs, t = i % kSliceDocs;
+        for (int32_t k = 0; k < dptr[i + 1] - dptr[i]; ++k)
+            snz[(size_t)sptr[s] + (size_t)k * kSliceDocs + t] = nzh[(size_t)dptr[i] + k];
+    }
+
     auto *c = new swmd_corpus();
     c->V = V;
+    c->n_slices = n_slices;
+    c->slice_total = slice_total;
     c->N = N;
     c->d = d;
     c->d4 = (d + 3) / 4 * 4;
@@ -593,6 +616,9 @@ int swmd_create_corpus(int32_t V, int32_t N, int64_t nnz, const int64_t *row_ptr
     if ((rc = dev_alloc(&c->doc_ptr, (size_t)Nl + 1, &c->base_bytes))) return bail(rc);
     if ((rc = dev_alloc(&c->nz, (size_t)std::max<int64_t>(nnz_l, 1), &c->base_bytes))) return bail(rc);
     if ((rc = dev_alloc(&c->doc_orig, (size_t)std::max(Nl, 1), &c->base_bytes))) return bail(rc);
+    if ((rc = dev_alloc(&c->slice_ptr, (size_t)n_slices + 1, &c->base_bytes))) return bail(rc);
+    if ((rc = dev_alloc(&c->slice_nz, (size_t)std::max<int64_t>(slice_total, 1), &c->base_bytes)))
+        return bail(rc);
     cudaError_t ce;
     if (c->d4 == d) {
         ce = cudaMemcpy(c->E, emb, sizeof(float) * (size_t)V * d, cudaMemcpyHostToDevice);
@@ -613,6 +639,12 @@ int swmd_create_corpus(int32_t V, int32_t N, int64_t nnz, const int64_t *row_ptr
     if (nnz_l > 0 && (ce = cudaMemcpy(c->nz, nzh.data(), sizeof(int2) * (size_t)nnz_l,
                                       cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(cuda_fail(ce, "copy nonzeros"));
+    if ((ce = cudaMemcpy(c->slice_ptr, sptr.data(), sizeof(int32_t) * sptr.size(),
+                         cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(cuda_fail(ce, "copy slice offsets"));
+    if (slice_total > 0 && (ce = cudaMemcpy(c->slice_nz, snz.data(), sizeof(int2) * (size_t)slice_total,
+                                            cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(cuda_fail(ce, "copy sliced nonzeros"));
     if (Nl > 0 && (ce = cudaMemcpy(c->doc_orig, order.data(), sizeof(int32_t) * (size_t)Nl,
                                    cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(cuda_fail(ce, "copy document order"));
@@ -636,6 +668,8 @@ void swmd_destroy_corpus(swmd_corpus *c) {
         dev_free(c->used);
         dev_free(c->doc_ptr);
         dev_free(c->nz);
+        dev_free(c->slice_ptr);
+        dev_free(c->slice_nz);
         dev_free(c->doc_orig);
         dev_free(c->tiles_dev);
         dev_free(c->tasks_dev);
@@ -749,6 +783,9 @@ static IterArgs iter_args(swmd_corpus *c, Slot &s) {
     ia.qp = s.qp;
     ia.doc0 = 0;
     ia.N = c->Nl;
+    ia.slice_ptr = c->slice_ptr;
+    ia.slice_nz = c->slice_nz;
+    ia.n_slices = c->n_slices;
     return ia;
 }
 

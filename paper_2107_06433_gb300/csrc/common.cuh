@@ -41,6 +41,9 @@ struct QParams {
     int *status;     // status word of this query
 };
 
+// Documents per slice of the sliced nonzero layout.
+constexpr int kSliceDocs = 32;
+
 struct IterArgs {
     const int *doc_ptr;
     const int2 *nz;
@@ -55,6 +58,11 @@ struct IterArgs {
     int N;                 // documents in this launch
     int first;             // 1: u = v_r (x = 1/v_r), do not read u
     double *out;           // if not NULL, the distances go here instead of qp->out
+    // sliced nonzeros (per-iteration walks): slices of 32 documents, entry (i, t)
+    // of slice s at slice_ptr[s] + 32 i + t; v (plain path) uses the same positions
+    const int *slice_ptr;
+    const int2 *slice_nz;
+    int n_slices;
 };
 
 struct CostArgs {
@@ -116,11 +124,11 @@ cudaError_t launch_spmm(const IterArgs &a, Mapping m, int kprec, int sms, cudaSt
 cudaError_t launch_final(const IterArgs &a, Mapping m, int kprec, int sms, cudaStream_t s);
 cudaError_t launch_resident(const ResidentArgs &a, Mapping m, int kprec, int sms,
                             cudaStream_t s);
-// Lanes-over-k walks (a team of VRP / 4 lanes per document; VRP in {4, 8, 16, 32, 64, 128}).
-cudaError_t launch_fused2(const IterArgs &a, int vrp, int kprec, int sms, cudaStream_t s);
-cudaError_t launch_sddmm2(const IterArgs &a, int vrp, int kprec, int sms, cudaStream_t s);
-cudaError_t launch_spmm2(const IterArgs &a, int vrp, int kprec, int sms, cudaStream_t s);
-cudaError_t launch_final2(const IterArgs &a, int vrp, int kprec, int sms, cudaStream_t s);
+// Walks over the sliced nonzeros with lanes over k (VRP in {4, 8, 16, 32, 64, 128}).
+cudaError_t launch_fused3(const IterArgs &a, int vrp, int kprec, int sms, cudaStream_t s);
+cudaError_t launch_sddmm3(const IterArgs &a, int vrp, int kprec, int sms, cudaStream_t s);
+cudaError_t launch_spmm3(const IterArgs &a, int vrp, int kprec, int sms, cudaStream_t s);
+cudaError_t launch_final3(const IterArgs &a, int vrp, int kprec, int sms, cudaStream_t s);
 // Documents packed into tiles of at most `nt` nonzeros (at most 64 documents,
 // consecutive in the internal order): tiles[0..n_tiles] are document offsets.
 struct TileSet {

@@ -75,6 +75,11 @@ struct swmd_corpus {
     int *used = nullptr;
     int *doc_ptr = nullptr;
     int2 *nz = nullptr;
+    // the same nonzeros in slices of 32 documents (per-iteration walks)
+    int *slice_ptr = nullptr;
+    int2 *slice_nz = nullptr;
+    int n_slices = 0;
+    int64_t slice_total = 0;       // entries including the slices' padding
     int *doc_orig = nullptr;
     std::vector<int> len_sorted;   // document lengths in internal order (host)
     double mean_len = 0;

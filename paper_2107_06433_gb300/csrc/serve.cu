@@ -116,7 +116,7 @@ struct ServerSlot {
 size_t query_bytes(swmd_corpus *c, int vrp, int path) {
     size_t b = 2 * (size_t)c->Vu * vrp * kprec_bytes(c->opt.k_precision);
     if (path != SWMD_PATH_RESIDENT) b += (size_t)c->Nl * vrp * sizeof(float);
-    if (path == SWMD_PATH_PLAIN) b += (size_t)c->nnz * sizeof(float);
+    if (path == SWMD_PATH_PLAIN) b += (size_t)std::max(c->nnz, c->slice_total) * sizeof(float);
     return b + 3 * 256;
 }
 
@@ -176,7 +176,7 @@ int launch_on_slot(swmd_server *S, ServerSlot &sl) {
     sl.ws.KT = carve(kbytes);
     sl.ws.KMT = carve(kbytes);
     sl.ws.u = path != SWMD_PATH_RESIDENT ? (float *)carve((size_t)c->Nl * m.vrp * sizeof(float)) : nullptr;
-    sl.ws.v = path == SWMD_PATH_PLAIN ? (float *)carve((size_t)c->nnz * sizeof(float)) : nullptr;
+    sl.ws.v = path == SWMD_PATH_PLAIN ? (float *)carve((size_t)std::max(c->nnz, c->slice_total) * sizeof(float)) : nullptr;
     std::memcpy(sl.h_q, R.ids.data(), sizeof(int32_t) * R.vr);
     std::memcpy(sl.h_r, R.r.data(), sizeof(float) * R.vr);
     SWMD_CK(cudaMemcpyAsync(sl.ws.q_in, sl.h_q, sizeof(int32_t) * R.vr, cudaMemcpyHostToDevice, sl.stream));

@@ -1,5 +1,5 @@
 // a4: the final step of Algorithm 1 (SDDMM_SpMM type 2) and the distance.
-#include "walk2.cuh"
+#include "walk3.cuh"
 
 namespace swmd {
 
@@ -32,8 +32,8 @@ int vrp_for(int vr, int q) {
 }
 
 
-cudaError_t launch_final2(const IterArgs &a, int vrp, int kprec, int sms, cudaStream_t s) {
-    return dispatch_walk2_prec<Kind::Final>(a, vrp, kprec, sms, s);
+cudaError_t launch_final3(const IterArgs &a, int vrp, int kprec, int sms, cudaStream_t s) {
+    return dispatch_walk3_prec<Kind::Final>(a, vrp, kprec, sms, s);
 }
 
 }  // namespace swmd

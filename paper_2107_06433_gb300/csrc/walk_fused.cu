@@ -1,5 +1,5 @@
 // a3: the fused SDDMM-SpMM iteration (Section III-C, SDDMM_SpMM type 1).
-#include "walk2.cuh"
+#include "walk3.cuh"
 
 namespace swmd {
 
@@ -8,8 +8,8 @@ cudaError_t launch_fused(const IterArgs &a, Mapping m, int kprec, int sms, cudaS
 }
 
 
-cudaError_t launch_fused2(const IterArgs &a, int vrp, int kprec, int sms, cudaStream_t s) {
-    return dispatch_walk2_prec<Kind::Fused>(a, vrp, kprec, sms, s);
+cudaError_t launch_fused3(const IterArgs &a, int vrp, int kprec, int sms, cudaStream_t s) {
+    return dispatch_walk3_prec<Kind::Fused>(a, vrp, kprec, sms, s);
 }
 
 }  // namespace swmd
