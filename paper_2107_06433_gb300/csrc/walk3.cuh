@@ -19,11 +19,12 @@
 // documents of its slice, launch or partition.
 #pragma once
 
+#include <type_traits>
+
 #include "walk.cuh"
 
 namespace swmd {
 
-constexpr int kWalk3Threads = 256;
 constexpr int kSlice = kSliceDocs;
 
 template <int VRP, class KT_t>
@@ -34,8 +35,6 @@ struct W3 {
     static constexpr int WORDS = P * EB / 4;                     // 32-bit words per lane and row
     static constexpr int TPW = 32 / Q;                           // documents per warp
     static constexpr int RB = 4;                                 // rows per batch
-    static constexpr int ROWS = Q > RB ? Q : RB;                 // rows per group
-    static constexpr int EPL = ROWS / Q;                         // entries loaded per lane per group
     static_assert(P % 2 == 0 && WORDS >= 2 && WORDS <= 8, "lane slice of 8 to 32 bytes");
     static_assert((Q & (Q - 1)) == 0 && Q <= 32, "team must be a power of two");
 };
@@ -76,6 +75,39 @@ __device__ __forceinline__ float2 pair_of<__half>(const uint32_t *w, int i) {
     return __half22float2(h);
 }
 
+// The same widening as pair_of, written so the compiler cannot reuse (and keep
+// live) the values pair_of produced earlier: for 16-bit rows that would hold
+// twice the registers of the raw row across the whole batch.
+template <class KT_t>
+__device__ __forceinline__ float2 pair_again(const uint32_t *w, int i) {
+    return pair_of<KT_t>(w, i);
+}
+template <>
+__device__ __forceinline__ float2 pair_again<__nv_bfloat16>(const uint32_t *w, int i) {
+    uint32_t lo, hi;
+    asm volatile("shl.b32 %0, %2, 16;\n\tand.b32 %1, %2, 0xffff0000;" : "=r"(lo), "=r"(hi) : "r"(w[i]));
+    return make_float2(__uint_as_float(lo), __uint_as_float(hi));
+}
+template <>
+__device__ __forceinline__ float2 pair_again<__half>(const uint32_t *w, int i) {
+    float x, y;
+    asm volatile("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\tcvt.f32.f16 %0, l;\n\tcvt.f32.f16 %1, h;\n\t}"
+                 : "=f"(x), "=f"(y) : "r"(w[i]));
+    return make_float2(x, y);
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// 1/x from the SFU's approximate reciprocal (relative error about 2^-23;
+// subnormal x flushes to zero, so 1/x is then infinite).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <int P>
 __device__ __forceinline__ void load_floats(const float *p, float (&v)[P]) {
 #pragma unroll
@@ -85,48 +117,73 @@ __device__ __forceinline__ void load_floats(const float *p, float (&v)[P]) {
     }
 }
 
-template <int VRP, class KT_t, Kind KIND>
-__global__ void __launch_bounds__(kWalk3Threads) k_walk3(IterArgs a) {
+template <int VRP, class KT_t, Kind KIND, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
     using C = W3<VRP, KT_t>;
-    constexpr int P = C::P, Q = C::Q, WORDS = C::WORDS, TPW = C::TPW, RB = C::RB;
-    constexpr int ROWS = C::ROWS, EPL = C::EPL;
+    constexpr int P = C::P, Q = C::Q, WORDS = C::WORDS, TPW = C::TPW;
+    constexpr int RB = C::RB;
     constexpr bool kDots = KIND != Kind::Spmm;
 
     const int lane = threadIdx.x & 31;
     const int tl = lane & (Q - 1);
     const int team = lane / Q;
-    const int lead = lane & ~(Q - 1);
     const long warp_global = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
     const int vr = a.qp->vr;
     const float u0 = a.qp->u0;
     int *const status = a.qp->status;
     double *const out = a.out ? a.out : a.qp->out;
-    const char *KT = reinterpret_cast<const char *>(a.KT);
-    const char *KMT = reinterpret_cast<const char *>(a.KMT);
     constexpr long kRowBytes = (long)VRP * C::EB;
     const long lane_off = (long)tl * P * C::EB;
+    const char *KTl = reinterpret_cast<const char *>(a.KT) + lane_off;
+    const char *KMTl = reinterpret_cast<const char *>(a.KMT) + lane_off;
     const long n_groups = (long)a.n_slices * Q;
 
+    // slice bounds of the warp's next group, loaded one group ahead
+    int nb = 0, ne = 0;
+    if (warp_global < n_groups) {
+        const int s0 = (int)(warp_global / Q);
+        nb = __ldg(a.slice_ptr + s0);
+        ne = __ldg(a.slice_ptr + s0 + 1);
+    }
     for (long g = warp_global; g < n_groups; g += nwarps) {
         const int s = (int)(g / Q);
         const int t = (int)(g - (long)s * Q) * TPW + team;   // document within the slice
         const long ld = (long)s * kSlice + t;                  // local document
         const bool has = ld < a.N;
-        const int sbeg = __ldg(a.slice_ptr + s);
-        const int Ls = (__ldg(a.slice_ptr + s + 1) - sbeg) / kSlice;
+        const int sbeg = nb;
+        const int Ls = (ne - nb) / kSlice;
         const int2 *ent = a.slice_nz + sbeg + t;
+        // The next group: its bounds now, its u_j (and, below, its first entries)
+        // into L2 while this group runs.
+        const long g2 = g + nwarps;
+        const int s2 = (int)(g2 / Q);
+        const int t2 = (int)(g2 - (long)s2 * Q) * TPW;
+        if (g2 < n_groups) {
+            nb = __ldg(a.slice_ptr + s2);
+            ne = __ldg(a.slice_ptr + s2 + 1);
+            const long ld2 = (long)s2 * kSlice + t2 + team;
+            if (kDots && !a.first && ld2 < a.N) prefetch_l2(a.u + ld2 * VRP + tl * P);
+        }
 
-        float u[P];
+        // u_j's values of this lane as pairs (the operands of the packed FMA)
+        float2 u[P / 2];
         if constexpr (kDots) {
             if (a.first) {
 #pragma unroll
-                for (int p = 0; p < P; ++p) u[p] = has && tl * P + p < vr ? u0 : 0.f;
+                for (int p = 0; p < P / 2; ++p)
+                    u[p] = make_float2(has && tl * P + 2 * p < vr ? u0 : 0.f, has && tl * P + 2 * p + 1 < vr ? u0 : 0.f);
             } else if (has) {
-                load_floats<P>(a.u + ld * VRP + tl * P, u);
+                const float4 *src = reinterpret_cast<const float4 *>(a.u + ld * VRP + tl * P);
+#pragma unroll
+                for (int i = 0; i < P / 4; ++i) {
+                    const float4 f = src[i];
+                    u[2 * i] = make_float2(f.x, f.y);
+                    u[2 * i + 1] = make_float2(f.z, f.w);
+                }
             } else {
 #pragma unroll
-                for (int p = 0; p < P; ++p) u[p] = 0.f;
+                for (int p = 0; p < P / 2; ++p) u[p] = make_float2(0.f, 0.f);
             }
         }
         float2 acc[P / 2];
@@ -134,52 +191,41 @@ __global__ void __launch_bounds__(kWalk3Threads) k_walk3(IterArgs a) {
         for (int p = 0; p < P / 2; ++p) acc[p] = make_float2(0.f, 0.f);
         double dist = 0.0;
 
-        // entries of the first group; the next group's are fetched while this one runs
-        int2 e[EPL];
-        float ev[EPL];
+        // Every lane reads its document's entries itself: the teams of a warp walk
+        // consecutive documents of the slice, so their i-th entries are adjacent
+        // and one load instruction serves the warp.  The next batch's entries are
+        // fetched while this one runs.
+        int2 e[RB];
+        float ev[RB];
 #pragma unroll
-        for (int j = 0; j < EPL; ++j) {
-            const int i = j * Q + tl;
-            e[j] = i < Ls ? __ldg(ent + (long)i * kSlice) : make_int2(0, 0);
-            if constexpr (KIND == Kind::Spmm) ev[j] = i < Ls ? __ldg(a.v + sbeg + (long)i * kSlice + t) : 0.f;
+        for (int rr = 0; rr < RB; ++rr) {
+            e[rr] = rr < Ls ? __ldg(ent + (long)rr * kSlice) : make_int2(0, 0);
+            if constexpr (KIND == Kind::Spmm) ev[rr] = rr < Ls ? __ldg(a.v + sbeg + (long)rr * kSlice + t) : 0.f;
         }
-        for (int i0 = 0; i0 < Ls; i0 += ROWS) {
-            int2 en[EPL];
-            float evn[EPL];
+        for (int i0 = 0; i0 < Ls; i0 += RB) {
+            int2 en[RB];
+            float evn[RB];
 #pragma unroll
-            for (int j = 0; j < EPL; ++j) {
-                const int i = i0 + ROWS + j * Q + tl;
-                en[j] = i < Ls ? __ldg(ent + (long)i * kSlice) : make_int2(0, 0);
-                if constexpr (KIND == Kind::Spmm)
-                    evn[j] = i < Ls ? __ldg(a.v + sbeg + (long)i * kSlice + t) : 0.f;
+            for (int rr = 0; rr < RB; ++rr) {
+                const int i = i0 + RB + rr;
+                en[rr] = i < Ls ? __ldg(ent + (long)i * kSlice) : make_int2(0, 0);
+                if constexpr (KIND == Kind::Spmm) evn[rr] = i < Ls ? __ldg(a.v + sbeg + (long)i * kSlice + t) : 0.f;
             }
-#pragma unroll
-            for (int b = 0; b < ROWS / RB; ++b) {
+#pragma unroll 1
+            for (int once = 0; once < 1; ++once) {   // `continue` ends the batch early
                 int wv[RB];
                 float cv[RB], tv[RB];
 #pragma unroll
                 for (int rr = 0; rr < RB; ++rr) {
-                    const int ri = b * RB + rr, j = ri / Q, q = ri % Q;
-                    if constexpr (Q == 1) {
-                        wv[rr] = e[j].x;
-                        cv[rr] = __int_as_float(e[j].y);
-                        if constexpr (KIND == Kind::Spmm) tv[rr] = ev[j];
-                    } else {
-                        wv[rr] = __shfl_sync(kFull, e[j].x, lead + q);
-                        cv[rr] = __shfl_sync(kFull, __int_as_float(e[j].y), lead + q);
-                        if constexpr (KIND == Kind::Spmm) tv[rr] = __shfl_sync(kFull, ev[j], lead + q);
-                    }
+                    wv[rr] = e[rr].x;
+                    cv[rr] = __int_as_float(e[rr].y);
+                    if constexpr (KIND == Kind::Spmm) tv[rr] = ev[rr];
                 }
+                // padding entries (c = 0) read row 0, always valid: no zero fill, and
+                // their tau is 0
                 uint32_t kw[RB][WORDS];
 #pragma unroll
-                for (int rr = 0; rr < RB; ++rr) {
-                    if (cv[rr] != 0.f) {
-                        load_words<WORDS>(KT + (long)wv[rr] * kRowBytes + lane_off, kw[rr]);
-                    } else {
-#pragma unroll
-                        for (int x = 0; x < WORDS; ++x) kw[rr][x] = 0u;
-                    }
-                }
+                for (int rr = 0; rr < RB; ++rr) load_words<WORDS>(KTl + (long)wv[rr] * kRowBytes, kw[rr]);
                 float tau[RB];
                 if constexpr (KIND == Kind::Spmm) {
 #pragma unroll
@@ -188,10 +234,10 @@ __global__ void __launch_bounds__(kWalk3Threads) k_walk3(IterArgs a) {
                     float d[RB];
 #pragma unroll
                     for (int rr = 0; rr < RB; ++rr) {
-                        float2 d2 = make_float2(0.f, 0.f);
+                        float2 d2 = __fmul2_rn(pair_of<KT_t>(kw[rr], 0), u[0]);
 #pragma unroll
-                        for (int p = 0; p < P / 2; ++p)
-                            d2 = __ffma2_rn(pair_of<KT_t>(kw[rr], p), make_float2(u[2 * p], u[2 * p + 1]), d2);
+                        for (int p = 1; p < P / 2; ++p)
+                            d2 = __ffma2_rn(pair_of<KT_t>(kw[rr], p), u[p], d2);
                         d[rr] = d2.x + d2.y;
                     }
                     float dm[KIND == Kind::Final ? RB : 1];
@@ -199,16 +245,11 @@ __global__ void __launch_bounds__(kWalk3Threads) k_walk3(IterArgs a) {
                     if constexpr (KIND == Kind::Final) {
 #pragma unroll
                         for (int rr = 0; rr < RB; ++rr) {
-                            if (cv[rr] != 0.f) {
-                                load_words<WORDS>(KMT + (long)wv[rr] * kRowBytes + lane_off, mw[rr]);
-                            } else {
+                            load_words<WORDS>(KMTl + (long)wv[rr] * kRowBytes, mw[rr]);
+                            float2 m2 = __fmul2_rn(pair_of<KT_t>(mw[rr], 0), u[0]);
 #pragma unroll
-                                for (int x = 0; x < WORDS; ++x) mw[rr][x] = 0u;
-                            }
-                            float2 m2 = make_float2(0.f, 0.f);
-#pragma unroll
-                            for (int p = 0; p < P / 2; ++p)
-                                m2 = __ffma2_rn(pair_of<KT_t>(mw[rr], p), make_float2(u[2 * p], u[2 * p + 1]), m2);
+                            for (int p = 1; p < P / 2; ++p)
+                                m2 = __ffma2_rn(pair_of<KT_t>(mw[rr], p), u[p], m2);
                             dm[rr] = m2.x + m2.y;
                         }
                     }
@@ -220,10 +261,16 @@ __global__ void __launch_bounds__(kWalk3Threads) k_walk3(IterArgs a) {
                             if constexpr (KIND == Kind::Final) dm[rr] += __shfl_xor_sync(kFull, dm[rr], o);
                         }
                     }
+                    if constexpr (KIND == Kind::Final) {
+#pragma unroll
+                        for (int rr = 0; rr < RB; ++rr) tau[rr] = cv[rr] * (dm[rr] / d[rr]);
+                    } else {
+#pragma unroll
+                        for (int rr = 0; rr < RB; ++rr) tau[rr] = cv[rr] * rcp_approx(d[rr]);
+                    }
                     bool tiny = false;
 #pragma unroll
                     for (int rr = 0; rr < RB; ++rr) tiny |= cv[rr] != 0.f && !(d[rr] >= 0x1p-100f);
-                    double fix[RB];
                     unsigned fixed = 0;
                     if (__any_sync(kFull, tiny)) {
                         SWMD_COLD_PATH();
@@ -235,10 +282,10 @@ __global__ void __launch_bounds__(kWalk3Threads) k_walk3(IterArgs a) {
 #pragma unroll
                             for (int p = 0; p < P / 2; ++p) {
                                 const float2 k2 = pair_of<KT_t>(kw[rr], p);
-                                sd += (double)k2.x * u[2 * p] + (double)k2.y * u[2 * p + 1];
+                                sd += (double)k2.x * u[p].x + (double)k2.y * u[p].y;
                                 if constexpr (KIND == Kind::Final) {
                                     const float2 m2 = pair_of<KT_t>(mw[rr], p);
-                                    md += (double)m2.x * u[2 * p] + (double)m2.y * u[2 * p + 1];
+                                    md += (double)m2.x * u[p].x + (double)m2.y * u[p].y;
                                 }
                             }
 #pragma unroll
@@ -247,49 +294,60 @@ __global__ void __launch_bounds__(kWalk3Threads) k_walk3(IterArgs a) {
                                 if constexpr (KIND == Kind::Final) md += __shfl_xor_sync(kFull, md, o);
                             }
                             if (cv[rr] != 0.f && !(d[rr] >= 0x1p-100f)) {
-                                if constexpr (KIND == Kind::Final) fix[rr] = (double)cv[rr] * (md / sd);
-                                else fix[rr] = sd > 0.0 ? (double)cv[rr] / sd : 0.0;
+                                if constexpr (KIND == Kind::Final) {
+                                    if (tl == (rr & (Q - 1))) dist += (double)cv[rr] * (md / sd);
+                                }
+                                else tau[rr] = sd > 0.0 ? (float)((double)cv[rr] / sd) : 0.f;
                                 fixed |= 1u << rr;
                                 if (tl == 0) atomicOr(status, sd > 0.0 ? ST_GUARD : ST_NUMERIC);
                             }
                         }
                     }
                     if constexpr (KIND == Kind::Final) {
+                        // Every lane holds every row's contribution; lane tl adds rows
+                        // tl, tl + Q, ... in FP64, one FP64 add per row and warp (the
+                        // FP64 pipe is narrow), and the team's sums are combined at the end.
 #pragma unroll
-                        for (int rr = 0; rr < RB; ++rr)
-                            if (cv[rr] != 0.f)
-                                dist += (fixed >> rr & 1u) ? fix[rr] : (double)(cv[rr] * (dm[rr] / d[rr]));
+                        for (int r0 = 0; r0 < RB; r0 += Q) {
+                            float mine = 0.f;
+#pragma unroll
+                            for (int q = 0; q < Q && r0 + q < RB; ++q) {
+                                const int rr = r0 + q;
+                                const float c_rr = cv[rr] != 0.f && !(fixed >> rr & 1u) ? tau[rr] : 0.f;
+                                mine = tl == q ? c_rr : mine;
+                            }
+                            dist += (double)mine;
+                        }
                         continue;
                     } else {
 #pragma unroll
-                        for (int rr = 0; rr < RB; ++rr) {
-                            tau[rr] = cv[rr] != 0.f ? __fdividef(cv[rr], d[rr]) : 0.f;
-                            if (fixed >> rr & 1u) tau[rr] = (float)fix[rr];
-                        }
+                        for (int rr = 0; rr < RB; ++rr) tau[rr] = cv[rr] != 0.f ? tau[rr] : 0.f;
                     }
                     if constexpr (KIND == Kind::Sddmm) {
 #pragma unroll
                         for (int rr = 0; rr < RB; ++rr) {
-                            const int ri = b * RB + rr, q = ri % Q;
-                            const int i = i0 + ri;
-                            if (tl == q && cv[rr] != 0.f) a.v[sbeg + (long)i * kSlice + t] = tau[rr];
+                            const int i = i0 + rr;
+                            if (tl == (rr & (Q - 1)) && cv[rr] != 0.f) a.v[sbeg + (long)i * kSlice + t] = tau[rr];
                         }
                         continue;
                     }
                 }
-                // acc += tau K^T[w] over this lane's P values
+                // acc += tau K^T[w] over this lane's P values (16-bit rows are widened
+                // again here rather than kept widened across the batch)
 #pragma unroll
                 for (int rr = 0; rr < RB; ++rr) {
                     const float2 t2 = make_float2(tau[rr], tau[rr]);
 #pragma unroll
-                    for (int p = 0; p < P / 2; ++p) acc[p] = __ffma2_rn(t2, pair_of<KT_t>(kw[rr], p), acc[p]);
+                    for (int p = 0; p < P / 2; ++p) acc[p] = __ffma2_rn(t2, pair_again<KT_t>(kw[rr], p), acc[p]);
                 }
             }
 #pragma unroll
-            for (int j = 0; j < EPL; ++j) {
-                e[j] = en[j];
-                if constexpr (KIND == Kind::Spmm) ev[j] = evn[j];
+            for (int rr = 0; rr < RB; ++rr) {
+                e[rr] = en[rr];
+                if constexpr (KIND == Kind::Spmm) ev[rr] = evn[rr];
             }
+            if (i0 == 0 && g2 < n_groups && lane < (ne - nb) / kSlice)
+                prefetch_l2(a.slice_nz + nb + (long)lane * kSlice + t2);   // the next group's row `lane`
         }
 
         if constexpr (KIND == Kind::Fused || KIND == Kind::Spmm) {
@@ -300,8 +358,8 @@ __global__ void __launch_bounds__(kWalk3Threads) k_walk3(IterArgs a) {
 #pragma unroll
                 for (int p = 0; p < P / 2; ++p) {
                     const int k = tl * P + 2 * p;
-                    nu[2 * p] = k < vr ? __fdividef(rr[2 * p], acc[p].x) : 0.f;
-                    nu[2 * p + 1] = k + 1 < vr ? __fdividef(rr[2 * p + 1], acc[p].y) : 0.f;
+                    nu[2 * p] = k < vr ? rr[2 * p] * rcp_approx(acc[p].x) : 0.f;
+                    nu[2 * p + 1] = k + 1 < vr ? rr[2 * p + 1] * rcp_approx(acc[p].y) : 0.f;
                     bad |= !(nu[2 * p] < INFINITY) || !(nu[2 * p + 1] < INFINITY);
                 }
                 if (bad) atomicOr(status, ST_NUMERIC);
@@ -312,7 +370,8 @@ __global__ void __launch_bounds__(kWalk3Threads) k_walk3(IterArgs a) {
                         make_float4(nu[4 * i], nu[4 * i + 1], nu[4 * i + 2], nu[4 * i + 3]);
             }
         } else if constexpr (KIND == Kind::Final) {
-            // every lane of the team holds the same sum (the dots were all-reduced)
+#pragma unroll
+            for (int o = 1; o < Q; o <<= 1) dist += __shfl_xor_sync(kFull, dist, o);
             if (has && tl == 0) {
                 if (!(fabs(dist) < INFINITY)) atomicOr(status, ST_NUMERIC);
                 out[__ldg(a.doc_orig + ld)] = dist;
@@ -321,12 +380,12 @@ __global__ void __launch_bounds__(kWalk3Threads) k_walk3(IterArgs a) {
     }
 }
 
-template <int VRP, class KT_t, Kind KIND>
-cudaError_t run_walk3(const IterArgs &a, int sms, cudaStream_t s) {
-    auto kern = k_walk3<VRP, KT_t, KIND>;
+template <int VRP, class KT_t, Kind KIND, int NT, int MINB>
+cudaError_t run_walk3_v(const IterArgs &a, int sms, cudaStream_t s) {
+    auto kern = k_walk3<VRP, KT_t, KIND, NT, MINB>;
     static int per_sm = 0;
     if (per_sm <= 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWalk3Threads, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, 0) != cudaSuccess ||
             per_sm < 1) {
             (void)cudaGetLastError();
             per_sm = 1;
@@ -334,12 +393,22 @@ cudaError_t run_walk3(const IterArgs &a, int sms, cudaStream_t s) {
     }
     constexpr int Q = W3<VRP, KT_t>::Q;
     const long groups = (long)a.n_slices * Q;
-    const long need = (groups * 32 + kWalk3Threads - 1) / kWalk3Threads;
+    const long need = (groups * 32 + NT - 1) / NT;
     long blocks = (long)sms * per_sm;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    if (a.N > 0) kern<<<(unsigned)blocks, kWalk3Threads, 0, s>>>(a);
+    if (a.N > 0) kern<<<(unsigned)blocks, NT, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+// Launch shape: 128-thread blocks with a register cap that lets 4 blocks share an
+// SM (3 for FP16 rows, whose widening takes more registers); the final step, with a
+// second row per nonzero, 3 (FP32) or 2.
+template <int VRP, class KT_t, Kind KIND>
+cudaError_t run_walk3(const IterArgs &a, int sms, cudaStream_t s) {
+    constexpr bool f32 = sizeof(KT_t) == 4, bf = std::is_same<KT_t, __nv_bfloat16>::value;
+    constexpr int MINB = KIND == Kind::Final ? (f32 ? 3 : 2) : (f32 || bf ? 4 : 3);
+    return run_walk3_v<VRP, KT_t, KIND, 128, MINB>(a, sms, s);
 }
 
 template <class KT_t, Kind KIND>
