@@ -86,8 +86,10 @@ int alloc_slot(swmd_corpus *c, Slot &s, int max_vr, int kprec, bool with_v) {
     if ((rc = dev_alloc(&kmt, (size_t)std::max(c->Vu, 1) * vrp * kb, &s.bytes))) return rc;
     s.KMT = kmt;
     if ((rc = dev_alloc(&s.u, (size_t)std::max(c->Nl, 1) * vrp, &s.bytes))) return rc;
-    if (with_v && (rc = dev_alloc(&s.v, (size_t)std::max<int64_t>(std::max(c->nnz, c->slice_total), 1), &s.bytes)))
-        return rc;
+    if (with_v) {
+        s.v_elems = std::max<int64_t>(std::max(c->nnz, c->slice_total), 1);
+        if ((rc = dev_alloc(&s.v, (size_t)s.v_elems, &s.bytes))) return rc;
+    }
     if ((rc = dev_alloc(&s.q_ids, vrp, &s.bytes))) return rc;
     if ((rc = dev_alloc(&s.r, vrp, &s.bytes))) return rc;
     if ((rc = dev_alloc(&s.qp, 1, &s.bytes))) return rc;
@@ -331,6 +333,8 @@ static int launch_sequence(swmd_corpus *c, Slot &s, Mapping m, int t, int path, 
         ra.it.first = 1;
         return run_resident(c, ra, m, kprec, st);
     }
+    if (path == SWMD_PATH_PLAIN && (!s.v || s.v_elems < std::max(c->nnz, c->slice_total)))
+        return set_error(SWMD_EINVAL, "plain path: SDDMM output buffer missing or too small");
     for (int it = 0; it < t; ++it) {
         ia.first = it == 0;
         if (path == SWMD_PATH_PLAIN) {
@@ -558,10 +562,12 @@ int swmd_create_corpus(int32_t V, int32_t N, int64_t nnz, const int64_t *row_ptr
 
     // ---- the sliced copy: slices of 32 consecutive documents, entry (i, t) at
     // slice_ptr[s] + 32 i + t, padded with (0, c = 0) to the slice's longest document
+    // rounded up to a multiple of kSliceRows rows
     const int n_slices = (Nl + kSliceDocs - 1) / kSliceDocs;
     std::vector<int32_t> sptr((size_t)n_slices + 1, 0);
     for (int s = 0; s < n_slices; ++s) {
-        const int64_t next = (int64_t)sptr[s] + (int64_t)kSliceDocs * (dptr[s * kSliceDocs + 1] - dptr[s * kSliceDocs]);
+        const int64_t rows = (dptr[s * kSliceDocs + 1] - dptr[s * kSliceDocs] + kSliceRows - 1) / kSliceRows * kSliceRows;
+        const int64_t next = (int64_t)sptr[s] + (int64_t)kSliceDocs * rows;
         if (next > INT32_MAX) return set_error(SWMD_EINVAL, "swmd_create_corpus: too many nonzeros");
         sptr[s + 1] = (int32_t)next;
     }
@@ -841,11 +847,14 @@ int swmd_step_iterate(swmd_corpus *c, int32_t v_r, int32_t n_iter, int32_t first
     Slot &s = c->main;
     if (path == SWMD_PATH_PLAIN && !s.v) {
         int64_t extra = 0;
-        if ((rc = dev_alloc(&s.v, (size_t)std::max<int64_t>(c->nnz, 1), &extra))) return rc;
+        s.v_elems = std::max<int64_t>(std::max(c->nnz, c->slice_total), 1);
+        if ((rc = dev_alloc(&s.v, (size_t)s.v_elems, &extra))) return rc;
         s.bytes += extra;
         for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
         c->graphs.clear();
     }
+    if (path == SWMD_PATH_PLAIN && s.v_elems < std::max(c->nnz, c->slice_total))
+        return set_error(SWMD_EINVAL, "swmd_step_iterate: SDDMM output buffer too small");
     const Mapping m = walk_mapping(c, slot_vrp(c, s, v_r), path);
     IterArgs ia = iter_args(c, s);
     for (int it = 0; it < n_iter; ++it) {

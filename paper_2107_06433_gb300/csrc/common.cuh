@@ -41,8 +41,10 @@ struct QParams {
     int *status;     // status word of this query
 };
 
-// Documents per slice of the sliced nonzero layout.
+// Documents per slice of the sliced nonzero layout, and the multiple its row
+// count is padded to (so a walk takes rows in fours without bounds checks).
 constexpr int kSliceDocs = 32;
+constexpr int kSliceRows = 4;
 
 struct IterArgs {
     const int *doc_ptr;

@@ -38,7 +38,8 @@ struct Slot {
     void *KT = nullptr;
     void *KMT = nullptr;
     float *u = nullptr;
-    float *v = nullptr;   // plain path only: SDDMM output [nnz]
+    float *v = nullptr;   // plain path only: SDDMM output at the sliced positions
+    int64_t v_elems = 0;  // capacity of v (checked against the corpus's slice_total)
     int *q_ids = nullptr; // [vrp_cap]
     float *r = nullptr;   // [vrp_cap], zero padded
     QParams *qp = nullptr;

@@ -176,7 +176,8 @@ int launch_on_slot(swmd_server *S, ServerSlot &sl) {
     sl.ws.KT = carve(kbytes);
     sl.ws.KMT = carve(kbytes);
     sl.ws.u = path != SWMD_PATH_RESIDENT ? (float *)carve((size_t)c->Nl * m.vrp * sizeof(float)) : nullptr;
-    sl.ws.v = path == SWMD_PATH_PLAIN ? (float *)carve((size_t)std::max(c->nnz, c->slice_total) * sizeof(float)) : nullptr;
+    sl.ws.v_elems = path == SWMD_PATH_PLAIN ? std::max(c->nnz, c->slice_total) : 0;
+    sl.ws.v = path == SWMD_PATH_PLAIN ? (float *)carve((size_t)sl.ws.v_elems * sizeof(float)) : nullptr;
     std::memcpy(sl.h_q, R.ids.data(), sizeof(int32_t) * R.vr);
     std::memcpy(sl.h_r, R.r.data(), sizeof(float) * R.vr);
     SWMD_CK(cudaMemcpyAsync(sl.ws.q_in, sl.h_q, sizeof(int32_t) * R.vr, cudaMemcpyHostToDevice, sl.stream));

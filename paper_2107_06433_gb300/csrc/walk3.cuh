@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
         const int sbeg = nb;
         const int Ls = (ne - nb) / kSlice;
         const int2 *ent = a.slice_nz + sbeg + t;
+        static_assert(kSliceRows % C::RB == 0, "slices hold whole batches");
         // The next group: its bounds now, its u_j (and, below, its first entries)
         // into L2 while this group runs.
         const long g2 = g + nwarps;
@@ -195,29 +196,30 @@ __global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
         // consecutive documents of the slice, so their i-th entries are adjacent
         // and one load instruction serves the warp.  The next batch's entries are
         // fetched while this one runs.
-        int2 e[RB];
-        float ev[RB];
+        // (a slice's row count is a multiple of RB: whole batches, no bounds checks)
+        const float *vent = a.v + sbeg + t;
+        int2 e[RB], en[RB];
+        float ev[RB], evn[RB];
 #pragma unroll
         for (int rr = 0; rr < RB; ++rr) {
-            e[rr] = rr < Ls ? __ldg(ent + (long)rr * kSlice) : make_int2(0, 0);
-            if constexpr (KIND == Kind::Spmm) ev[rr] = rr < Ls ? __ldg(a.v + sbeg + (long)rr * kSlice + t) : 0.f;
+            e[rr] = __ldg(ent + rr * kSlice);
+            if constexpr (KIND == Kind::Spmm) ev[rr] = __ldg(vent + rr * kSlice);
         }
         for (int i0 = 0; i0 < Ls; i0 += RB) {
-            int2 en[RB];
-            float evn[RB];
+            if (i0 + RB < Ls) {
+                ent += RB * kSlice;
+                if constexpr (KIND == Kind::Spmm) vent += RB * kSlice;
 #pragma unroll
-            for (int rr = 0; rr < RB; ++rr) {
-                const int i = i0 + RB + rr;
-                en[rr] = i < Ls ? __ldg(ent + (long)i * kSlice) : make_int2(0, 0);
-                if constexpr (KIND == Kind::Spmm) evn[rr] = i < Ls ? __ldg(a.v + sbeg + (long)i * kSlice + t) : 0.f;
+                for (int rr = 0; rr < RB; ++rr) {
+                    en[rr] = __ldg(ent + rr * kSlice);
+                    if constexpr (KIND == Kind::Spmm) evn[rr] = __ldg(vent + rr * kSlice);
+                }
             }
 #pragma unroll 1
             for (int once = 0; once < 1; ++once) {   // `continue` ends the batch early
-                int wv[RB];
                 float cv[RB], tv[RB];
 #pragma unroll
                 for (int rr = 0; rr < RB; ++rr) {
-                    wv[rr] = e[rr].x;
                     cv[rr] = __int_as_float(e[rr].y);
                     if constexpr (KIND == Kind::Spmm) tv[rr] = ev[rr];
                 }
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
                 // their tau is 0
                 uint32_t kw[RB][WORDS];
 #pragma unroll
-                for (int rr = 0; rr < RB; ++rr) load_words<WORDS>(KTl + (long)wv[rr] * kRowBytes, kw[rr]);
+                for (int rr = 0; rr < RB; ++rr) load_words<WORDS>(KTl + (long)e[rr].x * kRowBytes, kw[rr]);
                 float tau[RB];
                 if constexpr (KIND == Kind::Spmm) {
 #pragma unroll
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
                     if constexpr (KIND == Kind::Final) {
 #pragma unroll
                         for (int rr = 0; rr < RB; ++rr) {
-                            load_words<WORDS>(KMTl + (long)wv[rr] * kRowBytes, mw[rr]);
+                            load_words<WORDS>(KMTl + (long)e[rr].x * kRowBytes, mw[rr]);
                             float2 m2 = __fmul2_rn(pair_of<KT_t>(mw[rr], 0), u[0]);
 #pragma unroll
                             for (int p = 1; p < P / 2; ++p)
@@ -263,7 +265,7 @@ __global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
                     }
                     if constexpr (KIND == Kind::Final) {
 #pragma unroll
-                        for (int rr = 0; rr < RB; ++rr) tau[rr] = cv[rr] * (dm[rr] / d[rr]);
+                        for (int rr = 0; rr < RB; ++rr) tau[rr] = cv[rr] * (dm[rr] * rcp_approx(d[rr]));
                     } else {
 #pragma unroll
                         for (int rr = 0; rr < RB; ++rr) tau[rr] = cv[rr] * rcp_approx(d[rr]);
@@ -334,11 +336,13 @@ __global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
                 }
                 // acc += tau K^T[w] over this lane's P values (16-bit rows are widened
                 // again here rather than kept widened across the batch)
+                if constexpr (KIND == Kind::Fused || KIND == Kind::Spmm) {
 #pragma unroll
-                for (int rr = 0; rr < RB; ++rr) {
-                    const float2 t2 = make_float2(tau[rr], tau[rr]);
+                    for (int rr = 0; rr < RB; ++rr) {
+                        const float2 t2 = make_float2(tau[rr], tau[rr]);
 #pragma unroll
-                    for (int p = 0; p < P / 2; ++p) acc[p] = __ffma2_rn(t2, pair_again<KT_t>(kw[rr], p), acc[p]);
+                        for (int p = 0; p < P / 2; ++p) acc[p] = __ffma2_rn(t2, pair_again<KT_t>(kw[rr], p), acc[p]);
+                    }
                 }
             }
 #pragma unroll
