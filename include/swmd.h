@@ -60,17 +60,23 @@ extern "C" {
  *             formulation of Section III-B4 (writes v, then reads it back).
  *   RESIDENT: all t iterations and the final step of a document in one launch,
  *             u held on chip; legal because the documents (columns of c) are
- *             independent problems in Algorithm 1. */
+ *             independent problems in Algorithm 1.
+ *   AUTO:     RESIDENT or FUSED for each query: the choice swmd_autotune measured
+ *             for its v_r, else RESIDENT for corpora under 20,000 documents or v_r
+ *             up to 24, FUSED otherwise (on large corpora the per-iteration walk
+ *             is faster for wide queries).  The choice depends only on v_r and
+ *             the tuning, so a query's result is the same alone, batched or served. */
 #define SWMD_PATH_FUSED 0
 #define SWMD_PATH_PLAIN 1
 #define SWMD_PATH_RESIDENT 2
+#define SWMD_PATH_AUTO 3
 
 typedef struct swmd_corpus swmd_corpus;
 typedef struct swmd_server swmd_server;
 
 typedef struct swmd_options {
     int32_t k_precision;   /* SWMD_K_*; default SWMD_K_FP32 */
-    int32_t path;          /* SWMD_PATH_*; default SWMD_PATH_RESIDENT */
+    int32_t path;          /* SWMD_PATH_*; default SWMD_PATH_AUTO */
     int32_t use_graph;     /* 1: replay the query's launches as a captured CUDA graph (default 1) */
     int32_t column_shift;  /* 1: K'[k,w] = exp(-lambda (M[k,w] - min_k M[k,w])), an exact
                               rescaling of the columns of K (default 1) */
@@ -261,6 +267,10 @@ SWMD_API int swmd_step_resident(swmd_corpus *corpus, int32_t v_r, int32_t max_it
  * lane one float4 slice of every row (the per-iteration paths' default). */
 SWMD_API int swmd_get_mapping(swmd_corpus *corpus, int32_t v_r, int32_t path, int32_t *out3);
 
+/* The concrete path (SWMD_PATH_RESIDENT, FUSED or PLAIN) a query of v_r words
+ * takes on this corpus: the corpus's path, or SWMD_PATH_AUTO's choice. */
+SWMD_API int swmd_resolve_path(swmd_corpus *corpus, int32_t v_r, int32_t *out_path);
+
 /* Copies a workspace array to host memory for inspection (tests):
  *   what 0: K^T  [V_used][v_r] as float (FP32/BF16/FP16 widened)
  *   what 1: KM^T [V_used][v_r] as float
@@ -278,17 +288,22 @@ typedef struct swmd_tune_result {
     float default_ms;      /* whole-query time with the settings before tuning */
     float best_ms;         /* whole-query time with the chosen settings */
     int32_t candidates;    /* configurations timed */
-    int32_t reserved;
+    int32_t path;          /* the path chosen for this v_r (SWMD_PATH_RESIDENT or, under
+                              SWMD_PATH_AUTO, SWMD_PATH_FUSED when that was faster) */
 } swmd_tune_result;
 
 /* Times the resident-path kernels of this corpus for queries of v_r words over
  * the candidate lane mappings (register solver rows per lane; shared-memory
  * solver; threads per word of the cost kernel), each `reps` times (>= 1) with
- * CUDA events on a query of v_r distinct words drawn from the corpus, and keeps
- * the fastest for this layout: later queries with the same VRP and K precision
- * use it unless swmd_options fixes the field.  Synchronous; allocates nothing
- * beyond the corpus's workspace.  The paper has no counterpart (it tuned by hand
- * for Xeon and PIUMA, Sections IV-V). */
+ * CUDA events on a query of v_r distinct words, and keeps the fastest for this
+ * layout: later queries with the same VRP and K precision use it unless
+ * swmd_options fixes the field.  On a corpus with SWMD_PATH_AUTO it also times the
+ * per-iteration fused path and records, for this v_r, whichever path was faster.
+ * The corpus's path must be SWMD_PATH_RESIDENT or SWMD_PATH_AUTO.  Synchronous;
+ * allocates nothing beyond the corpus's workspace; call it before serving from the
+ * corpus (a running server reads the tuning).  A tuned setting may change the
+ * rounding of later results (within the FP32 tolerance), never their meaning.  The
+ * paper has no counterpart (it tuned by hand for Xeon and PIUMA, Sections IV-V). */
 SWMD_API int swmd_autotune(swmd_corpus *corpus, int32_t v_r, int32_t reps, swmd_tune_result *out);
 
 /* ------------------------------------------------------------------ batch */

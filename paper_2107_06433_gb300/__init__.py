@@ -21,9 +21,10 @@ LIB_PATH = os.path.join(_HERE, "_build", "libswmd.so")
 
 SWMD_OK, SWMD_EINVAL, SWMD_ENOMEM, SWMD_ECUDA, SWMD_ETIMEDOUT, SWMD_ENUMERIC, SWMD_ESTOPPED = range(7)
 K_FP32, K_BF16, K_FP16 = 0, 1, 2
-PATH_FUSED, PATH_PLAIN, PATH_RESIDENT = 0, 1, 2
+PATH_FUSED, PATH_PLAIN, PATH_RESIDENT, PATH_AUTO = 0, 1, 2, 3
 _KPREC = {"fp32": K_FP32, "bf16": K_BF16, "fp16": K_FP16}
-_PATHS = {"fused": PATH_FUSED, "plain": PATH_PLAIN, "resident": PATH_RESIDENT}
+_PATHS = {"fused": PATH_FUSED, "plain": PATH_PLAIN, "resident": PATH_RESIDENT, "auto": PATH_AUTO}
+_PATH_NAMES = {v: k for k, v in _PATHS.items()}
 
 
 class SwmdError(RuntimeError):
@@ -67,7 +68,7 @@ class swmd_tune_result(ctypes.Structure):
     _fields_ = [("vrp", ctypes.c_int32), ("solver", ctypes.c_int32),
                 ("nnz_per_lane", ctypes.c_int32), ("cost_split", ctypes.c_int32),
                 ("default_ms", ctypes.c_float), ("best_ms", ctypes.c_float),
-                ("candidates", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("candidates", ctypes.c_int32), ("path", ctypes.c_int32)]
 
 
 _lib = None
@@ -97,6 +98,7 @@ _SIGS = {
     "swmd_debug_read": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P]),
     "swmd_query_batch": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P, ctypes.c_int32, P]),
     "swmd_autotune": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P]),
+    "swmd_resolve_path": (ctypes.c_int, [P, ctypes.c_int32, P]),
     "swmd_default_serve_config": (None, [P]),
     "swmd_serve_start": (ctypes.c_int, [P, P, P]),
     "swmd_serve_submit": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.c_float, ctypes.c_int32,
@@ -299,6 +301,13 @@ def swmd_get_mapping(corpus: Corpus, v_r: int, path="resident"):
     return int(out[0]), int(out[1]), int(out[2])
 
 
+def swmd_resolve_path(corpus: Corpus, v_r: int) -> str:
+    """The path ("resident", "fused" or "plain") a query of v_r words takes."""
+    out = ctypes.c_int32()
+    _err(lib().swmd_resolve_path(corpus.handle, int(v_r), ctypes.byref(out)), "swmd_resolve_path")
+    return _PATH_NAMES[out.value]
+
+
 def swmd_debug_read(corpus: Corpus, what: str, v_r: int = 0) -> np.ndarray:
     info = corpus.info()
     code = {"KT": 0, "KMT": 1, "u": 2, "used": 3}[what]
@@ -336,7 +345,7 @@ def swmd_autotune(corpus: Corpus, v_r: int, reps: int = 5) -> dict:
     res = swmd_tune_result()
     _err(lib().swmd_autotune(corpus.handle, int(v_r), int(reps), ctypes.byref(res)),
          "swmd_autotune")
-    return {f: getattr(res, f) for f, _ in swmd_tune_result._fields_ if f != "reserved"}
+    return {f: getattr(res, f) for f, _ in swmd_tune_result._fields_}
 
 
 class Server:

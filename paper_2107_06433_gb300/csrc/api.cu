@@ -149,6 +149,13 @@ Mapping walk_mapping(swmd_corpus *c, int vrp, int path) {
     return Mapping{vrp, 1, 4};
 }
 
+int resolve_path(swmd_corpus *c, int vr) {
+    if (c->opt.path != SWMD_PATH_AUTO) return c->opt.path;
+    auto it = c->tuned_path.find(std::make_pair(vr, c->opt.k_precision));
+    if (it != c->tuned_path.end()) return it->second;
+    return (c->Nl < kAutoResidentDocs || vr <= kAutoResidentVr) ? SWMD_PATH_RESIDENT : SWMD_PATH_FUSED;
+}
+
 Mapping choose_mapping(swmd_corpus *c, int vr, int path) {
     return walk_mapping(c, layout_vrp(c, vr, path), path);
 }
@@ -353,7 +360,7 @@ static int launch_sequence(swmd_corpus *c, Slot &s, Mapping m, int t, int path, 
 int enqueue_query(swmd_corpus *c, Slot &s, const int *d_ids, const float *d_r, int vr,
                   float lambda, int t, double *d_out, int *d_status, cudaStream_t st,
                   bool allow_graph) {
-    const int path = c->opt.path;
+    const int path = resolve_path(c, vr);
     const int kprec = c->opt.k_precision;
     if (!s.external && (s.kprec != kprec || (path == SWMD_PATH_PLAIN && !s.v))) {
         // buffers move: every captured graph of this corpus is stale
@@ -404,7 +411,7 @@ void swmd_default_options(swmd_options *opt) {
     if (!opt) return;
     std::memset(opt, 0, sizeof *opt);
     opt->k_precision = SWMD_K_FP32;
-    opt->path = SWMD_PATH_RESIDENT;
+    opt->path = SWMD_PATH_AUTO;
     opt->use_graph = 1;
     opt->column_shift = 1;
     opt->max_vr = 128;
@@ -492,7 +499,7 @@ int swmd_create_corpus(int32_t V, int32_t N, int64_t nnz, const int64_t *row_ptr
         return set_error(SWMD_EINVAL, "swmd_create_corpus: NULL input array");
     if (opt.max_vr <= 0) opt.max_vr = 128;
     if (opt.max_vr > 128) return set_error(SWMD_EINVAL, "swmd_create_corpus: max_vr above 128");
-    if (opt.k_precision < 0 || opt.k_precision > 2 || opt.path < 0 || opt.path > 2)
+    if (opt.k_precision < 0 || opt.k_precision > 2 || opt.path < 0 || opt.path > 3)
         return set_error(SWMD_EINVAL, "swmd_create_corpus: bad k_precision or path");
     int b = opt.doc_begin < 0 ? 0 : opt.doc_begin;
     int e = opt.doc_end < 0 ? N : opt.doc_end;
@@ -700,7 +707,7 @@ int swmd_corpus_get_info(const swmd_corpus *c, swmd_corpus_info *out) {
 
 int swmd_corpus_set_options(swmd_corpus *c, const swmd_options *opt) {
     if (!c || !opt) return set_error(SWMD_EINVAL, "swmd_corpus_set_options: NULL argument");
-    if (opt->k_precision < 0 || opt->k_precision > 2 || opt->path < 0 || opt->path > 2)
+    if (opt->k_precision < 0 || opt->k_precision > 2 || opt->path < 0 || opt->path > 3)
         return set_error(SWMD_EINVAL, "swmd_corpus_set_options: bad k_precision or path");
     std::lock_guard<std::mutex> lk(c->mu);
     c->opt.k_precision = opt->k_precision;
@@ -773,7 +780,7 @@ int swmd_query_device(swmd_corpus *c, const int32_t *d_ids, const float *d_r, in
 // VRP of the K^T layout the last swmd_step_cost / query wrote (v_r's default
 // layout for the corpus's path if none yet)
 static int slot_vrp(swmd_corpus *c, Slot &s, int v_r) {
-    return (s.cur_vrp > 0 && s.cur_vr == v_r) ? s.cur_vrp : layout_vrp(c, v_r, c->opt.path);
+    return (s.cur_vrp > 0 && s.cur_vr == v_r) ? s.cur_vrp : layout_vrp(c, v_r, resolve_path(c, v_r));
 }
 
 static IterArgs iter_args(swmd_corpus *c, Slot &s) {
@@ -810,7 +817,7 @@ int swmd_step_cost(swmd_corpus *c, const int32_t *d_ids, const float *d_r, int32
         if ((rc = alloc_slot(c, s, c->opt.max_vr, c->opt.k_precision, c->opt.path == SWMD_PATH_PLAIN)))
             return rc;
     }
-    const Mapping m = choose_mapping(c, v_r, c->opt.path);
+    const Mapping m = choose_mapping(c, v_r, resolve_path(c, v_r));
     s.cur_vrp = m.vrp;
     s.cur_vr = v_r;
     SWMD_CK(launch_prep(s.qp, lambda, v_r, c->V, d_ids, d_r, s.q_ids, s.r, s.vrp_cap, s.out,
@@ -878,7 +885,7 @@ int swmd_step_final(swmd_corpus *c, int32_t v_r, int32_t t0, double *d_out, void
     DeviceGuard guard(c->device);
     cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
     Slot &s = c->main;
-    const Mapping m = walk_mapping(c, slot_vrp(c, s, v_r), c->opt.path);
+    const Mapping m = walk_mapping(c, slot_vrp(c, s, v_r), SWMD_PATH_FUSED);
     IterArgs ia = iter_args(c, s);
     ia.first = t0 ? 1 : 0;
     ia.out = d_out;
@@ -906,10 +913,19 @@ int swmd_get_mapping(swmd_corpus *c, int32_t v_r, int32_t path, int32_t *out3) {
     if (!c || !out3) return set_error(SWMD_EINVAL, "swmd_get_mapping: NULL argument");
     if (v_r < 1 || v_r > c->opt.max_vr) return set_error(SWMD_EINVAL, "swmd_get_mapping: bad v_r");
     std::lock_guard<std::mutex> lk(c->mu);
+    if (path == SWMD_PATH_AUTO) path = resolve_path(c, v_r);
     const Mapping m = choose_mapping(c, v_r, path);
     out3[0] = m.vrp;
     out3[1] = m.q;
     out3[2] = m.p;
+    return SWMD_OK;
+}
+
+int swmd_resolve_path(swmd_corpus *c, int32_t v_r, int32_t *out_path) {
+    if (!c || !out_path) return set_error(SWMD_EINVAL, "swmd_resolve_path: NULL argument");
+    if (v_r < 1 || v_r > c->opt.max_vr) return set_error(SWMD_EINVAL, "swmd_resolve_path: bad v_r");
+    std::lock_guard<std::mutex> lk(c->mu);
+    *out_path = resolve_path(c, v_r);
     return SWMD_OK;
 }
 

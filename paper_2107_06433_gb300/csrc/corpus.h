@@ -104,6 +104,8 @@ struct swmd_corpus {
     std::map<std::tuple<int, int, int>, swmd::Mapping> tuned;  // (vr bucket, path, kprec)
     // autotuned resident-path settings per (VRP, K precision): solver, rows per lane, cost split
     std::map<std::pair<int, int>, std::tuple<int, int, int>> tuned_resident;
+    // autotuned path (RESIDENT or FUSED) per (v_r, K precision), used by SWMD_PATH_AUTO
+    std::map<std::pair<int, int>, int> tuned_path;
     std::mutex mu;                 // serialises use of `main` and the graph cache
 };
 
@@ -113,6 +115,12 @@ int alloc_slot(swmd_corpus *c, Slot &s, int max_vr, int kprec, bool with_v);
 void free_slot(Slot &s);
 Mapping choose_mapping(swmd_corpus *c, int vr, int path);
 int layout_vrp(swmd_corpus *c, int vr, int path);
+// The concrete path a query of vr words takes (resolves SWMD_PATH_AUTO).
+int resolve_path(swmd_corpus *c, int vr);
+// Corpora with fewer documents than this take the resident path under SWMD_PATH_AUTO
+// unless tuned otherwise.
+constexpr int kAutoResidentDocs = 20000;
+constexpr int kAutoResidentVr = 24;
 Mapping walk_mapping(swmd_corpus *c, int vrp, int path);
 // Enqueues a whole query whose ids / r are already in device memory (d_ids,
 // d_r), writing the distances to d_out and the status to d_status.

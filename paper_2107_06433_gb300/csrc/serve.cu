@@ -164,7 +164,7 @@ void finish(swmd_server *S, ServerSlot &sl, int code, const std::string &err) {
 int launch_on_slot(swmd_server *S, ServerSlot &sl) {
     swmd_corpus *c = S->c;
     auto &R = *sl.req;
-    const int path = c->opt.path;
+    const int path = resolve_path(c, R.vr);
     const Mapping m = choose_mapping(c, R.vr, path);
     const size_t kbytes = (size_t)c->Vu * m.vrp * kprec_bytes(c->opt.k_precision);
     char *p = static_cast<char *>(sl.arena_ptr);
@@ -212,8 +212,9 @@ void worker_main(swmd_server *S) {
             for (auto &sl : S->slots) {
                 if (sl.req || S->pending.empty()) continue;
                 auto R = S->pending.front();
-                const Mapping mp = choose_mapping(S->c, R->vr, S->c->opt.path);
-                const size_t need = query_bytes(S->c, mp.vrp, S->c->opt.path);
+                const int rpath = resolve_path(S->c, R->vr);
+                const Mapping mp = choose_mapping(S->c, R->vr, rpath);
+                const size_t need = query_bytes(S->c, mp.vrp, rpath);
                 void *mem = S->arena.alloc(need);
                 if (!mem) break;   // admission waits for memory to free up
                 S->pending.pop_front();
@@ -315,58 +316,40 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
     const int kprec = c->opt.k_precision;
     const size_t kb = kprec_bytes(kprec);
 
-    if (c->opt.path != SWMD_PATH_RESIDENT) {
-        // per-iteration paths: the queries run one after another on the corpus's slot
-        int32_t *d_ids = nullptr;
-        float *d_r = nullptr;
-        double *d_out = nullptr;
-        int *d_status = nullptr;
-        int rc = SWMD_OK;
-        std::vector<int> h_status((size_t)n_queries, 0);
-        cudaError_t e = cudaMalloc(&d_ids, sizeof(int32_t) * ids.size());
-        if (e == cudaSuccess) e = cudaMalloc(&d_r, sizeof(float) * rs.size());
-        if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(double) * (size_t)n_queries * c->Nl);
-        if (e == cudaSuccess) e = cudaMalloc(&d_status, sizeof(int) * (size_t)n_queries);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d_ids, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d_r, rs.data(), sizeof(float) * rs.size(), cudaMemcpyHostToDevice, st);
-        for (int32_t i = 0; e == cudaSuccess && i < n_queries && rc == SWMD_OK; ++i)
-            rc = enqueue_query(c, c->main, d_ids + off[i], d_r + off[i], vrs[i], h_lambdas[i], max_iter,
-                               d_out + (size_t)i * c->Nl, d_status + i, st, true);
-        if (e == cudaSuccess && rc == SWMD_OK)
-            e = cudaMemcpyAsync(h_out, d_out, sizeof(double) * (size_t)n_queries * c->Nl, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess && rc == SWMD_OK)
-            e = cudaMemcpyAsync(h_status.data(), d_status, sizeof(int) * (size_t)n_queries, cudaMemcpyDeviceToHost, st);
-        cudaError_t e2 = cudaStreamSynchronize(st);
-        cudaFree(d_ids); cudaFree(d_r); cudaFree(d_out); cudaFree(d_status);
-        if (rc) return rc;
-        if (e != cudaSuccess || e2 != cudaSuccess) return cuda_fail(e != cudaSuccess ? e : e2, "swmd_query_batch");
-        int all = 0;
-        for (int x : h_status) all |= x;
-        return status_to_code(all);
-    }
-
-    // ---- resident path: one batched launch per kernel and layout group
-    std::vector<int> vrp((size_t)n_queries);
-    std::map<int, std::vector<int>> groups;   // layout VRP -> queries
+    // Each query takes its own path (resolve_path: a function of v_r and the
+    // tuning).  Resident queries of one layout run as one batched cost launch and
+    // one batched solver launch; per-iteration queries run one after another on
+    // the corpus's slot.
+    std::vector<int> path((size_t)n_queries), vrp((size_t)n_queries, 0);
+    std::map<int, std::vector<int>> groups;   // layout VRP -> resident queries
+    std::vector<int> others;                  // per-iteration queries
     for (int32_t i = 0; i < n_queries; ++i) {
-        vrp[i] = layout_vrp(c, vrs[i], SWMD_PATH_RESIDENT);
-        groups[vrp[i]].push_back(i);
+        path[i] = resolve_path(c, vrs[i]);
+        if (path[i] == SWMD_PATH_RESIDENT) {
+            vrp[i] = layout_vrp(c, vrs[i], SWMD_PATH_RESIDENT);
+            groups[vrp[i]].push_back(i);
+        } else {
+            others.push_back(i);
+        }
     }
     auto up = [](size_t n) { return (n + 255) & ~size_t(255); };
-    // device workspace: per query K^T, KM^T, parameter block, ids, r, status; then
-    // the outputs, the staged query arrays and the argument arrays
-    std::vector<size_t> kt_off((size_t)n_queries);
+    // device workspace: per resident query K^T, KM^T, parameter block, ids, r; then
+    // the outputs, the statuses, the staged query arrays and the argument arrays
+    std::vector<size_t> kt_off((size_t)n_queries, 0);
     size_t bytes = 0;
     for (int32_t i = 0; i < n_queries; ++i) {
+        if (path[i] != SWMD_PATH_RESIDENT) continue;
         kt_off[i] = bytes;
-        bytes += 2 * up((size_t)c->Vu * vrp[i] * kb) + up(sizeof(QParams)) + 2 * up(sizeof(float) * vrp[i]) + 256;
+        bytes += 2 * up((size_t)c->Vu * vrp[i] * kb) + up(sizeof(QParams)) + 2 * up(sizeof(float) * vrp[i]);
     }
     const size_t o_out = bytes;
     bytes += up(sizeof(double) * (size_t)n_queries * c->Nl);
+    const size_t o_status = bytes;
+    bytes += up(sizeof(int) * (size_t)n_queries);
     const size_t o_ids = bytes;
-    bytes += up(sizeof(int32_t) * ids.size());
+    bytes += up(sizeof(int32_t) * std::max<size_t>(ids.size(), 1));
     const size_t o_r = bytes;
-    bytes += up(sizeof(float) * rs.size());
+    bytes += up(sizeof(float) * std::max<size_t>(rs.size(), 1));
     const size_t o_prep = bytes;
     bytes += up(sizeof(PrepArgs) * n_queries);
     const size_t o_cost = bytes;
@@ -385,32 +368,34 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
         c->batch_ws_bytes = bytes;
     }
     char *ws = static_cast<char *>(c->batch_ws);
-    std::vector<PrepArgs> prep((size_t)n_queries);
+    int32_t *d_ids = reinterpret_cast<int32_t *>(ws + o_ids);
+    float *d_r = reinterpret_cast<float *>(ws + o_r);
+    double *d_out = reinterpret_cast<double *>(ws + o_out);
+    int *d_status = reinterpret_cast<int *>(ws + o_status);
+    std::vector<PrepArgs> prep;
     std::vector<CostArgs> cost((size_t)n_queries);
     std::vector<ResidentArgs> res((size_t)n_queries);
-    std::vector<int *> status_ptr((size_t)n_queries);
     for (int32_t i = 0; i < n_queries; ++i) {
+        if (path[i] != SWMD_PATH_RESIDENT) continue;
         char *b = ws + kt_off[i];
         void *KT = b;
         void *KMT = b + up((size_t)c->Vu * vrp[i] * kb);
         QParams *qp = reinterpret_cast<QParams *>(b + 2 * up((size_t)c->Vu * vrp[i] * kb));
         int *q_ids = reinterpret_cast<int *>(reinterpret_cast<char *>(qp) + up(sizeof(QParams)));
         float *r = reinterpret_cast<float *>(reinterpret_cast<char *>(q_ids) + up(sizeof(float) * vrp[i]));
-        int *status = reinterpret_cast<int *>(reinterpret_cast<char *>(r) + up(sizeof(float) * vrp[i]));
-        double *out = reinterpret_cast<double *>(ws + o_out) + (size_t)i * c->Nl;
-        status_ptr[i] = status;
-        PrepArgs &p = prep[i];
+        PrepArgs p{};
         p.qp = qp;
-        p.src_ids = reinterpret_cast<const int *>(ws + o_ids) + off[i];
-        p.src_r = reinterpret_cast<const float *>(ws + o_r) + off[i];
+        p.src_ids = d_ids + off[i];
+        p.src_r = d_r + off[i];
         p.q_ids = q_ids;
         p.r = r;
-        p.out = out;
-        p.status = status;
+        p.out = d_out + (size_t)i * c->Nl;
+        p.status = d_status + i;
         p.lambda = h_lambdas[i];
         p.vr = vrs[i];
         p.vrp_cap = vrp[i];
         p.pad = 0;
+        prep.push_back(p);
         CostArgs &ca = cost[i];
         ca = CostArgs{};
         ca.E = c->E;
@@ -453,27 +438,36 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
             res_g.push_back(res[i]);
         }
     }
-    SWMD_CK(cudaMemcpyAsync(ws + o_ids, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice, st));
-    SWMD_CK(cudaMemcpyAsync(ws + o_r, rs.data(), sizeof(float) * rs.size(), cudaMemcpyHostToDevice, st));
-    SWMD_CK(cudaMemcpyAsync(ws + o_prep, prep.data(), sizeof(PrepArgs) * prep.size(), cudaMemcpyHostToDevice, st));
-    SWMD_CK(cudaMemcpyAsync(ws + o_cost, cost_g.data(), sizeof(CostArgs) * cost_g.size(), cudaMemcpyHostToDevice, st));
-    SWMD_CK(cudaMemcpyAsync(ws + o_res, res_g.data(), sizeof(ResidentArgs) * res_g.size(), cudaMemcpyHostToDevice, st));
-    SWMD_CK(launch_prep_batch(reinterpret_cast<const PrepArgs *>(ws + o_prep), n_queries, c->V, st));
-    for (size_t gi = 0; gi < gstart.size(); ++gi) {
-        const int v = gstart[gi].first;
-        const size_t g0 = gstart[gi].second;
-        const int ng = (int)groups[v].size();
-        const Mapping m = walk_mapping(c, v, SWMD_PATH_RESIDENT);
-        SWMD_CK(launch_cost_batch(cost_g[g0], v, kprec, ng,
-                                  reinterpret_cast<const CostArgs *>(ws + o_cost) + g0, st));
-        int rc = run_resident_batch(c, res_g[g0], m, kprec, ng,
-                                    reinterpret_cast<const ResidentArgs *>(ws + o_res) + g0, st);
+    if (!ids.empty())
+        SWMD_CK(cudaMemcpyAsync(d_ids, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice, st));
+    if (!rs.empty())
+        SWMD_CK(cudaMemcpyAsync(d_r, rs.data(), sizeof(float) * rs.size(), cudaMemcpyHostToDevice, st));
+    SWMD_CK(cudaMemsetAsync(d_status, 0, sizeof(int) * (size_t)n_queries, st));
+    if (!prep.empty()) {
+        SWMD_CK(cudaMemcpyAsync(ws + o_prep, prep.data(), sizeof(PrepArgs) * prep.size(), cudaMemcpyHostToDevice, st));
+        SWMD_CK(cudaMemcpyAsync(ws + o_cost, cost_g.data(), sizeof(CostArgs) * cost_g.size(), cudaMemcpyHostToDevice, st));
+        SWMD_CK(cudaMemcpyAsync(ws + o_res, res_g.data(), sizeof(ResidentArgs) * res_g.size(), cudaMemcpyHostToDevice, st));
+        SWMD_CK(launch_prep_batch(reinterpret_cast<const PrepArgs *>(ws + o_prep), (int)prep.size(), c->V, st));
+        for (size_t gi = 0; gi < gstart.size(); ++gi) {
+            const int v = gstart[gi].first;
+            const size_t g0 = gstart[gi].second;
+            const int ng = (int)groups[v].size();
+            const Mapping m = walk_mapping(c, v, SWMD_PATH_RESIDENT);
+            SWMD_CK(launch_cost_batch(cost_g[g0], v, kprec, ng,
+                                      reinterpret_cast<const CostArgs *>(ws + o_cost) + g0, st));
+            int rc = run_resident_batch(c, res_g[g0], m, kprec, ng,
+                                        reinterpret_cast<const ResidentArgs *>(ws + o_res) + g0, st);
+            if (rc) return rc;
+        }
+    }
+    for (int i : others) {
+        int rc = enqueue_query(c, c->main, d_ids + off[i], d_r + off[i], vrs[i], h_lambdas[i], max_iter,
+                               d_out + (size_t)i * c->Nl, d_status + i, st, true);
         if (rc) return rc;
     }
     std::vector<int> h_status((size_t)n_queries, 0);
-    SWMD_CK(cudaMemcpyAsync(h_out, ws + o_out, sizeof(double) * (size_t)n_queries * c->Nl, cudaMemcpyDeviceToHost, st));
-    for (int32_t i = 0; i < n_queries; ++i)
-        SWMD_CK(cudaMemcpyAsync(&h_status[i], status_ptr[i], sizeof(int), cudaMemcpyDeviceToHost, st));
+    SWMD_CK(cudaMemcpyAsync(h_out, d_out, sizeof(double) * (size_t)n_queries * c->Nl, cudaMemcpyDeviceToHost, st));
+    SWMD_CK(cudaMemcpyAsync(h_status.data(), d_status, sizeof(int) * (size_t)n_queries, cudaMemcpyDeviceToHost, st));
     SWMD_CK(cudaStreamSynchronize(st));
     int all = 0;
     for (int x : h_status) all |= x;
@@ -497,8 +491,14 @@ int swmd_serve_start(swmd_corpus *c, const swmd_serve_config *cfg_in, swmd_serve
     else swmd_default_serve_config(&cfg);
     if (cfg.max_batch < 1 || cfg.max_batch > 1024 || cfg.memory_budget <= 0 || cfg.queue_capacity < 1)
         return set_error(SWMD_EINVAL, "swmd_serve_start: bad configuration");
-    const Mapping mx = choose_mapping(c, c->opt.max_vr, c->opt.path);
-    const size_t largest = query_bytes(c, std::max(mx.vrp, vrp_for(c->opt.max_vr, 8)), c->opt.path);
+    // the largest single query: every path a query may take, at max_vr words
+    size_t largest = 0;
+    for (int p : {SWMD_PATH_FUSED, SWMD_PATH_PLAIN, SWMD_PATH_RESIDENT}) {
+        if (c->opt.path != SWMD_PATH_AUTO && p != c->opt.path) continue;
+        if (c->opt.path == SWMD_PATH_AUTO && p == SWMD_PATH_PLAIN) continue;
+        const Mapping mx = choose_mapping(c, c->opt.max_vr, p);
+        largest = std::max(largest, query_bytes(c, std::max(mx.vrp, vrp_for(c->opt.max_vr, 8)), p));
+    }
     if ((size_t)cfg.memory_budget < largest)
         return set_error(SWMD_ENOMEM, "swmd_serve_start: memory_budget %lld below one query of %d words (%zu bytes)",
                          (long long)cfg.memory_budget, c->opt.max_vr, largest);

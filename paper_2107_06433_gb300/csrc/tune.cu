@@ -72,9 +72,9 @@ float time_query(swmd_corpus *c, Slot &s, int vr, int reps, cudaStream_t st, cud
 int swmd_autotune(swmd_corpus *c, int32_t v_r, int32_t reps, swmd_tune_result *out) {
     if (!c || !out) return set_error(SWMD_EINVAL, "swmd_autotune: NULL argument");
     if (reps < 1) return set_error(SWMD_EINVAL, "swmd_autotune: reps must be >= 1");
-    if (c->opt.path != SWMD_PATH_RESIDENT)
-        return set_error(SWMD_EINVAL, "swmd_autotune tunes the resident path; the corpus uses path %d",
-                         c->opt.path);
+    if (c->opt.path != SWMD_PATH_RESIDENT && c->opt.path != SWMD_PATH_AUTO)
+        return set_error(SWMD_EINVAL, "swmd_autotune tunes the resident path and the automatic choice; "
+                         "the corpus uses path %d", c->opt.path);
     if (v_r < 1 || v_r > c->opt.max_vr || v_r > c->V)
         return set_error(SWMD_EINVAL, "swmd_autotune: v_r %d outside [1, min(max_vr %d, V %d)]", v_r,
                          c->opt.max_vr, c->V);
@@ -106,9 +106,12 @@ int swmd_autotune(swmd_corpus *c, int32_t v_r, int32_t reps, swmd_tune_result *o
     const int kprec = c->opt.k_precision;
     const auto key = std::make_pair(vrp, kprec);
 
-    // time with every tunable field free; the caller's fixed fields are put back after
+    // time with every tunable field free and the resident path forced; the caller's
+    // fields are put back after
     const int fix_solver = c->opt.solver, fix_npl = c->opt.nnz_per_lane, fix_split = c->opt.cost_split;
+    const int fix_path = c->opt.path;
     c->opt.solver = c->opt.nnz_per_lane = c->opt.cost_split = 0;
+    c->opt.path = SWMD_PATH_RESIDENT;
     c->tuned_resident.erase(key);
 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -142,10 +145,22 @@ int swmd_autotune(swmd_corpus *c, int32_t v_r, int32_t reps, swmd_tune_result *o
             if (ms > 0.0f && (best_ms <= 0.0f || ms < best_ms)) best_ms = ms, best = cfg;
         }
     }
+    c->tuned_resident[key] = best;
+    // under SWMD_PATH_AUTO, the per-iteration fused path for the same query
+    int chosen = SWMD_PATH_RESIDENT;
+    float fused_ms = -1.0f;
+    if (fix_path == SWMD_PATH_AUTO) {
+        c->opt.path = SWMD_PATH_FUSED;
+        fused_ms = time_query(c, s, v_r, reps, st, e0, e1);
+        cudaGetLastError();
+        ++out->candidates;
+        if (fused_ms > 0.0f && (best_ms <= 0.0f || fused_ms < best_ms)) chosen = SWMD_PATH_FUSED;
+        c->tuned_path[std::make_pair(v_r, kprec)] = chosen;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    c->opt.path = fix_path;
 
-    c->tuned_resident[key] = best;
     c->opt.solver = fix_solver;
     c->opt.nnz_per_lane = fix_npl;
     c->opt.cost_split = fix_split;
@@ -153,11 +168,13 @@ int swmd_autotune(swmd_corpus *c, int32_t v_r, int32_t reps, swmd_tune_result *o
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
 
-    if (best_ms <= 0.0f) return set_error(SWMD_ECUDA, "swmd_autotune: no configuration ran for v_r %d", v_r);
+    if (best_ms <= 0.0f && fused_ms <= 0.0f)
+        return set_error(SWMD_ECUDA, "swmd_autotune: no configuration ran for v_r %d", v_r);
     out->vrp = vrp;
     out->solver = std::get<0>(best);
     out->nnz_per_lane = std::get<1>(best);
     out->cost_split = std::get<2>(best);
-    out->best_ms = best_ms;
+    out->best_ms = chosen == SWMD_PATH_FUSED ? fused_ms : best_ms;
+    out->path = chosen;
     return SWMD_OK;
 }

@@ -56,7 +56,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_default_options(lib):
     o = swmd.swmd_default_options()
     assert (o.k_precision, o.path, o.use_graph, o.column_shift, o.max_vr, o.device) == \
-        (swmd.K_FP32, swmd.PATH_RESIDENT, 1, 1, 128, -1)
+        (swmd.K_FP32, swmd.PATH_AUTO, 1, 1, 128, -1)
     cfg = swmd.swmd_default_serve_config()
     assert cfg.max_batch == 32 and cfg.memory_budget == 4 << 30
 

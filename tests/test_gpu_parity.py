@@ -350,3 +350,48 @@ def test_autotune_rejects_per_iteration_paths(paper):
     corpus = swmd.corpus_from_synth(E, C, path="fused")
     with pytest.raises(swmd.SwmdError):
         swmd.swmd_autotune(corpus, 8, 1)
+
+
+@pytest.fixture(scope="module")
+def wide():
+    """24,000 short documents (5-30 Zipf words): above the automatic path's
+    resident-only size, so wide queries take the per-iteration fused path."""
+    rng = np.random.default_rng(2024)
+    V, N, d = 20000, 24000, 64
+    E = synth.embeddings(rng, V, d)
+    lens = rng.integers(5, 31, size=N)
+    C = synth.corpus(rng, V, N, lens, 10)
+    return E, C
+
+
+def test_automatic_path_by_query_width(wide):
+    E, C = wide
+    corpus = swmd.corpus_from_synth(E, C)
+    assert swmd.swmd_resolve_path(corpus, 8) == "resident"
+    assert swmd.swmd_resolve_path(corpus, 64) == "fused"
+    qs = [synth.query(np.random.default_rng(k), C.V, vr) for k, vr in enumerate((8, 64, 20, 40))]
+    for qi, qw in qs[:2]:
+        got = swmd.swmd_query(corpus, qi, qw, 1.0, 15)
+        assert rel_err(got, oracle_wmd(E, C, qi, qw, 1.0, 15)) <= RTOL
+    # one batch mixing both paths: every query equals itself alone, bit for bit
+    batch = swmd.swmd_query_batch(corpus, qs, 1.0, 15)
+    for i, (qi, qw) in enumerate(qs):
+        np.testing.assert_array_equal(batch[i], swmd.swmd_query(corpus, qi, qw, 1.0, 15))
+    # and served alongside each other
+    srv = swmd.swmd_serve_start(corpus, max_batch=4, memory_budget=1 << 30)
+    tickets = [swmd.swmd_serve_submit(srv, qi, qw, 1.0, 15) for qi, qw in qs]
+    for tk, ref in zip(tickets, batch):
+        np.testing.assert_array_equal(swmd.swmd_serve_wait(srv, tk, 60000), ref)
+    srv.stop()
+
+
+def test_autotune_records_the_path(wide):
+    E, C = wide
+    corpus = swmd.corpus_from_synth(E, C)
+    res = swmd.swmd_autotune(corpus, 48, 2)
+    assert res["path"] in (swmd.PATH_RESIDENT, swmd.PATH_FUSED)
+    assert swmd.swmd_resolve_path(corpus, 48) == {swmd.PATH_RESIDENT: "resident",
+                                                  swmd.PATH_FUSED: "fused"}[res["path"]]
+    qi, qw = synth.query(np.random.default_rng(48), C.V, 48)
+    got = swmd.swmd_query(corpus, qi, qw, 1.0, 15)
+    assert rel_err(got, oracle_wmd(E, C, qi, qw, 1.0, 15)) <= RTOL
