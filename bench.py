@@ -16,11 +16,15 @@ words, v_r=19, lambda=1, 15 iterations).  Inputs are synthetic (synth.py).
              plain (separate SDDMM and SpMM launches) paths, and the per-iteration
              fused vs plain kernels.
   hbm_regime the per-iteration fused and plain kernels on the 1,000,000-document
-             workload (17.5M nonzeros, v_r=32), where c and u exceed L2: effective
-             GB/s against the HBM peak.
-  serving    a query server fed by Poisson arrivals (v_r uniform in [4,128]) over
-             the resident paper-shaped corpus: queries/s, p50/p99 latency, against
-             the same queries run one at a time through swmd_query.
+             workload (17.5M nonzeros, v_r=32), where c and u exceed L2, with FP32
+             and BF16 K: effective GB/s against the HBM peak; whole queries per path.
+  batched    256 queries (v_r uniform in [4,64]) over 100,000 documents of 10-200
+             words in one swmd_query_batch call after autotuning, FP32 and BF16 K,
+             against the same queries one at a time.
+  serving    a query server over the resident 1,000,000-document corpus with BF16 K
+             fed by Poisson arrivals at 50, 200 and 1000 queries/s (v_r uniform in
+             [4,128]): queries/s and p50/p99 latency, against the same queries run
+             one at a time through swmd_query with FP32 K, and the BF16 error.
   cpu_baseline  the FP64 oracle timed on the host cores on a bounded sample.
 
 `--impl reference` times the oracle alone (the reference arm).  Under torchrun
@@ -59,12 +63,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--path", default="resident", choices=["resident", "fused", "plain"])
+    ap.add_argument("--path", default="resident", choices=["resident", "fused", "plain", "auto"])
     ap.add_argument("--kprec", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-paths", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -315,8 +320,26 @@ def iteration_kernels(swmd, corpus, d_ids, d_r, d_status, flush, stream, vr, lam
     return per
 
 
+def time_query_device(swmd, torch, corpus, stream, flush, ids, r, lam, t, out, status, reps=3):
+    d_ids = torch.from_numpy(ids).cuda()
+    d_r = torch.from_numpy(r).cuda()
+    evs = []
+    with torch.cuda.stream(stream):
+        swmd.swmd_query_device(corpus, d_ids, d_r, len(ids), lam, t, out, status, stream=stream)
+        for _ in range(reps):
+            flush.zero_()
+            a, b = event_pair()
+            a.record(stream)
+            swmd.swmd_query_device(corpus, d_ids, d_r, len(ids), lam, t, out, status, stream=stream)
+            b.record(stream)
+            evs.append((a, b))
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in evs)
+
+
 def hbm_regime(swmd, synth, torch, flush, stream, peaks):
-    """The per-iteration kernels where c and u exceed L2 (1M documents)."""
+    """The per-iteration kernels where c and u exceed L2 (1M documents), in FP32
+    and BF16 K, and whole queries on each path."""
     w = synth.WORKLOADS["large"]
     E, C, (qi, qw) = synth.make(w)
     corpus = swmd.corpus_from_synth(E, C, path="fused")
@@ -325,62 +348,110 @@ def hbm_regime(swmd, synth, torch, flush, stream, peaks):
     d_ids = torch.from_numpy(ids).cuda()
     d_r = torch.from_numpy(r).cuda()
     d_status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    per = iteration_kernels(swmd, corpus, d_ids, d_r, d_status, flush, stream, len(ids), w.lam,
-                            info, C, peaks, 4, reps=10)
+    per = {}
+    for kp, kb in (("fp32", 4), ("bf16", 2)):
+        swmd.swmd_corpus_set_options(corpus, k_precision=kp)
+        per[kp] = iteration_kernels(swmd, corpus, d_ids, d_r, d_status, flush, stream, len(ids),
+                                    w.lam, info, C, peaks, kb, reps=10)
     d_out = torch.empty(C.N, dtype=torch.float64, device="cuda")
     q = {}
-    for path in ("resident", "fused"):
-        swmd.swmd_corpus_set_options(corpus, path=path)
-        with torch.cuda.stream(stream):
-            swmd.swmd_query_device(corpus, d_ids, d_r, len(ids), w.lam, w.max_iter, d_out,
-                                   d_status, stream=stream)
-            evs = []
-            for _ in range(3):
-                flush.zero_()
-                a, b = event_pair()
-                a.record(stream)
-                swmd.swmd_query_device(corpus, d_ids, d_r, len(ids), w.lam, w.max_iter, d_out,
-                                       d_status, stream=stream)
-                b.record(stream)
-                evs.append((a, b))
-        torch.cuda.synchronize()
-        ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
-        q[path] = {"ms_per_query": ms, "wmds_per_s": C.N / (ms * 1e-3)}
+    for path, kp in (("resident", "fp32"), ("fused", "fp32"), ("auto", "fp32"), ("fused", "bf16"),
+                     ("auto", "bf16")):
+        swmd.swmd_corpus_set_options(corpus, path=path, k_precision=kp)
+        ms = time_query_device(swmd, torch, corpus, stream, flush, ids, r, w.lam, w.max_iter,
+                               d_out, d_status)
+        q[f"{path}/{kp}"] = {"ms_per_query": ms, "wmds_per_s": C.N / (ms * 1e-3),
+                             "path_taken": swmd.swmd_resolve_path(corpus, len(ids))}
     corpus.close()
     return {"workload": "large", "documents": C.N, "nnz": info.nnz, "v_r": len(ids),
-            "iteration_kernel": per, "query": q}
+            "l2": "flushed before every timed launch", "iteration_kernel": per, "query": q}
 
 
-def serving(swmd, synth, corpus, C, rate_qps=2000.0, n=400):
-    """Poisson arrivals into the server vs the same queries one at a time."""
+def batched(swmd, synth, torch):
+    """256 queries (v_r uniform in [4, 64]) over 100,000 documents in one
+    swmd_query_batch call, autotuned, FP32 and BF16 K, against the same queries
+    one at a time through swmd_query."""
+    w = synth.WORKLOADS["batch"]
+    E, C, _ = synth.make(w)
+    qs = synth.batch_queries(C.V, 256, 4, 64, seed=synth.SEED + 2)
+    res = {"workload": "batch", "documents": C.N, "nnz": C.nnz, "queries": len(qs),
+           "v_r": "uniform 4-64", "lambda": 1.0, "max_iter": 15}
+    ref = None
+    for kp in ("fp32", "bf16"):
+        corpus = swmd.corpus_from_synth(E, C, k_precision=kp)
+        t0 = time.perf_counter()
+        paths = {}
+        for vr in sorted({len(q[0]) for q in qs}):
+            tr = swmd.swmd_autotune(corpus, vr, 2)
+            paths[tr["path"]] = paths.get(tr["path"], 0) + 1
+        tune_s = time.perf_counter() - t0
+        swmd.swmd_query_batch(corpus, qs[:8], 1.0, 15)
+        t0 = time.perf_counter()
+        out = swmd.swmd_query_batch(corpus, qs, 1.0, 15)
+        tb = time.perf_counter() - t0
+        row = {"batch_qps": len(qs) / tb, "batch_wmds_per_s": len(qs) * C.N / tb,
+               "batch_s": tb, "autotune_s": tune_s,
+               "paths_chosen": {("fused" if k == 0 else "resident"): v for k, v in paths.items()}}
+        if kp == "fp32":
+            t0 = time.perf_counter()
+            alone = [swmd.swmd_query(corpus, qi, qw, 1.0, 15) for qi, qw in qs]
+            ts = time.perf_counter() - t0
+            row["one_at_a_time_qps"] = len(qs) / ts
+            row["batch_speedup"] = ts / tb
+            row["batch_equals_alone_bitwise"] = bool(all(np.array_equal(out[i], alone[i])
+                                                         for i in range(len(qs))))
+            ref = out
+        else:
+            row["max_rel_err_vs_fp32"] = float(np.max(np.abs(out - ref) / np.abs(ref)))
+        res[kp] = row
+        corpus.close()
+    return res
+
+
+def serving(swmd, synth, torch, rates=(50.0, 200.0, 1000.0), n=200):
+    """Poisson arrivals (v_r uniform in [4, 128]) into a server over the resident
+    1,000,000-document corpus with BF16 K, against the same queries one at a time
+    through swmd_query with FP32 K."""
+    w = synth.WORKLOADS["large"]
+    E, C, _ = synth.make(w)
     qs = synth.batch_queries(C.V, n, 4, 128, seed=synth.SEED + 1)
-    arrivals = synth.poisson_arrivals(rate_qps, n)
-    swmd.swmd_corpus_set_options(corpus, path="resident")
-    # one at a time through swmd_query (host in, host out)
-    lat = []
+    res = {"workload": "large", "documents": C.N, "queries_per_rate": n, "v_r": "uniform 4-128",
+           "lambda": 1.0, "max_iter": 15}
+    c32 = swmd.corpus_from_synth(E, C, k_precision="fp32")
+    lat, alone = [], []
     t0 = time.perf_counter()
     for qi, qw in qs:
         a = time.perf_counter()
-        swmd.swmd_query(corpus, qi, qw, 1.0, 15)
+        alone.append(swmd.swmd_query(c32, qi, qw, 1.0, 15))
         lat.append((time.perf_counter() - a) * 1e3)
     one_qps = n / (time.perf_counter() - t0)
-    srv = swmd.swmd_serve_start(corpus, max_batch=32, memory_budget=2 << 30)
-    tickets = []
-    t0 = time.perf_counter()
-    for (qi, qw), at in zip(qs, arrivals):
-        now = time.perf_counter() - t0
-        if at > now:
-            time.sleep(at - now)
-        tickets.append(swmd.swmd_serve_submit(srv, qi, qw, 1.0, 15))
-    for tk in tickets:
-        swmd.swmd_serve_wait(srv, tk, 60000)
-    st = swmd.swmd_serve_stats(srv)
-    srv.stop()
-    return {"queries": n, "v_r": "uniform 4-128", "arrivals": f"Poisson {rate_qps:.0f} qps",
-            "served": {"qps": st["qps"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                       "mean_batch": st["mean_batch"]},
-            "one_at_a_time": {"qps": one_qps, "p50_ms": float(np.percentile(lat, 50)),
-                              "p99_ms": float(np.percentile(lat, 99))}}
+    c32.close()
+    res["one_at_a_time_fp32"] = {"qps": one_qps, "p50_ms": float(np.percentile(lat, 50)),
+                                 "p99_ms": float(np.percentile(lat, 99))}
+    c16 = swmd.corpus_from_synth(E, C, k_precision="bf16")
+    served = {}
+    err = 0.0
+    for rate in rates:
+        arrivals = synth.poisson_arrivals(rate, n, seed=synth.SEED + int(rate))
+        srv = swmd.swmd_serve_start(c16, max_batch=32, memory_budget=4 << 30)
+        tickets = []
+        t0 = time.perf_counter()
+        for (qi, qw), at in zip(qs, arrivals):
+            now = time.perf_counter() - t0
+            if at > now:
+                time.sleep(at - now)
+            tickets.append(swmd.swmd_serve_submit(srv, qi, qw, 1.0, 15))
+        outs = [swmd.swmd_serve_wait(srv, tk, 120000) for tk in tickets]
+        st = swmd.swmd_serve_stats(srv)
+        srv.stop()
+        if rate == rates[0]:
+            err = max(float(np.max(np.abs(o - r) / np.abs(r))) for o, r in zip(outs, alone))
+        served[f"{rate:.0f}"] = {"offered_qps": rate, "qps": st["qps"], "p50_ms": st["p50_ms"],
+                                 "p99_ms": st["p99_ms"], "mean_batch": st["mean_batch"]}
+    c16.close()
+    res["served_bf16"] = served
+    res["bf16_max_rel_err_vs_fp32"] = err
+    return res
 
 
 def main():
@@ -412,6 +483,7 @@ def main():
     info = corpus.info()
     ids, r = swmd.swmd_select(C.V, qi, qw)
     vr = len(ids)
+    run_path = args.path if args.path != "auto" else swmd.swmd_resolve_path(corpus, vr)
     d_ids = torch.from_numpy(ids).cuda()
     d_r = torch.from_numpy(r).cuda()
     d_out = torch.empty(C.N, dtype=torch.float64, device="cuda")
@@ -427,10 +499,10 @@ def main():
         swmd.swmd_step_cost(corpus, d_ids, d_r, vr, lam, d_status, stream=stream)
         if ev is not None:
             ev[1].record(stream)
-        if args.path == "resident":
+        if run_path == "resident":
             swmd.swmd_step_resident(corpus, vr, t, d_out, stream=stream)
         else:
-            swmd.swmd_step_iterate(corpus, vr, t, 1, args.path, stream=stream)
+            swmd.swmd_step_iterate(corpus, vr, t, 1, run_path, stream=stream)
             swmd.swmd_step_final(corpus, vr, int(t == 0), d_out, stream=stream)
         if ev is not None:
             ev[2].record(stream)
@@ -488,21 +560,21 @@ def main():
 
     # ---- roofline of the dominant kernel
     peaks, peak_kind = load_peaks()
-    vrp = swmd.swmd_get_mapping(corpus, vr, args.path)[0]
+    vrp = swmd.swmd_get_mapping(corpus, vr, run_path)[0]
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     cost_avg = statistics.mean(cost_ms) * 1e-3
     solve_avg = statistics.mean(solve_ms) * 1e-3
     cb, cf = cost_counts(info.V_used, w.d, vrp, vr, kb)
-    if args.path == "resident":
+    if run_path == "resident":
         sb, sf = resident_counts(info.nnz, C.N, info.V_used, vrp, vr, kb, t)
         skey = f"resident:{w.name}"
     else:
         sb = t * fused_iter_bytes(info.nnz, C.N, info.V_used, vrp, kb)
         sf = float(t + 1) * info.nnz * (4 * vr + 1)
-        skey = f"{args.path}:{w.name}"
+        skey = f"{run_path}:{w.name}"
     alu_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s at the sampled clock
     if solve_avg >= cost_avg:
-        name, key, dur, byts, flops = f"{args.path} solver (a3 x t + a4)", skey, solve_avg, sb, sf
+        name, key, dur, byts, flops = f"{run_path} solver (a3 x t + a4)", skey, solve_avg, sb, sf
     else:
         name, key, dur, byts, flops = "cost/kernel matrix (a1)", f"cost:{w.name}", cost_avg, cb, cf
     ridge = alu_peak * 1e12 / (peaks["hbm_gbs"] * 1e9)
@@ -526,24 +598,27 @@ def main():
         "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if kprec == 0 else args.kprec + "-K/f32",
-        "data": "synthetic", "config": config_dict(w, C) | {"path": args.path,
+        "data": "synthetic", "config": config_dict(w, C) | {"path": run_path,
                                                            "k_precision": args.kprec},
         "e2e": {"value": C.N * world * e2e_steps / e2e_s, "unit": "WMD/s",
                 "h2d_bytes_per_step": int(len(qi) * 8), "d2h_bytes_per_step": int(C.N * 8 + 4)},
         "roofline": roof,
         "kernels_ms": {"cost": statistics.mean(cost_ms), "solver": statistics.mean(solve_ms)},
-        "gpu_launches": K * (3 if args.path == "resident" else
-                             (2 + t * (2 if args.path == "plain" else 1) + 1)),
+        "gpu_launches": K * (3 if run_path == "resident" else
+                             (2 + t * (2 if run_path == "plain" else 1) + 1)),
         "clocks": clocks, "status": st,
     }
     if rank == 0 and not args.no_paths:
         line["paths"] = compare_paths(swmd, corpus, d_ids, d_r, d_out, d_status, flush, stream,
                                       vr, lam, t, info, C, peaks, kb)
-    if rank == 0 and not args.no_serve:
-        line["serving"] = serving(swmd, synth, corpus, C)
-    if rank == 0 and not args.no_large:
+    if rank == 0:
         corpus.close()
+    if rank == 0 and not args.no_large:
         line["hbm_regime"] = hbm_regime(swmd, synth, torch, flush, stream, peaks)
+    if rank == 0 and not args.no_batch:
+        line["batched"] = batched(swmd, synth, torch)
+    if rank == 0 and not args.no_serve:
+        line["serving"] = serving(swmd, synth, torch)
     if rank == 0 and not args.no_cpu_baseline:
         runs, el, cores = time_oracle(E, C, qi, qw, lam, t)
         line["cpu_baseline"] = {"value": C.N * runs / el, "unit": "WMD/s", "cores": cores,

@@ -168,6 +168,9 @@ typedef struct swmd_corpus_info {
 
 SWMD_API int swmd_corpus_get_info(const swmd_corpus *corpus, swmd_corpus_info *out);
 
+/* The corpus's current options (as created, or as last set). */
+SWMD_API int swmd_corpus_get_options(const swmd_corpus *corpus, swmd_options *out);
+
 /* Changes the iteration path / K precision / graph use / mapping of later
  * queries (fields as in swmd_options; the corpus-shape fields are ignored). */
 SWMD_API int swmd_corpus_set_options(swmd_corpus *corpus, const swmd_options *opt);

@@ -83,6 +83,7 @@ _SIGS = {
     "swmd_destroy_corpus": (None, [P]),
     "swmd_corpus_get_info": (ctypes.c_int, [P, P]),
     "swmd_corpus_set_options": (ctypes.c_int, [P, P]),
+    "swmd_corpus_get_options": (ctypes.c_int, [P, P]),
     "swmd_query": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.c_float, ctypes.c_int32, P]),
     "swmd_query_device": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.c_float, ctypes.c_int32,
                                          P, P, P]),
@@ -239,9 +240,23 @@ def swmd_corpus_get_info(corpus: Corpus) -> swmd_corpus_info:
     return info
 
 
+def swmd_corpus_get_options(corpus: Corpus) -> swmd_options:
+    o = swmd_options()
+    _err(lib().swmd_corpus_get_options(corpus.handle, ctypes.byref(o)), "swmd_corpus_get_options")
+    return o
+
+
 def swmd_corpus_set_options(corpus: Corpus, opt: swmd_options | None = None, **kw):
+    """Sets the corpus's options: `opt` whole, or the fields named in `kw` on top of
+    the current ones."""
     if opt is None:
-        opt = swmd_default_options(**kw)
+        opt = swmd_corpus_get_options(corpus)
+        for k, v in kw.items():
+            if k == "k_precision" and isinstance(v, str):
+                v = _KPREC[v]
+            if k == "path" and isinstance(v, str):
+                v = _PATHS[v]
+            setattr(opt, k, int(v))
     _err(lib().swmd_corpus_set_options(corpus.handle, ctypes.byref(opt)), "swmd_corpus_set_options")
 
 

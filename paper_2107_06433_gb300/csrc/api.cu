@@ -705,6 +705,12 @@ int swmd_corpus_get_info(const swmd_corpus *c, swmd_corpus_info *out) {
     return SWMD_OK;
 }
 
+int swmd_corpus_get_options(const swmd_corpus *c, swmd_options *out) {
+    if (!c || !out) return set_error(SWMD_EINVAL, "swmd_corpus_get_options: NULL argument");
+    *out = c->opt;
+    return SWMD_OK;
+}
+
 int swmd_corpus_set_options(swmd_corpus *c, const swmd_options *opt) {
     if (!c || !opt) return set_error(SWMD_EINVAL, "swmd_corpus_set_options: NULL argument");
     if (opt->k_precision < 0 || opt->k_precision > 2 || opt->path < 0 || opt->path > 3)

@@ -39,20 +39,57 @@ struct W3 {
     static_assert((Q & (Q - 1)) == 0 && Q <= 32, "team must be a power of two");
 };
 
-// WORDS 32-bit words from global memory, read-only path, one vector load.
+// L2 cache policies: the streamed arrays (c's entries, u) are read once per launch
+// and would push the gathered K^T rows (re-read by every document that holds the
+// word) out of L2; they are loaded evict-first and skip L1, K^T rows evict-last.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ int2 ld_stream(const int2 *p, uint64_t pol) {
+    int2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.s32 {%0, %1}, [%2], %3;"
+                 : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float ld_stream(const float *p, uint64_t pol) {
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float4 ld_stream4(const float *p, uint64_t pol) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_stream4(float *p, float4 v, uint64_t pol) {
+    asm volatile("st.global.L1::no_allocate.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
+                 ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol) : "memory");
+}
+
+// WORDS 32-bit words of a K^T row slice, read-only path, one vector load, kept in L2.
 template <int WORDS>
-__device__ __forceinline__ void load_words(const void *p, uint32_t (&w)[WORDS]) {
+__device__ __forceinline__ void load_words(const void *p, uint32_t (&w)[WORDS], uint64_t pol) {
     if constexpr (WORDS == 8) {
-        asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        asm volatile("ld.global.nc.L1::evict_last.L2::cache_hint.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
                      : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]),
                        "=r"(w[6]), "=r"(w[7])
-                     : "l"(p));
+                     : "l"(p), "l"(pol));
     } else if constexpr (WORDS == 4) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
-        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+        asm volatile("ld.global.nc.L1::evict_last.L2::cache_hint.v4.b32 {%0,%1,%2,%3}, [%4], %5;"
+                     : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+                     : "l"(p), "l"(pol));
     } else {
-        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
-        w[0] = v.x; w[1] = v.y;
+        asm volatile("ld.global.nc.L1::evict_last.L2::cache_hint.v2.b32 {%0,%1}, [%2], %3;"
+                     : "=r"(w[0]), "=r"(w[1])
+                     : "l"(p), "l"(pol));
     }
 }
 
@@ -138,6 +175,7 @@ __global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
     const char *KTl = reinterpret_cast<const char *>(a.KT) + lane_off;
     const char *KMTl = reinterpret_cast<const char *>(a.KMT) + lane_off;
     const long n_groups = (long)a.n_slices * Q;
+    const uint64_t pol_stream = policy_evict_first(), pol_keep = policy_evict_last();
 
     // slice bounds of the warp's next group, loaded one group ahead
     int nb = 0, ne = 0;
@@ -175,10 +213,10 @@ __global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
                 for (int p = 0; p < P / 2; ++p)
                     u[p] = make_float2(has && tl * P + 2 * p < vr ? u0 : 0.f, has && tl * P + 2 * p + 1 < vr ? u0 : 0.f);
             } else if (has) {
-                const float4 *src = reinterpret_cast<const float4 *>(a.u + ld * VRP + tl * P);
+                const float *src = a.u + ld * VRP + tl * P;
 #pragma unroll
                 for (int i = 0; i < P / 4; ++i) {
-                    const float4 f = src[i];
+                    const float4 f = ld_stream4(src + 4 * i, pol_stream);
                     u[2 * i] = make_float2(f.x, f.y);
                     u[2 * i + 1] = make_float2(f.z, f.w);
                 }
@@ -202,8 +240,8 @@ __global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
         float ev[RB], evn[RB];
 #pragma unroll
         for (int rr = 0; rr < RB; ++rr) {
-            e[rr] = __ldg(ent + rr * kSlice);
-            if constexpr (KIND == Kind::Spmm) ev[rr] = __ldg(vent + rr * kSlice);
+            e[rr] = ld_stream(ent + rr * kSlice, pol_stream);
+            if constexpr (KIND == Kind::Spmm) ev[rr] = ld_stream(vent + rr * kSlice, pol_stream);
         }
         for (int i0 = 0; i0 < Ls; i0 += RB) {
             if (i0 + RB < Ls) {
@@ -211,8 +249,8 @@ __global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
                 if constexpr (KIND == Kind::Spmm) vent += RB * kSlice;
 #pragma unroll
                 for (int rr = 0; rr < RB; ++rr) {
-                    en[rr] = __ldg(ent + rr * kSlice);
-                    if constexpr (KIND == Kind::Spmm) evn[rr] = __ldg(vent + rr * kSlice);
+                    en[rr] = ld_stream(ent + rr * kSlice, pol_stream);
+                    if constexpr (KIND == Kind::Spmm) evn[rr] = ld_stream(vent + rr * kSlice, pol_stream);
                 }
             }
 #pragma unroll 1
@@ -227,7 +265,7 @@ __global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
                 // their tau is 0
                 uint32_t kw[RB][WORDS];
 #pragma unroll
-                for (int rr = 0; rr < RB; ++rr) load_words<WORDS>(KTl + (long)e[rr].x * kRowBytes, kw[rr]);
+                for (int rr = 0; rr < RB; ++rr) load_words<WORDS>(KTl + (long)e[rr].x * kRowBytes, kw[rr], pol_keep);
                 float tau[RB];
                 if constexpr (KIND == Kind::Spmm) {
 #pragma unroll
@@ -247,7 +285,7 @@ __global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
                     if constexpr (KIND == Kind::Final) {
 #pragma unroll
                         for (int rr = 0; rr < RB; ++rr) {
-                            load_words<WORDS>(KMTl + (long)e[rr].x * kRowBytes, mw[rr]);
+                            load_words<WORDS>(KMTl + (long)e[rr].x * kRowBytes, mw[rr], pol_keep);
                             float2 m2 = __fmul2_rn(pair_of<KT_t>(mw[rr], 0), u[0]);
 #pragma unroll
                             for (int p = 1; p < P / 2; ++p)
@@ -370,8 +408,8 @@ __global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
                 float *dst = a.u + ld * VRP + tl * P;
 #pragma unroll
                 for (int i = 0; i < P / 4; ++i)
-                    reinterpret_cast<float4 *>(dst)[i] =
-                        make_float4(nu[4 * i], nu[4 * i + 1], nu[4 * i + 2], nu[4 * i + 3]);
+                    st_stream4(dst + 4 * i, make_float4(nu[4 * i], nu[4 * i + 1], nu[4 * i + 2], nu[4 * i + 3]),
+                               pol_stream);
             }
         } else if constexpr (KIND == Kind::Final) {
 #pragma unroll
@@ -389,6 +427,8 @@ cudaError_t run_walk3_v(const IterArgs &a, int sms, cudaStream_t s) {
     auto kern = k_walk3<VRP, KT_t, KIND, NT, MINB>;
     static int per_sm = 0;
     if (per_sm <= 0) {
+        // no shared memory: all of the SM's L1 for the gathered K^T rows
+        (void)cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, 0) != cudaSuccess ||
             per_sm < 1) {
             (void)cudaGetLastError();
