@@ -86,10 +86,12 @@ typedef struct swmd_options {
     int32_t doc_begin;     /* documents [doc_begin, doc_end) of the CSR columns are loaded;
                               -1/-1 = all.  One replica per GPU loads its own range. */
     int32_t doc_end;
-    int32_t team_lanes;    /* per-iteration paths: 0 = autotuned, else lanes per document
-                              (1..32, power of 2) */
-    int32_t lanes_per_nz;  /* per-iteration paths: 0 = autotuned, else lanes sharing one
-                              nonzero's dot (power of 2) */
+    int32_t team_lanes;    /* per-iteration paths: 0 = the sliced walk (default: VRP / 8
+                              lanes per document in FP32, VRP / 16 in BF16/FP16); else
+                              the general document walk with this many lanes per
+                              document (1..32, power of 2), used with lanes_per_nz */
+    int32_t lanes_per_nz;  /* per-iteration paths, general walk: lanes sharing one
+                              nonzero's dot (power of 2 dividing team_lanes) */
     int32_t tile_threads;  /* resident path: threads per block (64, 128 or 256; 0 = 128) */
     int32_t nnz_per_lane;  /* resident path: nonzeros (rows of K^T) per lane and pass; a
                               document of n nonzeros gets about n / nnz_per_lane lanes
