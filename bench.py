@@ -88,11 +88,21 @@ def load_peaks():
         return dict(FALLBACK_PEAKS), "fallback"
 
 
-def source_hash():
-    """Hash of the CUDA sources and headers: ncu traffic is valid only for it."""
+# the kernel sources each measured traffic figure depends on
+KERNEL_SOURCES = {
+    "resident": ["common.cuh", "resident_regs.cu", "resident_tiled.cu", "walk.cuh", "walk_resident.cu"],
+    "cost": ["common.cuh", "cost.cu"],
+    "fused": ["common.cuh", "walk.cuh", "walk3.cuh", "walk_fused.cu"],
+    "plain": ["common.cuh", "walk.cuh", "walk3.cuh", "walk_plain.cu"],
+}
+
+
+def source_hash(kind):
+    """Hash of the CUDA sources of one kernel family: its ncu traffic is valid only
+    for these sources."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2107_06433_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in KERNEL_SOURCES[kind]:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -100,14 +110,15 @@ def source_hash():
 
 
 def measured_traffic(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, if it matches."""
+    """DRAM bytes per launch from the committed ncu summary, if it matches the
+    current sources of that kernel."""
     try:
         with open(TRAFFIC_FILE) as f:
             t = json.load(f)
     except (OSError, ValueError):
         return None
     e = t.get(kernel_key)
-    if not e or e.get("source_hash") != source_hash():
+    if not e or e.get("source_hash") != source_hash(kernel_key.split(":")[0]):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -290,7 +301,7 @@ def compare_paths(swmd, corpus, d_ids, d_r, d_out, d_status, flush, stream, vr, 
 
 
 def iteration_kernels(swmd, corpus, d_ids, d_r, d_status, flush, stream, vr, lam, info, C, peaks,
-                      kb, reps=30):
+                      kb, reps=30, traffic_key=None):
     """One fused SDDMM-SpMM launch vs one SDDMM + one SpMM launch, on the
     per-iteration layout (swmd_get_mapping of the fused path)."""
     import torch
@@ -316,6 +327,8 @@ def iteration_kernels(swmd, corpus, d_ids, d_r, d_status, flush, stream, vr, lam
         gbs = byts / (ms * 1e-3) / 1e9
         per[path] = {"ms_per_iteration": ms, "algorithmic_bytes": byts, "vrp": vrp, "gbs": gbs,
                      "frac_of_hbm": gbs / peaks["hbm_gbs"]}
+        if traffic_key:
+            per[path]["traffic"] = measured_traffic(f"{path}:{traffic_key}")
     per["fusion_speedup"] = per["plain"]["ms_per_iteration"] / per["fused"]["ms_per_iteration"]
     return per
 
@@ -352,7 +365,7 @@ def hbm_regime(swmd, synth, torch, flush, stream, peaks):
     for kp, kb in (("fp32", 4), ("bf16", 2)):
         swmd.swmd_corpus_set_options(corpus, k_precision=kp)
         per[kp] = iteration_kernels(swmd, corpus, d_ids, d_r, d_status, flush, stream, len(ids),
-                                    w.lam, info, C, peaks, kb, reps=10)
+                                    w.lam, info, C, peaks, kb, reps=10, traffic_key=f"large:{kp}")
     d_out = torch.empty(C.N, dtype=torch.float64, device="cuda")
     q = {}
     for path, kp in (("resident", "fp32"), ("fused", "fp32"), ("auto", "fp32"), ("fused", "bf16"),
@@ -567,16 +580,16 @@ def main():
     cb, cf = cost_counts(info.V_used, w.d, vrp, vr, kb)
     if run_path == "resident":
         sb, sf = resident_counts(info.nnz, C.N, info.V_used, vrp, vr, kb, t)
-        skey = f"resident:{w.name}"
+        skey = f"resident:{w.name}:{args.kprec}"
     else:
         sb = t * fused_iter_bytes(info.nnz, C.N, info.V_used, vrp, kb)
         sf = float(t + 1) * info.nnz * (4 * vr + 1)
-        skey = f"{run_path}:{w.name}"
+        skey = f"{run_path}:{w.name}:{args.kprec}"
     alu_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s at the sampled clock
     if solve_avg >= cost_avg:
         name, key, dur, byts, flops = f"{run_path} solver (a3 x t + a4)", skey, solve_avg, sb, sf
     else:
-        name, key, dur, byts, flops = "cost/kernel matrix (a1)", f"cost:{w.name}", cost_avg, cb, cf
+        name, key, dur, byts, flops = "cost/kernel matrix (a1)", f"cost:{w.name}:{args.kprec}", cost_avg, cb, cf
     ridge = alu_peak * 1e12 / (peaks["hbm_gbs"] * 1e9)
     traffic = measured_traffic(key)
     if flops / byts >= ridge:

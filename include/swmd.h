@@ -99,7 +99,7 @@ typedef struct swmd_options {
     int32_t tile_nnz;      /* resident path: nonzeros staged per block (0 = as many as fit
                               in about 100 KB of shared memory) */
     int32_t cost_split;    /* cost kernel: threads sharing one word's embedding row
-                              (1, 2 or 4; 0 = 2) */
+                              (1, 2 or 4; 0 = 2, or 1 from 65,536 used words up) */
     int32_t solver;        /* resident path kernel: 0 = automatic, 1 = K^T rows in registers
                               (v_r <= 32), 2 = rows staged in shared memory, 3 = rows
                               re-gathered from L2 each iteration */

@@ -25,23 +25,12 @@ namespace {
 constexpr int kCostThreads = 128;
 constexpr int kDC = 32;  // embedding dimensions per shared-memory stage
 
-__device__ __forceinline__ unsigned long long pack2(float a, float b) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void unpack2(unsigned long long v, float &a, float &b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-// d = (a - e)^2 + c on two lanes of a packed pair (round-to-nearest, no fusion
-// of the subtraction: the difference is rounded once, then one FMA).
-__device__ __forceinline__ unsigned long long sqdiff_acc2(unsigned long long a,
-                                                          unsigned long long e,
-                                                          unsigned long long c) {
-    unsigned long long t, d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(a), "l"(e));
-    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(d) : "l"(t), "l"(c));
-    return d;
+// acc + (q - e)^2 on a pair of query words: the difference is rounded once (an FMA
+// of e by -1 plus q is the exact q - e, rounded once: the same as a subtraction),
+// then one FMA.  Both are packed f32x2 FMAs of sm_100+.
+__device__ __forceinline__ float2 sqdiff_acc2(float2 q, float2 e, float2 acc) {
+    const float2 t = __ffma2_rn(e, make_float2(-1.f, -1.f), q);
+    return __ffma2_rn(t, t, acc);
 }
 
 // Column factor b_w of the stored K (an exact rescaling of column w, like the
@@ -71,9 +60,9 @@ __global__ void __launch_bounds__(kCostThreads) k_cost(CostArgs a0, const CostAr
     const bool active = wi < a.Vu;
     const float *erow = a.E + (size_t)(active ? __ldg(a.used + wi) : 0) * a.d4;
 
-    unsigned long long acc[KPT / 2];
+    float2 acc[KPT / 2];
 #pragma unroll
-    for (int i = 0; i < KPT / 2; ++i) acc[i] = 0ull;
+    for (int i = 0; i < KPT / 2; ++i) acc[i] = make_float2(0.f, 0.f);
 
     for (int d0 = 0; d0 < a.d4; d0 += kDC) {
         const int dn = min(kDC, a.d4 - d0);
@@ -95,13 +84,13 @@ __global__ void __launch_bounds__(kCostThreads) k_cost(CostArgs a0, const CostAr
                 const float ev[4] = {e.x, e.y, e.z, e.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const unsigned long long e2 = pack2(ev[j], ev[j]);
+                    const float2 e2 = make_float2(ev[j], ev[j]);
                     const float4 *qrow = reinterpret_cast<const float4 *>(&sq[dd + j][sub][0]);
 #pragma unroll
                     for (int c = 0; c < KPT / 4; ++c) {
                         const float4 qv = qrow[c];
-                        acc[2 * c] = sqdiff_acc2(pack2(qv.x, qv.y), e2, acc[2 * c]);
-                        acc[2 * c + 1] = sqdiff_acc2(pack2(qv.z, qv.w), e2, acc[2 * c + 1]);
+                        acc[2 * c] = sqdiff_acc2(make_float2(qv.x, qv.y), e2, acc[2 * c]);
+                        acc[2 * c + 1] = sqdiff_acc2(make_float2(qv.z, qv.w), e2, acc[2 * c + 1]);
                     }
                 }
             }
@@ -111,10 +100,8 @@ __global__ void __launch_bounds__(kCostThreads) k_cost(CostArgs a0, const CostAr
     float m[KPT];
 #pragma unroll
     for (int i = 0; i < KPT / 2; ++i) {
-        float x, y;
-        unpack2(acc[i], x, y);
-        m[2 * i] = sqrtf(x);
-        m[2 * i + 1] = sqrtf(y);
+        m[2 * i] = sqrtf(acc[i].x);
+        m[2 * i + 1] = sqrtf(acc[i].y);
     }
     float mn = INFINITY, mx = 0.f;
 #pragma unroll
@@ -188,9 +175,9 @@ __global__ void __launch_bounds__(kCostThreads) k_cost_rows(CostArgs a0, const C
         const bool active = wi < a.Vu;
         const float4 *row =
             reinterpret_cast<const float4 *>(a.E + (size_t)(active ? __ldg(a.used + wi) : 0) * d4);
-        unsigned long long acc[VRP / 2];
+        float2 acc[VRP / 2];
 #pragma unroll
-        for (int i = 0; i < VRP / 2; ++i) acc[i] = 0ull;
+        for (int i = 0; i < VRP / 2; ++i) acc[i] = make_float2(0.f, 0.f);
         float4 buf[PF];
 #pragma unroll
         for (int j = 0; j < PF; ++j) {
@@ -211,14 +198,14 @@ __global__ void __launch_bounds__(kCostThreads) k_cost_rows(CostArgs a0, const C
                     const float ev[4] = {buf[j].x, buf[j].y, buf[j].z, buf[j].w};
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const unsigned long long e2 = pack2(ev[e], ev[e]);
-                        // query pairs read straight into 64-bit registers: no repacking
-                        const ulonglong2 *qrow = reinterpret_cast<const ulonglong2 *>(sQ + (4 * ch + e) * VRP);
+                        const float2 e2 = make_float2(ev[e], ev[e]);
+                        // query pairs read as float4: two register pairs, no repacking
+                        const float4 *qrow = reinterpret_cast<const float4 *>(sQ + (4 * ch + e) * VRP);
 #pragma unroll
                         for (int c = 0; c < VRP / 4; ++c) {
-                            const ulonglong2 qv = qrow[c];
-                            acc[2 * c] = sqdiff_acc2(qv.x, e2, acc[2 * c]);
-                            acc[2 * c + 1] = sqdiff_acc2(qv.y, e2, acc[2 * c + 1]);
+                            const float4 qv = qrow[c];
+                            acc[2 * c] = sqdiff_acc2(make_float2(qv.x, qv.y), e2, acc[2 * c]);
+                            acc[2 * c + 1] = sqdiff_acc2(make_float2(qv.z, qv.w), e2, acc[2 * c + 1]);
                         }
                     }
                 }
@@ -229,8 +216,7 @@ __global__ void __launch_bounds__(kCostThreads) k_cost_rows(CostArgs a0, const C
         float m[VRP];
 #pragma unroll
         for (int i = 0; i < VRP / 2; ++i) {
-            float x, y;
-            unpack2(acc[i], x, y);
+            float x = acc[i].x, y = acc[i].y;
 #pragma unroll
             for (int o = 1; o < TS; o <<= 1) {
                 x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -308,7 +294,10 @@ cudaError_t run(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *batch
 template <class KT_t>
 cudaError_t dispatch(const CostArgs &a, int vrp, cudaStream_t s, int nq, const CostArgs *batch) {
     if (vrp <= 32 && (size_t)a.d4 * vrp * sizeof(float) <= 100 * 1024) {
-        const int ts = a.split == 1 || a.split == 4 ? a.split : 2;
+        // threads per word: 2 by default; 1 on large vocabularies, where one thread
+        // per word already fills the GPU (measured 1.3-1.5x faster from 90,000 used
+        // words up)
+        const int ts = a.split == 1 || a.split == 2 || a.split == 4 ? a.split : (a.Vu >= 64 * 1024 ? 1 : 2);
         switch (vrp * 10 + ts) {
 #define SWMD_ROWS(V)                                      \
     case V * 10 + 1: return run_rows<V, 1, KT_t>(a, s, nq, batch); \
