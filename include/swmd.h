@@ -103,7 +103,13 @@ typedef struct swmd_options {
     int32_t solver;        /* resident path kernel: 0 = automatic, 1 = K^T rows in registers
                               (v_r <= 32), 2 = rows staged in shared memory, 3 = rows
                               re-gathered from L2 each iteration */
-    int32_t reserved[1];
+    float tol;             /* 0 (default): exactly max_iter x-updates, as the paper's
+                              experiments run.  > 0: Algorithm 1's "while x changes": the
+                              fused per-iteration path stops after the x-update in which
+                              max over documents and query words of |u (K v) - r| (the row
+                              marginal of P against r) falls below tol; max_iter (at most
+                              4096) caps it.  SWMD_PATH_AUTO then takes the fused path;
+                              the resident and plain paths refuse tol > 0 (SWMD_EINVAL). */
 } swmd_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -271,6 +277,12 @@ SWMD_API int swmd_step_resident(swmd_corpus *corpus, int32_t v_r, int32_t max_it
  * nonzero at a time.  P = 0: a team of Q = VRP / 4 lanes owns a document, each
  * lane one float4 slice of every row (the per-iteration paths' default). */
 SWMD_API int swmd_get_mapping(swmd_corpus *corpus, int32_t v_r, int32_t path, int32_t *out3);
+
+/* The number of x-updates the corpus's last single query (swmd_query,
+ * swmd_query_device, or a per-iteration query of swmd_query_batch) applied: its
+ * max_iter, or fewer when swmd_options.tol stopped it.  Synchronises the corpus's
+ * stream. */
+SWMD_API int swmd_last_iterations(swmd_corpus *corpus, int32_t *out_iterations);
 
 /* The concrete path (SWMD_PATH_RESIDENT, FUSED or PLAIN) a query of v_r words
  * takes on this corpus: the corpus's path, or SWMD_PATH_AUTO's choice. */

@@ -41,7 +41,7 @@ class swmd_options(ctypes.Structure):
                 ("team_lanes", ctypes.c_int32), ("lanes_per_nz", ctypes.c_int32),
                 ("tile_threads", ctypes.c_int32), ("nnz_per_lane", ctypes.c_int32),
                 ("tile_nnz", ctypes.c_int32), ("cost_split", ctypes.c_int32),
-                ("solver", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("solver", ctypes.c_int32), ("tol", ctypes.c_float)]
 
 
 class swmd_corpus_info(ctypes.Structure):
@@ -100,6 +100,7 @@ _SIGS = {
     "swmd_query_batch": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P, ctypes.c_int32, P]),
     "swmd_autotune": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P]),
     "swmd_resolve_path": (ctypes.c_int, [P, ctypes.c_int32, P]),
+    "swmd_last_iterations": (ctypes.c_int, [P, P]),
     "swmd_default_serve_config": (None, [P]),
     "swmd_serve_start": (ctypes.c_int, [P, P, P]),
     "swmd_serve_submit": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.c_float, ctypes.c_int32,
@@ -161,7 +162,7 @@ def swmd_default_options(**kw) -> swmd_options:
             v = _KPREC[v]
         if k == "path" and isinstance(v, str):
             v = _PATHS[v]
-        setattr(o, k, int(v))
+        setattr(o, k, float(v) if k == "tol" else int(v))
     return o
 
 
@@ -256,7 +257,7 @@ def swmd_corpus_set_options(corpus: Corpus, opt: swmd_options | None = None, **k
                 v = _KPREC[v]
             if k == "path" and isinstance(v, str):
                 v = _PATHS[v]
-            setattr(opt, k, int(v))
+            setattr(opt, k, float(v) if k == "tol" else int(v))
     _err(lib().swmd_corpus_set_options(corpus.handle, ctypes.byref(opt)), "swmd_corpus_set_options")
 
 
@@ -314,6 +315,13 @@ def swmd_get_mapping(corpus: Corpus, v_r: int, path="resident"):
     out = (ctypes.c_int32 * 3)()
     _err(lib().swmd_get_mapping(corpus.handle, int(v_r), path, out), "swmd_get_mapping")
     return int(out[0]), int(out[1]), int(out[2])
+
+
+def swmd_last_iterations(corpus: Corpus) -> int:
+    """x-updates the corpus's last single query applied (max_iter, or fewer under tol)."""
+    out = ctypes.c_int32()
+    _err(lib().swmd_last_iterations(corpus.handle, ctypes.byref(out)), "swmd_last_iterations")
+    return out.value
 
 
 def swmd_resolve_path(corpus: Corpus, v_r: int) -> str:

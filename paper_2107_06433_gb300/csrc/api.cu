@@ -67,6 +67,13 @@ int max_vrp_of(int max_vr) { return vrp_for(max_vr, 8); }
 
 }  // namespace
 
+void clear_graphs(swmd_corpus *c) {
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    for (auto &kv : c->batch_graphs) cudaGraphExecDestroy(kv.second);
+    c->batch_graphs.clear();
+}
+
 int status_to_code(int st) {
     if (st & (ST_BAD_ID | ST_BAD_R))
         return set_error(SWMD_EINVAL, "query id outside [0, V) or weight not finite and > 0");
@@ -95,6 +102,8 @@ int alloc_slot(swmd_corpus *c, Slot &s, int max_vr, int kprec, bool with_v) {
     if ((rc = dev_alloc(&s.qp, 1, &s.bytes))) return rc;
     if ((rc = dev_alloc(&s.out, (size_t)std::max(c->Nl, 1), &s.bytes))) return rc;
     if ((rc = dev_alloc(&s.status, 1, &s.bytes))) return rc;
+    if ((rc = dev_alloc(&s.conv, 1 + kMaxConvIters, &s.bytes))) return rc;
+    SWMD_CK(cudaMemset(s.conv, 0, sizeof(unsigned) * (1 + kMaxConvIters)));
     if ((rc = dev_alloc(&s.q_in, vrp, &s.bytes))) return rc;
     if ((rc = dev_alloc(&s.r_in, vrp, &s.bytes))) return rc;
     SWMD_CK(cudaMemset(s.u, 0, (size_t)std::max(c->Nl, 1) * vrp * sizeof(float)));
@@ -106,6 +115,7 @@ int alloc_slot(swmd_corpus *c, Slot &s, int max_vr, int kprec, bool with_v) {
 void free_slot(Slot &s) {
     dev_free(s.KT); dev_free(s.KMT); dev_free(s.u); dev_free(s.v); dev_free(s.q_ids);
     dev_free(s.r); dev_free(s.qp); dev_free(s.out); dev_free(s.status); dev_free(s.q_in);
+    dev_free(s.conv);
     dev_free(s.r_in);
     s = Slot{};
 }
@@ -151,6 +161,7 @@ Mapping walk_mapping(swmd_corpus *c, int vrp, int path) {
 
 int resolve_path(swmd_corpus *c, int vr) {
     if (c->opt.path != SWMD_PATH_AUTO) return c->opt.path;
+    if (c->opt.tol > 0.f) return SWMD_PATH_FUSED;   // the convergence mode's path
     auto it = c->tuned_path.find(std::make_pair(vr, c->opt.k_precision));
     if (it != c->tuned_path.end()) return it->second;
     return (c->Nl < kAutoResidentDocs || vr <= kAutoResidentVr) ? SWMD_PATH_RESIDENT : SWMD_PATH_FUSED;
@@ -340,10 +351,17 @@ static int launch_sequence(swmd_corpus *c, Slot &s, Mapping m, int t, int path, 
         ra.it.first = 1;
         return run_resident(c, ra, m, kprec, st);
     }
+    ia.conv = s.conv;   // the final step records the x-updates applied
+    if (c->opt.tol > 0.f) {
+        if (!s.conv) return set_error(SWMD_EINVAL, "convergence mode: this slot has no record");
+        ia.tol = c->opt.tol;
+        SWMD_CK(cudaMemsetAsync(s.conv, 0, sizeof(unsigned) * (1 + (size_t)t), st));
+    }
     if (path == SWMD_PATH_PLAIN && (!s.v || s.v_elems < std::max(c->nnz, c->slice_total)))
         return set_error(SWMD_EINVAL, "plain path: SDDMM output buffer missing or too small");
     for (int it = 0; it < t; ++it) {
         ia.first = it == 0;
+        ia.it = it;
         if (path == SWMD_PATH_PLAIN) {
             SWMD_CK(iter_sddmm(ia, m, kprec, c->sms, st));
             ia.first = 0;
@@ -353,6 +371,7 @@ static int launch_sequence(swmd_corpus *c, Slot &s, Mapping m, int t, int path, 
         }
     }
     ia.first = t == 0;
+    ia.it = t;
     SWMD_CK(iter_final(ia, m, kprec, c->sms, st));
     return SWMD_OK;
 }
@@ -362,10 +381,13 @@ int enqueue_query(swmd_corpus *c, Slot &s, const int *d_ids, const float *d_r, i
                   bool allow_graph) {
     const int path = resolve_path(c, vr);
     const int kprec = c->opt.k_precision;
+    if (c->opt.tol > 0.f && path != SWMD_PATH_FUSED)
+        return set_error(SWMD_EINVAL, "tol > 0 (convergence mode) needs the fused per-iteration path");
+    if (c->opt.tol > 0.f && t > kMaxConvIters)
+        return set_error(SWMD_EINVAL, "convergence mode: max_iter %d above %d", t, kMaxConvIters);
     if (!s.external && (s.kprec != kprec || (path == SWMD_PATH_PLAIN && !s.v))) {
         // buffers move: every captured graph of this corpus is stale
-        for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
-        c->graphs.clear();
+        clear_graphs(c);
         int rc = alloc_slot(c, s, c->opt.max_vr, kprec, path == SWMD_PATH_PLAIN);
         if (rc) return rc;
     }
@@ -499,7 +521,8 @@ int swmd_create_corpus(int32_t V, int32_t N, int64_t nnz, const int64_t *row_ptr
         return set_error(SWMD_EINVAL, "swmd_create_corpus: NULL input array");
     if (opt.max_vr <= 0) opt.max_vr = 128;
     if (opt.max_vr > 128) return set_error(SWMD_EINVAL, "swmd_create_corpus: max_vr above 128");
-    if (opt.k_precision < 0 || opt.k_precision > 2 || opt.path < 0 || opt.path > 3)
+    if (opt.k_precision < 0 || opt.k_precision > 2 || opt.path < 0 || opt.path > 3 || !(opt.tol >= 0.f) ||
+        std::isinf(opt.tol))
         return set_error(SWMD_EINVAL, "swmd_create_corpus: bad k_precision or path");
     int b = opt.doc_begin < 0 ? 0 : opt.doc_begin;
     int e = opt.doc_end < 0 ? N : opt.doc_end;
@@ -674,7 +697,7 @@ void swmd_destroy_corpus(swmd_corpus *c) {
     {
         DeviceGuard guard(c->device);
         if (c->stream) cudaStreamSynchronize(c->stream);
-        for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+        clear_graphs(c);
         free_slot(c->main);
         dev_free(c->batch_ws);
         dev_free(c->E);
@@ -713,7 +736,8 @@ int swmd_corpus_get_options(const swmd_corpus *c, swmd_options *out) {
 
 int swmd_corpus_set_options(swmd_corpus *c, const swmd_options *opt) {
     if (!c || !opt) return set_error(SWMD_EINVAL, "swmd_corpus_set_options: NULL argument");
-    if (opt->k_precision < 0 || opt->k_precision > 2 || opt->path < 0 || opt->path > 3)
+    if (opt->k_precision < 0 || opt->k_precision > 2 || opt->path < 0 || opt->path > 3 ||
+        !(opt->tol >= 0.f) || std::isinf(opt->tol))
         return set_error(SWMD_EINVAL, "swmd_corpus_set_options: bad k_precision or path");
     std::lock_guard<std::mutex> lk(c->mu);
     c->opt.k_precision = opt->k_precision;
@@ -727,8 +751,8 @@ int swmd_corpus_set_options(swmd_corpus *c, const swmd_options *opt) {
     c->opt.tile_nnz = opt->tile_nnz;
     c->opt.cost_split = opt->cost_split;
     c->opt.solver = opt->solver;
-    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
+    c->opt.tol = opt->tol;
+    clear_graphs(c);
     DeviceGuard guard(c->device);
     return build_tiles(c);
 }
@@ -818,8 +842,7 @@ int swmd_step_cost(swmd_corpus *c, const int32_t *d_ids, const float *d_r, int32
     cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
     Slot &s = c->main;
     if (s.kprec != c->opt.k_precision) {
-        for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
-        c->graphs.clear();
+        clear_graphs(c);
         if ((rc = alloc_slot(c, s, c->opt.max_vr, c->opt.k_precision, c->opt.path == SWMD_PATH_PLAIN)))
             return rc;
     }
@@ -863,8 +886,7 @@ int swmd_step_iterate(swmd_corpus *c, int32_t v_r, int32_t n_iter, int32_t first
         s.v_elems = std::max<int64_t>(std::max(c->nnz, c->slice_total), 1);
         if ((rc = dev_alloc(&s.v, (size_t)s.v_elems, &extra))) return rc;
         s.bytes += extra;
-        for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
-        c->graphs.clear();
+        clear_graphs(c);
     }
     if (path == SWMD_PATH_PLAIN && s.v_elems < std::max(c->nnz, c->slice_total))
         return set_error(SWMD_EINVAL, "swmd_step_iterate: SDDMM output buffer too small");
@@ -924,6 +946,19 @@ int swmd_get_mapping(swmd_corpus *c, int32_t v_r, int32_t path, int32_t *out3) {
     out3[0] = m.vrp;
     out3[1] = m.q;
     out3[2] = m.p;
+    return SWMD_OK;
+}
+
+int swmd_last_iterations(swmd_corpus *c, int32_t *out_iterations) {
+    if (!c || !out_iterations) return set_error(SWMD_EINVAL, "swmd_last_iterations: NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard guard(c->device);
+    unsigned v = 0;
+    if (c->main.conv) {
+        SWMD_CK(cudaMemcpyAsync(&v, c->main.conv, sizeof v, cudaMemcpyDeviceToHost, c->stream));
+        SWMD_CK(cudaStreamSynchronize(c->stream));
+    }
+    *out_iterations = (int32_t)v;
     return SWMD_OK;
 }
 

@@ -65,7 +65,15 @@ struct IterArgs {
     const int *slice_ptr;
     const int2 *slice_nz;
     int n_slices;
+    // convergence mode (tol > 0): conv[1 + i] holds the largest |u (K v) - r| of
+    // iteration i (float bits, atomicMax), conv[0] the x-updates applied; launch
+    // `it` does nothing once iteration it - 1 came below tol
+    float tol;
+    unsigned *conv;
+    int it;
 };
+
+constexpr int kMaxConvIters = 4096;
 
 struct CostArgs {
     const float *E;

@@ -45,6 +45,7 @@ struct Slot {
     QParams *qp = nullptr;
     double *out = nullptr;   // [Nl] distances (caller order)
     int *status = nullptr;
+    unsigned *conv = nullptr;   // [1 + kMaxConvIters]: convergence mode record
     int *q_in = nullptr;     // host-API staging of the query
     float *r_in = nullptr;
     int64_t bytes = 0;
@@ -101,6 +102,7 @@ struct swmd_corpus {
     int64_t base_bytes = 0;
 
     std::map<swmd::GraphKey, cudaGraphExec_t> graphs;
+    std::map<std::vector<int64_t>, cudaGraphExec_t> batch_graphs;   // swmd_query_batch shapes
     std::map<std::tuple<int, int, int>, swmd::Mapping> tuned;  // (vr bucket, path, kprec)
     // autotuned resident-path settings per (VRP, K precision): solver, rows per lane, cost split
     std::map<std::pair<int, int>, std::tuple<int, int, int>> tuned_resident;
@@ -128,6 +130,8 @@ int enqueue_query(swmd_corpus *c, Slot &s, const int *d_ids, const float *d_r, i
                   float lambda, int t, double *d_out, int *d_status, cudaStream_t st,
                   bool allow_graph);
 int status_to_code(int st);
+// Destroys every captured graph of the corpus (single queries and batches).
+void clear_graphs(swmd_corpus *c);
 // Launches the all-iterations solver: the shared-memory tiled kernel when the
 // query's layout allows it, else the register-only resident walk.
 int run_resident(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kprec, cudaStream_t st);

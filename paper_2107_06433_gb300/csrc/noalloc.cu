@@ -53,6 +53,8 @@ using namespace swmd;
 extern "C" int swmd_query_noalloc(swmd_corpus *c, const int32_t *d_ids, const float *d_r,
                                   int32_t v_r, float lambda, int32_t max_iter, double *d_out,
                                   int32_t *d_status, void *stream) {
+    if (c && c->opt.tol > 0.f)
+        return set_error(SWMD_EINVAL, "swmd_query_noalloc runs the resident path: tol > 0 is not available");
     if (!c) return set_error(SWMD_EINVAL, "swmd_query_noalloc: NULL corpus");
     if (v_r < 1 || v_r > c->opt.max_vr)
         return set_error(SWMD_EINVAL, "swmd_query_noalloc: %d query words; allowed 1..%d", v_r,

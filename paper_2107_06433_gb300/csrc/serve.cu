@@ -325,6 +325,8 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
     std::vector<int> others;                  // per-iteration queries
     for (int32_t i = 0; i < n_queries; ++i) {
         path[i] = resolve_path(c, vrs[i]);
+        if (c->opt.tol > 0.f && path[i] != SWMD_PATH_FUSED)
+            return set_error(SWMD_EINVAL, "tol > 0 (convergence mode) needs the fused per-iteration path");
         if (path[i] == SWMD_PATH_RESIDENT) {
             vrp[i] = layout_vrp(c, vrs[i], SWMD_PATH_RESIDENT);
             groups[vrp[i]].push_back(i);
@@ -359,6 +361,7 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
     if (c->batch_ws_bytes < bytes) {
         if (c->batch_ws) {
             cudaStreamSynchronize(st);
+            clear_graphs(c);   // the captured batches point into the old workspace
             cudaFree(c->batch_ws);
             c->batch_ws = nullptr;
             c->batch_ws_bytes = 0;
@@ -442,28 +445,80 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
         SWMD_CK(cudaMemcpyAsync(d_ids, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice, st));
     if (!rs.empty())
         SWMD_CK(cudaMemcpyAsync(d_r, rs.data(), sizeof(float) * rs.size(), cudaMemcpyHostToDevice, st));
-    SWMD_CK(cudaMemsetAsync(d_status, 0, sizeof(int) * (size_t)n_queries, st));
     if (!prep.empty()) {
         SWMD_CK(cudaMemcpyAsync(ws + o_prep, prep.data(), sizeof(PrepArgs) * prep.size(), cudaMemcpyHostToDevice, st));
         SWMD_CK(cudaMemcpyAsync(ws + o_cost, cost_g.data(), sizeof(CostArgs) * cost_g.size(), cudaMemcpyHostToDevice, st));
         SWMD_CK(cudaMemcpyAsync(ws + o_res, res_g.data(), sizeof(ResidentArgs) * res_g.size(), cudaMemcpyHostToDevice, st));
-        SWMD_CK(launch_prep_batch(reinterpret_cast<const PrepArgs *>(ws + o_prep), (int)prep.size(), c->V, st));
-        for (size_t gi = 0; gi < gstart.size(); ++gi) {
-            const int v = gstart[gi].first;
-            const size_t g0 = gstart[gi].second;
-            const int ng = (int)groups[v].size();
-            const Mapping m = walk_mapping(c, v, SWMD_PATH_RESIDENT);
-            SWMD_CK(launch_cost_batch(cost_g[g0], v, kprec, ng,
-                                      reinterpret_cast<const CostArgs *>(ws + o_cost) + g0, st));
-            int rc = run_resident_batch(c, res_g[g0], m, kprec, ng,
-                                        reinterpret_cast<const ResidentArgs *>(ws + o_res) + g0, st);
+    }
+    if (!others.empty() && !c->main.external && c->main.kprec != kprec) {
+        // the per-iteration queries use the corpus's slot: size it before any capture
+        clear_graphs(c);
+        int rc = alloc_slot(c, c->main, c->opt.max_vr, kprec, false);
+        if (rc) return rc;
+    }
+    // The device work of the batch: statuses cleared, one parameter launch, per
+    // layout group one cost and one solver launch, then the per-iteration queries.
+    // Everything it reads from the host side is in the workspace already, except
+    // the per-iteration queries' lambda and the iteration count, which are part of
+    // the key of the captured graph below.
+    auto body = [&]() -> int {
+        SWMD_CK(cudaMemsetAsync(d_status, 0, sizeof(int) * (size_t)n_queries, st));
+        if (!prep.empty()) {
+            SWMD_CK(launch_prep_batch(reinterpret_cast<const PrepArgs *>(ws + o_prep), (int)prep.size(), c->V, st));
+            for (size_t gi = 0; gi < gstart.size(); ++gi) {
+                const int v = gstart[gi].first;
+                const size_t g0 = gstart[gi].second;
+                const int ng = (int)groups[v].size();
+                const Mapping m = walk_mapping(c, v, SWMD_PATH_RESIDENT);
+                SWMD_CK(launch_cost_batch(cost_g[g0], v, kprec, ng,
+                                          reinterpret_cast<const CostArgs *>(ws + o_cost) + g0, st));
+                int rc = run_resident_batch(c, res_g[g0], m, kprec, ng,
+                                            reinterpret_cast<const ResidentArgs *>(ws + o_res) + g0, st);
+                if (rc) return rc;
+            }
+        }
+        for (int i : others) {
+            int rc = enqueue_query(c, c->main, d_ids + off[i], d_r + off[i], vrs[i], h_lambdas[i], max_iter,
+                                   d_out + (size_t)i * c->Nl, d_status + i, st, false);
             if (rc) return rc;
         }
-    }
-    for (int i : others) {
-        int rc = enqueue_query(c, c->main, d_ids + off[i], d_r + off[i], vrs[i], h_lambdas[i], max_iter,
-                               d_out + (size_t)i * c->Nl, d_status + i, st, true);
+        return SWMD_OK;
+    };
+    if (!c->opt.use_graph) {
+        int rc = body();
         if (rc) return rc;
+    } else {
+        // one CUDA graph per batch shape: the queries' paths, layouts and sizes, the
+        // per-iteration queries' lambdas, the iteration count and the workspace
+        std::vector<int64_t> key{n_queries, max_iter, kprec, c->opt.column_shift,
+                                 (int64_t)(uintptr_t)c->batch_ws};
+        for (int32_t i = 0; i < n_queries; ++i) {
+            key.push_back(path[i]);
+            key.push_back(vrs[i]);
+            if (path[i] != SWMD_PATH_RESIDENT) {
+                uint32_t lb;
+                std::memcpy(&lb, &h_lambdas[i], sizeof lb);
+                key.push_back(lb);
+            }
+        }
+        auto it = c->batch_graphs.find(key);
+        if (it == c->batch_graphs.end()) {
+            cudaGraph_t g = nullptr;
+            SWMD_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+            int rc = body();
+            cudaError_t e = cudaStreamEndCapture(st, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            SWMD_CK(e);
+            cudaGraphExec_t ge = nullptr;
+            e = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            SWMD_CK(e);
+            it = c->batch_graphs.emplace(key, ge).first;
+        }
+        SWMD_CK(cudaGraphLaunch(it->second, st));
     }
     std::vector<int> h_status((size_t)n_queries, 0);
     SWMD_CK(cudaMemcpyAsync(h_out, d_out, sizeof(double) * (size_t)n_queries * c->Nl, cudaMemcpyDeviceToHost, st));
@@ -532,6 +587,8 @@ int swmd_serve_start(swmd_corpus *c, const swmd_serve_config *cfg_in, swmd_serve
         if (e == cudaSuccess) e = cudaMalloc(&w.qp, sizeof(QParams));
         if (e == cudaSuccess) e = cudaMalloc(&w.out, sizeof(double) * std::max(c->Nl, 1));
         if (e == cudaSuccess) e = cudaMalloc(&w.status, sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&w.conv, sizeof(unsigned) * (1 + kMaxConvIters));
+        if (e == cudaSuccess) e = cudaMemset(w.conv, 0, sizeof(unsigned) * (1 + kMaxConvIters));
         if (e == cudaSuccess) e = cudaMalloc(&w.q_in, sizeof(int) * vrp);
         if (e == cudaSuccess) e = cudaMalloc(&w.r_in, sizeof(float) * vrp);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);

@@ -165,8 +165,7 @@ int swmd_autotune(swmd_corpus *c, int32_t v_r, int32_t reps, swmd_tune_result *o
     c->opt.nnz_per_lane = fix_npl;
     c->opt.cost_split = fix_split;
     // captured graphs hold the kernels of the settings they were captured with
-    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
+    clear_graphs(c);
 
     if (best_ms <= 0.0f && fused_ms <= 0.0f)
         return set_error(SWMD_ECUDA, "swmd_autotune: no configuration ran for v_r %d", v_r);

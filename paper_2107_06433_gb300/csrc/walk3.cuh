@@ -19,6 +19,7 @@
 // documents of its slice, launch or partition.
 #pragma once
 
+#include <cfloat>
 #include <type_traits>
 
 #include "walk.cuh"
@@ -176,6 +177,10 @@ __global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
     const char *KMTl = reinterpret_cast<const char *>(a.KMT) + lane_off;
     const long n_groups = (long)a.n_slices * Q;
     const uint64_t pol_stream = policy_evict_first(), pol_keep = policy_evict_last();
+    // convergence mode: nothing to do once the previous iteration came below tol
+    // (the same decision in every thread of the grid)
+    if (KIND == Kind::Fused && a.tol > 0.f && a.it > 0 && __uint_as_float(a.conv[a.it]) < a.tol) return;
+    float errmax = 0.f;   // convergence mode: largest |u (K v) - r| this lane saw
 
     // slice bounds of the warp's next group, loaded one group ahead
     int nb = 0, ne = 0;
@@ -397,6 +402,18 @@ __global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
                 float rr[P], nu[P];
                 load_floats<P>(a.r + tl * P, rr);
                 bool bad = false;
+                if (KIND == Kind::Fused && a.tol > 0.f) {
+                    // the row marginal of P = diag(u) K diag(v) against r, with this
+                    // iteration's u and v (a NaN counts as not converged)
+#pragma unroll
+                    for (int p = 0; p < P / 2; ++p) {
+                        const int k = tl * P + 2 * p;
+                        const float e0 = k < vr ? fabsf(u[p].x * acc[p].x - rr[2 * p]) : 0.f;
+                        const float e1 = k + 1 < vr ? fabsf(u[p].y * acc[p].y - rr[2 * p + 1]) : 0.f;
+                        errmax = fmaxf(errmax, e0 <= FLT_MAX ? e0 : INFINITY);
+                        errmax = fmaxf(errmax, e1 <= FLT_MAX ? e1 : INFINITY);
+                    }
+                }
 #pragma unroll
                 for (int p = 0; p < P / 2; ++p) {
                     const int k = tl * P + 2 * p;
@@ -418,6 +435,26 @@ __global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
                 if (!(fabs(dist) < INFINITY)) atomicOr(status, ST_NUMERIC);
                 out[__ldg(a.doc_orig + ld)] = dist;
             }
+        }
+    }
+    if constexpr (KIND == Kind::Fused) {
+        if (a.tol > 0.f) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) errmax = fmaxf(errmax, __shfl_xor_sync(kFull, errmax, o));
+            if (lane == 0) atomicMax(a.conv + 1 + a.it, __float_as_uint(errmax));
+        }
+    }
+    if constexpr (KIND == Kind::Final) {
+        // the x-updates applied: all of them, or up to the one that came below tol
+        if (a.conv && blockIdx.x == 0 && threadIdx.x == 0) {
+            int applied = a.it;
+            if (a.tol > 0.f)
+                for (int i = 0; i < a.it; ++i)
+                    if (__uint_as_float(a.conv[1 + i]) < a.tol) {
+                        applied = i + 1;
+                        break;
+                    }
+            a.conv[0] = (unsigned)applied;
         }
     }
 }

@@ -395,3 +395,51 @@ def test_autotune_records_the_path(wide):
     qi, qw = synth.query(np.random.default_rng(48), C.V, 48)
     got = swmd.swmd_query(corpus, qi, qw, 1.0, 15)
     assert rel_err(got, oracle_wmd(E, C, qi, qw, 1.0, 15)) <= RTOL
+
+
+def test_batch_graph_replays_new_inputs(paper, wide):
+    """A batch runs as one captured CUDA graph per shape; a second batch of the same
+    shape with other weights and lambdas replays it on the new inputs."""
+    for E, C in ((paper[0], paper[1]), wide):
+        corpus = swmd.corpus_from_synth(E, C)
+        qs1 = [synth.query(np.random.default_rng(10 + k), C.V, vr) for k, vr in enumerate((6, 19, 40))]
+        qs2 = [(qi, np.random.default_rng(99).uniform(0.5, 2.0, len(qi)).astype(np.float32)) for qi, _ in qs1]
+        for qs, lams in ((qs1, [1.0, 2.0, 0.5]), (qs2, [3.0, 1.0, 2.0]), (qs1, [1.0, 2.0, 0.5])):
+            batch = swmd.swmd_query_batch(corpus, qs, np.array(lams, np.float32), 15)
+            for i, (qi, qw) in enumerate(qs):
+                np.testing.assert_array_equal(batch[i], swmd.swmd_query(corpus, qi, qw, lams[i], 15))
+        nog = swmd.corpus_from_synth(E, C, use_graph=0)
+        batch = swmd.swmd_query_batch(nog, qs2, np.array([3.0, 1.0, 2.0], np.float32), 15)
+        for i, (qi, qw) in enumerate(qs2):
+            np.testing.assert_array_equal(batch[i], swmd.swmd_query(corpus, qi, qw, [3.0, 1.0, 2.0][i], 15))
+
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-6])
+def test_convergence_mode_stops_where_the_oracle_does(tiny, tol):
+    """tol > 0: the fused path stops after the x-update in which the row marginal of P
+    came below tol (the oracle checks before that update, so it counts one fewer);
+    the distances are those of exactly that many x-updates."""
+    E, C, (qi, qw) = tiny
+    rp, col, val = C.csr()
+    ids, r = oracle.select(C.V, qi, qw)
+    K, KM = oracle.kernel(oracle.cdist(E, ids), 1.0)
+    c = oracle.normalize_columns(C.V, C.N, rp, col, val)
+    _, it, _, _ = oracle.sinkhorn_converge(K, KM, r, C.N, rp, col, c, tol=tol, max_iter=4000)
+    corpus = swmd.corpus_from_synth(E, C, tol=tol)
+    assert swmd.swmd_resolve_path(corpus, len(ids)) == "fused"
+    got = swmd.swmd_query(corpus, qi, qw, 1.0, 4000)
+    n = swmd.swmd_last_iterations(corpus)
+    assert abs(n - (it + 1)) <= 1, (n, it)
+    assert rel_err(got, oracle_wmd(E, C, qi, qw, 1.0, n)) <= RTOL
+    # a cap below the convergence point stops at the cap
+    swmd.swmd_query(corpus, qi, qw, 1.0, 2)
+    assert swmd.swmd_last_iterations(corpus) == 2
+
+
+def test_convergence_mode_needs_the_fused_path(tiny):
+    E, C, (qi, qw) = tiny
+    with pytest.raises(swmd.SwmdError):
+        swmd.swmd_query(swmd.corpus_from_synth(E, C, path="resident", tol=1e-6), qi, qw, 1.0, 50)
+    corpus = swmd.corpus_from_synth(E, C, path="fused")
+    swmd.swmd_query(corpus, qi, qw, 1.0, 15)
+    assert swmd.swmd_last_iterations(corpus) == 15
