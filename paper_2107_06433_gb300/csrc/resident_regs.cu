@@ -31,6 +31,12 @@ constexpr int kWarps = kRegThreads / 32;
 // team, publishing u and reading it back are all free of bank conflicts.
 constexpr int kRowStride = 33;
 
+// Element k of a row held as pairs (k a compile-time index after unrolling).
+template <int N>
+__device__ __forceinline__ float row_at(const float2 (&r)[N], int k) {
+    return (k & 1) ? r[k >> 1].y : r[k >> 1].x;
+}
+
 template <int VRP, int NPL, int G, class KT_t>
 __device__ __forceinline__ void regs_task(const IterArgs &a, int t, int4 tk, int lane, float *wacc,
                                           float *wrow, float *wc, int ovf_cap) {
@@ -74,7 +80,8 @@ __device__ __forceinline__ void regs_task(const IterArgs &a, int t, int4 tk, int
         }
     }
 
-    float rows[NPL][VRP];
+    // rows as pairs: the operands of the packed f32x2 FMAs of the iteration
+    float2 rows2[NPL][VRP / 2];
     float cv[NPL];
     int wid[NPL];
 #pragma unroll
@@ -88,7 +95,8 @@ __device__ __forceinline__ void regs_task(const IterArgs &a, int t, int4 tk, int
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const float4 v = valid ? KIO<KT_t>::load4(KT, (long)e.x * C + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-            rows[j][4 * c] = v.x; rows[j][4 * c + 1] = v.y; rows[j][4 * c + 2] = v.z; rows[j][4 * c + 3] = v.w;
+            rows2[j][2 * c] = make_float2(v.x, v.y);
+            rows2[j][2 * c + 1] = make_float2(v.z, v.w);
         }
     }
     // r for the entries of u this lane finishes (k = p + G i)
@@ -104,20 +112,31 @@ __device__ __forceinline__ void regs_task(const IterArgs &a, int t, int4 tk, int
 
     for (int it = 0; it < t; ++it) {
         float acc[VRP];
+        float2 acc2[VRP / 2];
 #pragma unroll
-        for (int k = 0; k < VRP; ++k) acc[k] = 0.f;
+        for (int k = 0; k < VRP / 2; ++k) acc2[k] = make_float2(0.f, 0.f);
         bool tiny_any = false;
 #pragma unroll
         for (int j = 0; j < NPL; ++j) {
-            float d4[4] = {0.f, 0.f, 0.f, 0.f};
+            float2 da = make_float2(0.f, 0.f), db = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < VRP; ++k) d4[k & 3] = fmaf(rows[j][k], uu[k], d4[k & 3]);
-            const float dot = (d4[0] + d4[1]) + (d4[2] + d4[3]);
+            for (int k = 0; k < VRP / 2; k += 2) {
+                da = __ffma2_rn(rows2[j][k], make_float2(uu[2 * k], uu[2 * k + 1]), da);
+                if (k + 1 < VRP / 2)
+                    db = __ffma2_rn(rows2[j][k + 1], make_float2(uu[2 * k + 2], uu[2 * k + 3]), db);
+            }
+            const float dot = (da.x + da.y) + (db.x + db.y);
             const bool valid = cv[j] > 0.f;
             tiny_any |= valid && !(dot >= 0x1p-100f);
             const float tau = valid ? __fdividef(cv[j], dot) : 0.f;
+            const float2 t2 = make_float2(tau, tau);
 #pragma unroll
-            for (int k = 0; k < VRP; ++k) acc[k] = fmaf(tau, rows[j][k], acc[k]);
+            for (int k = 0; k < VRP / 2; ++k) acc2[k] = __ffma2_rn(t2, rows2[j][k], acc2[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < VRP / 2; ++k) {
+            acc[2 * k] = acc2[k].x;
+            acc[2 * k + 1] = acc2[k].y;
         }
         for (int x = 0; x < extra; ++x) {
             const int idx = p + G * (NPL + x);
@@ -162,19 +181,19 @@ __device__ __forceinline__ void regs_task(const IterArgs &a, int t, int4 tk, int
             for (int j = 0; j < NPL; ++j) {
                 float d4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int k = 0; k < VRP; ++k) d4[k & 3] = fmaf(rows[j][k], uu[k], d4[k & 3]);
+                for (int k = 0; k < VRP; ++k) d4[k & 3] = fmaf(row_at(rows2[j], k), uu[k], d4[k & 3]);
                 const float dot = (d4[0] + d4[1]) + (d4[2] + d4[3]);
                 const bool valid = cv[j] > 0.f;
                 float tau = valid ? __fdividef(cv[j], dot) : 0.f;
                 if (valid && !(dot >= 0x1p-100f)) {
                     double s = 0.0;
 #pragma unroll
-                    for (int k = 0; k < VRP; ++k) s = fma((double)rows[j][k], (double)uu[k], s);
+                    for (int k = 0; k < VRP; ++k) s = fma((double)row_at(rows2[j], k), (double)uu[k], s);
                     tau = s > 0.0 ? (float)((double)cv[j] / s) : 0.f;
                     atomicOr(status, s > 0.0 ? ST_GUARD : ST_NUMERIC);
                 }
 #pragma unroll
-                for (int k = 0; k < VRP; ++k) acc[k] = fmaf(tau, rows[j][k], acc[k]);
+                for (int k = 0; k < VRP; ++k) acc[k] = fmaf(tau, row_at(rows2[j], k), acc[k]);
             }
             for (int x = 0; x < extra; ++x) {
                 const int idx = p + G * (NPL + x);
@@ -245,7 +264,7 @@ __device__ __forceinline__ void regs_task(const IterArgs &a, int t, int4 tk, int
     for (int j = 0; j < NPL; ++j) {
         float d4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int k = 0; k < VRP; ++k) d4[k & 3] = fmaf(rows[j][k], uu[k], d4[k & 3]);
+        for (int k = 0; k < VRP; ++k) d4[k & 3] = fmaf(row_at(rows2[j], k), uu[k], d4[k & 3]);
         const float dot = (d4[0] + d4[1]) + (d4[2] + d4[3]);
         const bool valid = cv[j] > 0.f;
         float m4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -265,7 +284,7 @@ __device__ __forceinline__ void regs_task(const IterArgs &a, int t, int4 tk, int
                 SWMD_COLD_PATH();
                 double s = 0.0, m = 0.0;
 #pragma unroll
-                for (int k = 0; k < VRP; ++k) s = fma((double)rows[j][k], (double)uu[k], s);
+                for (int k = 0; k < VRP; ++k) s = fma((double)row_at(rows2[j], k), (double)uu[k], s);
                 for (int c = 0; c < C; ++c) {
                     const float4 v = KIO<KT_t>::load4(KMT, (long)wid[j] * C + c);
                     m = fma((double)v.x, (double)uu[4 * c], m);
