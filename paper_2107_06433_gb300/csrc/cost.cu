@@ -67,8 +67,11 @@ __global__ void __launch_bounds__(kCostThreads) k_cost(CostArgs a0, const CostAr
     for (int d0 = 0; d0 < a.d4; d0 += kDC) {
         const int dn = min(kDC, a.d4 - d0);
         __syncthreads();
+#pragma unroll 4
         for (int i = tid; i < dn * VRP; i += kCostThreads) {
-            const int k = i / dn, dd = i - k * dn;
+            // query word fastest across threads: independent loads, and the stores
+            // of a warp fill consecutive slots
+            const int dd = i / VRP, k = i - dd * VRP;
             float val = 0.f;
             if (k < vr) {
                 const int qid = __ldg(a.q_ids + k);
@@ -154,14 +157,24 @@ __global__ void __launch_bounds__(kCostThreads) k_cost_rows(CostArgs a0, const C
     const int vr = a.qp->vr;
     const float lam = a.qp->lambda;
     const int d4 = a.d4;
-    for (int i = threadIdx.x; i < d4 * VRP; i += kCostThreads) {
-        const int k = i / d4, dim = i - k * d4;
-        float val = 0.f;
-        if (k < vr) {
-            const int qid = __ldg(a.q_ids + k);
-            if (qid >= 0 && qid < a.V) val = __ldg(a.E + (size_t)qid * d4 + dim);
+    {
+        // Q^T staged with float4 loads, query word fastest across threads (so the
+        // transposed stores hit consecutive banks); the iterations are independent,
+        // so their loads overlap instead of running one L2 round trip at a time
+        const int n4q = d4 / 4;
+#pragma unroll 4
+        for (int i = threadIdx.x; i < n4q * VRP; i += kCostThreads) {
+            const int c = i / VRP, k = i - c * VRP;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k < vr) {
+                const int qid = __ldg(a.q_ids + k);
+                if (qid >= 0 && qid < a.V) v = __ldg(reinterpret_cast<const float4 *>(a.E + (size_t)qid * d4) + c);
+            }
+            sQ[(4 * c) * VRP + k] = v.x;
+            sQ[(4 * c + 1) * VRP + k] = v.y;
+            sQ[(4 * c + 2) * VRP + k] = v.z;
+            sQ[(4 * c + 3) * VRP + k] = v.w;
         }
-        sQ[dim * VRP + k] = val;
     }
     __syncthreads();
     const int n4 = d4 / 4;
