@@ -271,11 +271,13 @@ SWMD_API int swmd_step_final(swmd_corpus *corpus, int32_t v_r, int32_t t0, doubl
 SWMD_API int swmd_step_resident(swmd_corpus *corpus, int32_t v_r, int32_t max_iter,
                                 double *d_out, void *stream);
 
-/* The layout and lane mapping the corpus uses for a query of v_r words on `path`:
- * out[0] = VRP (v_r padded: the row length of K^T, KM^T and u), out[1] = Q,
- * out[2] = P.  P > 0: P sub-teams of Q lanes own a document, each sub-team one
- * nonzero at a time.  P = 0: a team of Q = VRP / 4 lanes owns a document, each
- * lane one float4 slice of every row (the per-iteration paths' default). */
+/* The layout and lane mapping the corpus uses for a query of v_r words on `path`
+ * (SWMD_PATH_AUTO: the path it resolves to): out[0] = VRP (v_r padded: the row
+ * length of K^T, KM^T and u), out[1] = Q, out[2] = P.  P > 0: the general walk,
+ * P sub-teams of Q lanes own a document, each sub-team one nonzero at a time.
+ * P = 0: the sliced walk (the per-iteration paths' default), VRP / 8 (FP32) or
+ * VRP / 16 (BF16/FP16) lanes own a document, each lane a contiguous 32-byte slice
+ * of every row; on the resident path P = 0 names the resident solvers. */
 SWMD_API int swmd_get_mapping(swmd_corpus *corpus, int32_t v_r, int32_t path, int32_t *out3);
 
 /* The number of x-updates the corpus's last single query (swmd_query,
@@ -330,7 +332,15 @@ SWMD_API int swmd_autotune(swmd_corpus *corpus, int32_t v_r, int32_t reps, swmd_
  *       of h_word_ids / h_weights (each as in swmd_query).
  *   h_lambdas[n_queries] (float, host): lambda of each query.
  *   h_out[n_queries * N] (double, host): row i = the distances of query i.
- * The result of each query equals its swmd_query result bit for bit. */
+ * Each query takes its own path (swmd_resolve_path).  The resident queries of one
+ * K^T layout run as one batched cost launch and one batched solver launch (grid
+ * row y = query y); the per-iteration queries run one after another.  The device
+ * work of the whole call is captured once per batch shape (the queries' paths and
+ * sizes, the per-iteration queries' lambdas, max_iter) as a CUDA graph and replayed
+ * on the next batch of that shape.  The workspace grows on demand (cudaMalloc) and
+ * is kept.  The result of each query equals its swmd_query result bit for bit.
+ * Returns the first failing query's error, or SWMD_ENUMERIC if any query flagged
+ * a NaN / infinity (the distances are still written). */
 SWMD_API int swmd_query_batch(swmd_corpus *corpus, int32_t n_queries, const int64_t *q_ptr,
                      const int32_t *h_word_ids, const float *h_weights, const float *h_lambdas,
                      int32_t max_iter, double *h_out);

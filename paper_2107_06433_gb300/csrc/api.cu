@@ -394,6 +394,8 @@ int enqueue_query(swmd_corpus *c, Slot &s, const int *d_ids, const float *d_r, i
     const Mapping m = choose_mapping(c, vr, path);
     s.cur_vrp = m.vrp;
     s.cur_vr = vr;
+    s.last_t = t;
+    s.last_path = path;
     SWMD_CK(launch_prep(s.qp, lambda, vr, c->V, d_ids, d_r, s.q_ids, s.r, s.vrp_cap, d_out,
                         d_status ? d_status : s.status, st));
     const int shift = c->opt.column_shift ? 1 : 0;
@@ -953,8 +955,9 @@ int swmd_last_iterations(swmd_corpus *c, int32_t *out_iterations) {
     if (!c || !out_iterations) return set_error(SWMD_EINVAL, "swmd_last_iterations: NULL argument");
     std::lock_guard<std::mutex> lk(c->mu);
     DeviceGuard guard(c->device);
-    unsigned v = 0;
-    if (c->main.conv) {
+    // only the per-iteration walks stop early; the resident path always applies all
+    unsigned v = (unsigned)c->main.last_t;
+    if (c->main.conv && c->main.last_path == SWMD_PATH_FUSED) {
         SWMD_CK(cudaMemcpyAsync(&v, c->main.conv, sizeof v, cudaMemcpyDeviceToHost, c->stream));
         SWMD_CK(cudaStreamSynchronize(c->stream));
     }

@@ -52,6 +52,8 @@ struct Slot {
     bool external = false;   // buffers managed by a server (never reallocated here)
     int cur_vrp = 0;         // padding of the K^T layout the last query / cost step wrote
     int cur_vr = 0;          // ... and the query size it was written for
+    int last_t = 0;          // max_iter and path of the last query enqueued on the slot
+    int last_path = -1;
 };
 
 // Key of a captured launch sequence: everything baked into the launches.

@@ -440,6 +440,7 @@ def test_convergence_mode_needs_the_fused_path(tiny):
     E, C, (qi, qw) = tiny
     with pytest.raises(swmd.SwmdError):
         swmd.swmd_query(swmd.corpus_from_synth(E, C, path="resident", tol=1e-6), qi, qw, 1.0, 50)
-    corpus = swmd.corpus_from_synth(E, C, path="fused")
-    swmd.swmd_query(corpus, qi, qw, 1.0, 15)
-    assert swmd.swmd_last_iterations(corpus) == 15
+    for path in ("fused", "resident", "plain"):
+        corpus = swmd.corpus_from_synth(E, C, path=path)
+        swmd.swmd_query(corpus, qi, qw, 1.0, 15)
+        assert swmd.swmd_last_iterations(corpus) == 15
