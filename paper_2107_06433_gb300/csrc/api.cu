@@ -948,6 +948,12 @@ int swmd_get_mapping(swmd_corpus *c, int32_t v_r, int32_t path, int32_t *out3) {
     out3[0] = m.vrp;
     out3[1] = m.q;
     out3[2] = m.p;
+    if (m.p == 0 && path != SWMD_PATH_RESIDENT) {
+        // the sliced walk's team: a 32-byte slice of every row per lane
+        const int eb = (int)kprec_bytes(c->opt.k_precision);
+        const int per_lane = m.vrp * eb >= 32 ? 32 / eb : m.vrp;
+        out3[1] = m.vrp / per_lane;
+    }
     return SWMD_OK;
 }
 
