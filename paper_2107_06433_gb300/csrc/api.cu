@@ -123,8 +123,9 @@ void free_slot(Slot &s) {
 static bool pow2_times4(int v) { return v >= 4 && v <= 128 && ((v / 4) & (v / 4 - 1)) == 0 && v % 4 == 0; }
 
 // Padding VRP of the K^T / KM^T / u layout for a query of vr words on `path`:
-// the per-iteration paths use 4 x a power of two (a team of VRP / 4 lanes, one
-// float4 slice each); the resident solvers keep the tight padding.
+// the per-iteration paths use a power of two >= 4 (the sliced walk gives each lane
+// of a power-of-two team a 32-byte slice of every row); the resident solvers keep
+// the tight padding.
 int layout_vrp(swmd_corpus *c, int vr, int path) {
     const int tl = c->opt.team_lanes, lq = c->opt.lanes_per_nz;
     if (tl > 0 && lq > 0 && tl % lq == 0) {
@@ -139,8 +140,10 @@ int layout_vrp(swmd_corpus *c, int vr, int path) {
     return vrp_for(vr, vr <= 32 ? 1 : (vr <= 64 ? 2 : 4));
 }
 
-// Kernel mapping for walking a layout of padding vrp: p = 0 selects the
-// lanes-over-k walk (VRP / 4 lanes per document); otherwise P sub-teams of Q lanes.
+// Kernel mapping for walking a layout of padding vrp: p = 0 selects the sliced
+// walk (k_walk3; its team size follows from VRP and the K precision); otherwise
+// the general walk with P sub-teams of Q lanes (swmd_options team_lanes /
+// lanes_per_nz).
 Mapping walk_mapping(swmd_corpus *c, int vrp, int path) {
     const int tl = c->opt.team_lanes, lq = c->opt.lanes_per_nz;
     if (tl > 0 && lq > 0 && tl % lq == 0) {
@@ -171,7 +174,7 @@ Mapping choose_mapping(swmd_corpus *c, int vr, int path) {
     return walk_mapping(c, layout_vrp(c, vr, path), path);
 }
 
-// per-iteration launches of one mapping (lanes-over-k walk when m.p == 0)
+// per-iteration launches of one mapping (the sliced walk when m.p == 0)
 static cudaError_t iter_fused(const IterArgs &ia, Mapping m, int kprec, int sms, cudaStream_t st) {
     return m.p == 0 ? launch_fused3(ia, m.vrp, kprec, sms, st) : launch_fused(ia, m, kprec, sms, st);
 }
