@@ -118,3 +118,10 @@ def test_create_corpus_argument_checks(lib):
         swmd.swmd_create_corpus(4, 2, rp, di, v, E, max_vr=500)
     with pytest.raises(swmd.SwmdError):
         swmd.swmd_create_corpus(4, 2, rp, di, v, E, doc_begin=2, doc_end=1)
+
+
+def test_options_marshalling(lib):
+    o = swmd.swmd_default_options(path="fused", k_precision="bf16", tol=1e-6, cost_split=1)
+    assert (o.path, o.k_precision, o.cost_split) == (swmd.PATH_FUSED, swmd.K_BF16, 1)
+    assert abs(o.tol - 1e-6) < 1e-12
+    assert swmd.swmd_default_options().tol == 0.0
