@@ -69,6 +69,8 @@ def _load():
         lib.oracle_sinkhorn_converge.restype = ctypes.c_int
         lib.oracle_wmd.argtypes = [i64, i32, P, i64, P, P, P, i64, P, P, f64, i32, i32, P]
         lib.oracle_wmd.restype = ctypes.c_int
+        lib.oracle_wmd_pairs.argtypes = [i64, i32, P, i64, P, P, P, P, P, P, f64, i32, f64, P, P]
+        lib.oracle_wmd_pairs.restype = ctypes.c_int
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_set_threads.restype = None
         lib.oracle_get_threads.argtypes = []
@@ -210,3 +212,32 @@ def wmd(E, row_ptr, col, cval, N, q_ids, q_w, lam, t, mode="sparse"):
     _check(_load().oracle_wmd(V, d, _p(E), N, _p(row_ptr), _p(col), _p(cval), len(q_ids),
                               _p(q_ids), _p(q_w), float(lam), int(t), m, _p(out)), "wmd")
     return out
+
+
+def _ragged(sides):
+    """[(ids, weights), ...] -> (ptr int64, ids int32, weights float32)."""
+    ptr = np.zeros(len(sides) + 1, np.int64)
+    for i, (ids, _) in enumerate(sides):
+        ptr[i + 1] = ptr[i] + len(ids)
+    ids = np.concatenate([np.asarray(s[0], np.int32) for s in sides]) if sides else np.zeros(0, np.int32)
+    w = np.concatenate([np.asarray(s[1], np.float32) for s in sides]) if sides else np.zeros(0, np.float32)
+    return ptr, _c(ids, np.int32), _c(w, np.float32)
+
+
+def wmd_pairs(E, queries, targets, lam, t, tol=0.0, want_iters=False):
+    """1-to-1 WMD (Section III-E, Table II): the distance of queries[p] to targets[p],
+    each an (ids, weights) histogram, with the cost built over the target's words only.
+    tol > 0 runs the convergence mode with t as the cap."""
+    if len(queries) != len(targets):
+        raise ValueError("wmd_pairs: as many queries as targets")
+    E = _c(E, np.float32)
+    V, d = E.shape
+    qp, qi, qw = _ragged(queries)
+    xp, xi, xw = _ragged(targets)
+    n = len(queries)
+    out = np.empty(n, np.float64)
+    its = np.empty(n, np.int32)
+    _check(_load().oracle_wmd_pairs(V, d, _p(E), n, _p(qp), _p(qi), _p(qw), _p(xp), _p(xi),
+                                    _p(xw), float(lam), int(t), float(tol), _p(out), _p(its)),
+           "wmd_pairs")
+    return (out, its) if want_iters else out

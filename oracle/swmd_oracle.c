@@ -443,3 +443,102 @@ out:
     free(sel); free(r); free(w); free(craw); free(c); free(M); free(K); free(KM);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* 1-to-1 WMD (Section III-E, Table II, right column): the distance of one query
+ * histogram to ONE target histogram, with the cost matrix built only over the
+ * target's v_x distinct words (v_r x v_x) instead of the whole vocabulary.
+ * Algorithm 1 with a single column c: every word outside the target has c = 0,
+ * so its v entry is 0 and it adds nothing to x = K_over_r v or to the final sum;
+ * dropping those words is the restriction that gives Table II's per-pair cost.
+ *
+ * Both sides are selected and normalised as Section III-B1 does for r and for a
+ * column of c (repeated ids add up, zero weights dropped, sum 1).  The target's
+ * words become the vocabulary of a one-column problem solved by the dense
+ * routine above (tol == 0: exactly t x-updates) or by the convergence mode
+ * (tol > 0).
+ *
+ * Pair p: query (q_ids, q_w)[q_ptr[p] .. q_ptr[p+1]), target (x_ids, x_w)
+ * [x_ptr[p] .. x_ptr[p+1]).  wmd[n_pairs]; iters[n_pairs] (optional) receives
+ * the x-updates run.  Returns 0 or the first failing pair's error code. */
+static int wmd_pair_one(int64_t V, int32_t d, const float *E, int64_t nq, const int32_t *qi,
+                        const float *qw, int64_t nx, const int32_t *xi, const float *xw,
+                        double lambda, int32_t t, double tol, double *wmd, int32_t *iters)
+{
+    int rc = ORACLE_OK;
+    int64_t nmax = nq > nx ? nq : nx;
+    if (nmax < 1) nmax = 1;
+    int32_t *sq = (int32_t *)malloc(sizeof(int32_t) * (size_t)nmax);
+    int32_t *sx = (int32_t *)malloc(sizeof(int32_t) * (size_t)nmax);
+    double *r = (double *)malloc(sizeof(double) * (size_t)nmax);
+    double *cx = (double *)malloc(sizeof(double) * (size_t)nmax);
+    double *w = (double *)malloc(sizeof(double) * (size_t)nmax);
+    double *M = NULL, *K = NULL, *KM = NULL;
+    int64_t *rp = NULL;
+    int32_t *col = NULL;
+    if (!sq || !sx || !r || !cx || !w) { rc = ORACLE_ENOMEM; goto out; }
+    for (int64_t i = 0; i < nq; ++i) w[i] = (double)qw[i];
+    int64_t vr = oracle_select(V, nq, qi, w, sq, r);
+    if (vr <= 0) { rc = (int)(vr < 0 ? vr : ORACLE_EINVAL); goto out; }
+    for (int64_t i = 0; i < nx; ++i) w[i] = (double)xw[i];
+    int64_t vx = oracle_select(V, nx, xi, w, sx, cx);
+    if (vx <= 0) { rc = (int)(vx < 0 ? vx : ORACLE_EINVAL); goto out; }
+
+    /* M[k][j] = ||E[q_k] - E[x_j]||_2 over the target's words only (Section II-A) */
+    M = (double *)malloc(sizeof(double) * (size_t)(vr * vx));
+    K = (double *)malloc(sizeof(double) * (size_t)(vr * vx));
+    KM = (double *)malloc(sizeof(double) * (size_t)(vr * vx));
+    rp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(vx + 1));
+    col = (int32_t *)calloc((size_t)vx, sizeof(int32_t));
+    if (!M || !K || !KM || !rp || !col) { rc = ORACLE_ENOMEM; goto out; }
+    for (int64_t k = 0; k < vr; ++k)
+        for (int64_t j = 0; j < vx; ++j) {
+            const float *a = E + (size_t)sq[k] * d;
+            const float *b = E + (size_t)sx[j] * d;
+            double acc = 0.0;
+            for (int32_t e = 0; e < d; ++e) {
+                double diff = (double)a[e] - (double)b[e];
+                acc += diff * diff;
+            }
+            M[(size_t)k * vx + j] = sqrt(acc);
+        }
+    oracle_kernel(vr * vx, M, lambda, K, KM);
+    /* c as a vx x 1 CSR: target word j is row j, one nonzero in column 0 */
+    for (int64_t j = 0; j <= vx; ++j) rp[j] = j;
+    if (tol > 0.0) {
+        rc = oracle_sinkhorn_converge((int32_t)vr, vx, 1, K, KM, r, rp, col, cx, t, tol, iters,
+                                      wmd, NULL, NULL);
+    } else {
+        rc = oracle_sinkhorn_dense((int32_t)vr, vx, 1, K, KM, r, rp, col, cx, t, 1, wmd, NULL);
+        if (iters) *iters = t;
+    }
+out:
+    free(sq); free(sx); free(r); free(cx); free(w);
+    free(M); free(K); free(KM); free(rp); free(col);
+    return rc;
+}
+
+int oracle_wmd_pairs(int64_t V, int32_t d, const float *E, int64_t n_pairs, const int64_t *q_ptr,
+                     const int32_t *q_ids, const float *q_w, const int64_t *x_ptr,
+                     const int32_t *x_ids, const float *x_w, double lambda, int32_t t, double tol,
+                     double *wmd, int32_t *iters)
+{
+    if (!(lambda > 0.0) || isinf(lambda) || t < 0 || d <= 0 || n_pairs < 0 || !(tol >= 0.0))
+        return ORACLE_EINVAL;
+    int rc = ORACLE_OK;
+    int64_t p;
+    /* pairs are independent; each writes only its own outputs */
+#pragma omp parallel for schedule(dynamic, 1)
+    for (p = 0; p < n_pairs; ++p) {
+        int32_t it = 0;
+        int e = wmd_pair_one(V, d, E, q_ptr[p + 1] - q_ptr[p], q_ids + q_ptr[p], q_w + q_ptr[p],
+                             x_ptr[p + 1] - x_ptr[p], x_ids + x_ptr[p], x_w + x_ptr[p], lambda, t,
+                             tol, wmd + p, &it);
+        if (iters) iters[p] = it;
+        if (e != ORACLE_OK) {
+#pragma omp critical
+            if (rc == ORACLE_OK) rc = e;
+        }
+    }
+    return rc;
+}

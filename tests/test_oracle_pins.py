@@ -396,3 +396,137 @@ def test_golden_tiny_values(tiny):
     rp, col, val = C.csr()
     got = oracle.wmd(E, rp, col, val, C.N, qi, qw, 1.0, 15)
     np.testing.assert_allclose(got, ref, rtol=1e-12)
+
+
+# --------------------------------------------------------------------------- 1-to-1 WMD
+
+def _doc_side(C, j):
+    lo, hi = C.doc_ptr[j], C.doc_ptr[j + 1]
+    return C.word_ids[lo:hi], C.vals[lo:hi]
+
+
+@pytest.mark.parametrize("t", [0, 1, 15])
+@pytest.mark.parametrize("lam", [1.0, 10.0])
+@pytest.mark.parametrize("workload", ["tiny", "paper"])
+def test_pair_equals_column_of_the_one_to_many_problem(t, lam, workload):
+    """Table II's 1-to-1 problem builds the cost only over the target's words.  Every
+    other word has c = 0 in Algorithm 1, so v = 0 there and it adds nothing: the pair
+    distance equals that document's entry of the 1-to-N result."""
+    E, C, (qi, qw) = synth.make(workload, N=40) if workload == "paper" else synth.make("tiny")
+    rp, col, val = C.csr()
+    full = oracle.wmd(E, rp, col, val, C.N, qi, qw, lam, t)
+    pairs = oracle.wmd_pairs(E, [(qi, qw)] * C.N, [_doc_side(C, j) for j in range(C.N)], lam, t)
+    np.testing.assert_allclose(pairs, full, rtol=1e-12)
+
+
+@pytest.mark.parametrize("t", [0, 3, 15])
+def test_pair_single_word_sides_are_closed_forms(t):
+    """One query word: WMD = sum_j c_j M[q, x_j] (any t).  One target word, t >= 1:
+    WMD = sum_k r_k M[q_k, x].  Both: the word distance."""
+    rng = np.random.default_rng(21)
+    V = 50
+    E = _unit_rows(rng, V, 9)
+    xs, xw = [3, 17, 40, 41], [2.0, 1.0, 4.0, 1.0]
+    qs, qw = [0, 5, 17, 33, 49], [1.0, 1.0, 3.0, 2.0, 1.0]
+    got = oracle.wmd_pairs(E, [([7], [1.0]), (qs, qw), ([7], [2.0])],
+                           [(xs, xw), ([11], [1.0]), ([30], [5.0])], 2.0, t)
+    expect0 = sum(w / sum(xw) * _direct_dist(E, 7, x) for x, w in zip(xs, xw))
+    assert got[0] == pytest.approx(expect0, rel=1e-12)
+    if t >= 1:
+        expect1 = sum(w / sum(qw) * _direct_dist(E, q, 11) for q, w in zip(qs, qw))
+        assert got[1] == pytest.approx(expect1, rel=1e-12)
+    assert got[2] == pytest.approx(_direct_dist(E, 7, 30), rel=1e-13)
+
+
+@pytest.mark.parametrize("lam", [0.5, 4.0])
+def test_pair_zero_iterations_is_softmin_average(lam):
+    """t = 0: u stays uniform and WMD = sum_j c_j sum_k softmax_k(-lam M[k,j]) M[k,j]."""
+    rng = np.random.default_rng(22)
+    V = 60
+    E = _unit_rows(rng, V, 8)
+    qs, qw = [1, 9, 22, 37], [3.0, 1.0, 1.0, 2.0]
+    xs, xw = [4, 9, 50], [1.0, 2.0, 2.0]
+    got = oracle.wmd_pairs(E, [(qs, qw)], [(xs, xw)], lam, 0)[0]
+    tot = 0.0
+    for x, w in zip(xs, xw):
+        m = np.array([_direct_dist(E, q, x) for q in qs])
+        a = np.exp(-lam * (m - m.min()))
+        tot += w / sum(xw) * float(np.sum(a * m) / np.sum(a))
+    assert got == pytest.approx(tot, rel=1e-12)
+
+
+def test_pair_is_symmetric_at_convergence():
+    """The entropic plan is the unique minimiser whichever side Sinkhorn starts from,
+    so converged distances satisfy WMD(a, b) = WMD(b, a); after a fixed small t they
+    do not (the iteration starts from the query side)."""
+    rng = np.random.default_rng(23)
+    V = 80
+    E = _unit_rows(rng, V, 6)
+    A, B = [], []
+    for _ in range(6):
+        na, nb = int(rng.integers(2, 9)), int(rng.integers(2, 9))
+        A.append((rng.choice(V, na, replace=False), rng.integers(1, 6, na).astype(np.float32)))
+        B.append((rng.choice(V, nb, replace=False), rng.integers(1, 6, nb).astype(np.float32)))
+    ab, it_ab = oracle.wmd_pairs(E, A, B, 3.0, 200000, tol=1e-14, want_iters=True)
+    ba, it_ba = oracle.wmd_pairs(E, B, A, 3.0, 200000, tol=1e-14, want_iters=True)
+    assert np.all(it_ab < 200000) and np.all(it_ba < 200000)
+    np.testing.assert_allclose(ab, ba, rtol=1e-10)
+    ab2 = oracle.wmd_pairs(E, A, B, 3.0, 1)
+    ba2 = oracle.wmd_pairs(E, B, A, 3.0, 1)
+    assert np.max(np.abs(ab2 - ba2)) > 1e-6
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_pair_lambda_limit_against_linear_program(seed):
+    """Unequal masses: exact EMD from scipy's LP; the converged entropic cost lies
+    within min(H(r), H(c)) / lambda above it and falls as lambda grows."""
+    from scipy.optimize import linprog
+    rng = np.random.default_rng(300 + seed)
+    V = 40
+    E = _unit_rows(rng, V, 3)
+    qs = rng.choice(V, 4, replace=False)
+    xs = rng.choice(V, 5, replace=False)
+    qw = rng.integers(1, 6, 4).astype(np.float64)
+    xw = rng.integers(1, 6, 5).astype(np.float64)
+    r, c = qw / qw.sum(), xw / xw.sum()
+    M = np.array([[_direct_dist(E, a, b) for b in xs] for a in qs])
+    A_eq = np.zeros((4 + 5, 20))
+    for i in range(4):
+        A_eq[i, i * 5:(i + 1) * 5] = 1.0
+    for j in range(5):
+        A_eq[4 + j, j::5] = 1.0
+    lp = linprog(M.ravel(), A_eq=A_eq, b_eq=np.concatenate([r, c]), bounds=(0, None),
+                 method="highs")
+    emd = lp.fun
+    prev = None
+    for lam in (2.0, 8.0, 32.0, 128.0):
+        S = oracle.wmd_pairs(E, [(qs, qw.astype(np.float32))], [(xs, xw.astype(np.float32))],
+                             lam, 400000, tol=1e-12)[0]
+        assert S >= emd - 1e-9
+        assert S - emd <= min(_entropy(r), _entropy(c)) / lam + 1e-9
+        if prev is not None:
+            assert S <= prev + 1e-9
+        prev = S
+
+
+def test_pair_merges_duplicates_and_drops_zeros():
+    rng = np.random.default_rng(24)
+    E = _unit_rows(rng, 30, 5)
+    merged = oracle.wmd_pairs(E, [([2, 8], [1.0, 3.0])], [([4, 20, 21], [2.0, 1.0, 1.0])], 1.0, 9)
+    split = oracle.wmd_pairs(E, [([8, 2, 8, 11], [1.0, 1.0, 2.0, 0.0])],
+                             [([21, 4, 20, 4, 6], [1.0, 1.5, 1.0, 0.5, 0.0])], 1.0, 9)
+    np.testing.assert_array_equal(merged, split)
+
+
+def test_pair_rejects_invalid_sides():
+    rng = np.random.default_rng(25)
+    E = _unit_rows(rng, 10, 3)
+    ok = ([1, 2], [1.0, 1.0])
+    for bad in (([1, 10], [1.0, 1.0]), ([1, -1], [1.0, 1.0]), ([1, 2], [1.0, -1.0]),
+                ([1, 2], [0.0, 0.0]), ([], [])):
+        with pytest.raises(oracle.OracleError):
+            oracle.wmd_pairs(E, [ok], [bad], 1.0, 3)
+        with pytest.raises(oracle.OracleError):
+            oracle.wmd_pairs(E, [bad], [ok], 1.0, 3)
+    with pytest.raises(oracle.OracleError):
+        oracle.wmd_pairs(E, [ok], [ok], 0.0, 3)
