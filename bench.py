@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-pairs", action="store_true")
     return ap.parse_args()
 
 
@@ -350,6 +351,63 @@ def time_query_device(swmd, torch, corpus, stream, flush, ids, r, lam, t, out, s
     return statistics.mean(a.elapsed_time(b) for a, b in evs)
 
 
+def one_to_one(swmd, torch, corpus, C, qi, qw, lam, t, flush, stream, d, alu_peak, one_to_n_ms,
+               one_to_n_out):
+    """1-to-1 WMD (Section III-E, Table II): the query against documents as independent
+    pairs whose cost is built over each document's words only.  All documents of the
+    corpus, and a 100-candidate re-ranking set beside the whole 1-to-N query.
+    Algorithmic flops per pair: v_r v_x (3 d + 4 t + 4) -- the cost block (a
+    subtraction and an FMA per dimension), t SDDMM + SpMM passes (2 FMAs per entry)
+    and the final pass (2 FMAs per entry)."""
+    ids, r = swmd.swmd_select(C.V, qi, qw)
+    vr = len(ids)
+    docs = [swmd.swmd_select(C.V, C.word_ids[C.doc_ptr[j]:C.doc_ptr[j + 1]],
+                             C.vals[C.doc_ptr[j]:C.doc_ptr[j + 1]]) for j in range(C.N)]
+    dev = lambda x: torch.from_numpy(x).cuda()
+    res = {}
+    for label, sel, reps in (("all_documents", list(range(C.N)), 50),
+                             ("rerank_100", list(range(0, C.N, max(1, C.N // 100)))[:100], 200)):
+        qp, qi_, qr = swmd._ragged([(ids, r)] * len(sel))
+        xp, xi_, xc = swmd._ragged([docs[j] for j in sel])
+        args = [dev(x) for x in (qp, qi_, qr, xp, xi_, xc)]
+        max_x = max(len(docs[j][0]) for j in sel)
+        out = torch.empty(len(sel), dtype=torch.float64, device="cuda")
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        evs = []
+        with torch.cuda.stream(stream):
+            for k in range(reps + 3):
+                flush.zero_()
+                a_, b_ = event_pair()
+                a_.record(stream)
+                swmd.swmd_wmd_pairs_device(corpus, len(sel), *args, vr, max_x, lam, t, out, status,
+                                           stream=stream)
+                b_.record(stream)
+                if k >= 3:
+                    evs.append((a_, b_))
+        torch.cuda.synchronize()
+        ms = statistics.mean(x.elapsed_time(y) for x, y in evs)
+        flops = float(sum(vr * len(docs[j][0]) * (3 * d + 4 * t + 4) for j in sel))
+        ach = flops / (ms * 1e-3) / 1e12
+        got = out.cpu().numpy()
+        res[label] = {"pairs": len(sel), "ms": ms, "wmds_per_s": len(sel) / (ms * 1e-3),
+                      "algorithmic_flops": flops, "tflops": ach, "frac_of_alu": ach / alu_peak,
+                      "status": int(status.item()),
+                      "max_rel_vs_one_to_n": float(np.max(np.abs(got - one_to_n_out[sel]) /
+                                                          np.abs(one_to_n_out[sel])))}
+    res["rerank_100"]["one_to_n_whole_query_ms"] = one_to_n_ms
+    # end to end through the host entry point (selection on the host, copies both ways)
+    reps = 10
+    targets = [(C.word_ids[C.doc_ptr[j]:C.doc_ptr[j + 1]], C.vals[C.doc_ptr[j]:C.doc_ptr[j + 1]])
+               for j in range(C.N)]
+    swmd.swmd_wmd_pairs(corpus, [(qi, qw)] * C.N, targets, lam, t)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        swmd.swmd_wmd_pairs(corpus, [(qi, qw)] * C.N, targets, lam, t)
+    res["all_documents"]["e2e_wmds_per_s"] = C.N * reps / (time.perf_counter() - t0)
+    res["alu_peak_tflops"] = alu_peak
+    return res
+
+
 def hbm_regime(swmd, synth, torch, flush, stream, peaks):
     """The per-iteration kernels where c and u exceed L2 (1M documents), in FP32
     and BF16 K, and whole queries on each path."""
@@ -627,6 +685,9 @@ def main():
     if rank == 0 and not args.no_paths:
         line["paths"] = compare_paths(swmd, corpus, d_ids, d_r, d_out, d_status, flush, stream,
                                       vr, lam, t, info, C, peaks, kb)
+    if rank == 0 and not args.no_pairs:
+        line["one_to_one"] = one_to_one(swmd, torch, corpus, C, qi, qw, lam, t, flush, stream, w.d,
+                                        alu_peak, total_ms / K, out_dev)
     if rank == 0:
         corpus.close()
     if rank == 0 and not args.no_large:

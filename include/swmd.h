@@ -290,6 +290,58 @@ SWMD_API int swmd_last_iterations(swmd_corpus *corpus, int32_t *out_iterations);
  * takes on this corpus: the corpus's path, or SWMD_PATH_AUTO's choice. */
 SWMD_API int swmd_resolve_path(swmd_corpus *corpus, int32_t v_r, int32_t *out_path);
 
+/* ------------------------------------------------------------------ 1-to-1 WMD */
+/* The paper's per-pair variant (Section III-E, Table II, right column): the WMD of
+ * each of n_pairs independent (query, target) pairs of histograms over the corpus's
+ * vocabulary and embeddings, with the cost matrix built only over the target's v_x
+ * distinct words, so a pair costs O(v_x v_r d + t v_x v_r) instead of the 1-to-N
+ * query's O(V v_r d + t nnz v_r).  It is Algorithm 1 with c the target histogram
+ * as a single column (a word outside the target has c = 0 and adds nothing), so a
+ * pair's distance equals that document's entry of the 1-to-N result up to rounding.
+ * Use it when a query meets few documents (re-ranking candidates, pairwise
+ * distances); the corpus's c is not used, only its embeddings and column_shift.
+ *   Pair p: query words h_q_ids[h_q_ptr[p] .. h_q_ptr[p+1]) with h_q_weights,
+ *   target words h_x_ids[h_x_ptr[p] .. h_x_ptr[p+1]) with h_x_weights (host
+ *   arrays; h_q_ptr[0] = h_x_ptr[0] = 0, non-decreasing).  Each side is selected
+ *   and normalised like a query (swmd_select: repeated ids add up, zero weights
+ *   drop, sum 1); after that each side has 1 .. 4096 distinct words.
+ *   lambda finite > 0; max_iter >= 0 x-updates; tol: 0 = exactly max_iter updates,
+ *   > 0 = stop once max_k |u_k (K v)_k - r_k| < tol (Algorithm 1's "while x
+ *   changes") with max_iter as the cap -- per pair.
+ *   h_out[n_pairs] (double): the distances; h_iters[n_pairs] (int32, may be NULL):
+ *   the x-updates each pair ran.
+ * FP32 arithmetic (K and K.*M in FP32 whatever the corpus's k_precision), FP64
+ * final sum.  Blocks until the results are in host memory.  SWMD_EINVAL names the
+ * first invalid pair side; SWMD_ENUMERIC as for swmd_query. */
+SWMD_API int swmd_wmd_pairs(swmd_corpus *corpus, int32_t n_pairs, const int64_t *h_q_ptr,
+                            const int32_t *h_q_ids, const float *h_q_weights,
+                            const int64_t *h_x_ptr, const int32_t *h_x_ids,
+                            const float *h_x_weights, float lambda, int32_t max_iter, float tol,
+                            double *h_out, int32_t *h_iters);
+
+/* swmd_wmd_pairs on sides already selected and normalised (distinct ids, weights
+ * > 0 summing to 1) and resident on the device, asynchronously on `stream`:
+ *   d_q_ptr[n_pairs+1], d_x_ptr[n_pairs+1] (int64), d_q_ids / d_x_ids (int32),
+ *   d_r / d_c (float): as in swmd_wmd_pairs, in device memory.  Distinct ids are
+ *   the caller's promise (not checked).
+ *   max_q_words, max_x_words (1 .. 4096): bounds on every pair's side sizes; they
+ *   size the launch's shared memory, so tight bounds run faster.
+ *   d_out[n_pairs] (double), d_iters[n_pairs] (int32, may be NULL), d_status
+ *   (int32, required): the status word is OR-ed with the SWMD_E* condition bits of
+ *   the kernels (the caller zeroes it); a pair with an id outside [0, V), a weight
+ *   that is not finite and > 0, or a side outside [1, bound] gets a NaN distance.
+ * When K and K.*M of the largest pair (8 (max_q_words + 1) max_x_words bytes)
+ * exceed 48 KiB they live in a per-block region of global memory that the corpus
+ * allocates (at most 2 GiB) the first time a call needs it; that allocation
+ * synchronises the device, so make one call with the largest bounds before any
+ * stream capture. */
+SWMD_API int swmd_wmd_pairs_device(swmd_corpus *corpus, int32_t n_pairs, const int64_t *d_q_ptr,
+                                   const int32_t *d_q_ids, const float *d_r,
+                                   const int64_t *d_x_ptr, const int32_t *d_x_ids,
+                                   const float *d_c, int32_t max_q_words, int32_t max_x_words,
+                                   float lambda, int32_t max_iter, float tol, double *d_out,
+                                   int32_t *d_iters, int32_t *d_status, void *stream);
+
 /* Copies a workspace array to host memory for inspection (tests):
  *   what 0: K^T  [V_used][v_r] as float (FP32/BF16/FP16 widened)
  *   what 1: KM^T [V_used][v_r] as float

@@ -101,6 +101,11 @@ _SIGS = {
     "swmd_autotune": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P]),
     "swmd_resolve_path": (ctypes.c_int, [P, ctypes.c_int32, P]),
     "swmd_last_iterations": (ctypes.c_int, [P, P]),
+    "swmd_wmd_pairs": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P, P, P, ctypes.c_float,
+                                      ctypes.c_int32, ctypes.c_float, P, P]),
+    "swmd_wmd_pairs_device": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P, P, P, ctypes.c_int32,
+                                             ctypes.c_int32, ctypes.c_float, ctypes.c_int32,
+                                             ctypes.c_float, P, P, P, P]),
     "swmd_default_serve_config": (None, [P]),
     "swmd_serve_start": (ctypes.c_int, [P, P, P]),
     "swmd_serve_submit": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.c_float, ctypes.c_int32,
@@ -369,6 +374,48 @@ def swmd_autotune(corpus: Corpus, v_r: int, reps: int = 5) -> dict:
     _err(lib().swmd_autotune(corpus.handle, int(v_r), int(reps), ctypes.byref(res)),
          "swmd_autotune")
     return {f: getattr(res, f) for f, _ in swmd_tune_result._fields_}
+
+
+def _ragged(sides):
+    """[(ids, weights), ...] -> (ptr int64[n+1], ids int32, weights float32)."""
+    ptr = np.zeros(len(sides) + 1, np.int64)
+    for i, (ids, _) in enumerate(sides):
+        ptr[i + 1] = ptr[i] + len(ids)
+    if sides:
+        ids = np.concatenate([np.asarray(s[0], np.int32).ravel() for s in sides])
+        w = np.concatenate([np.asarray(s[1], np.float32).ravel() for s in sides])
+    else:
+        ids, w = np.zeros(0, np.int32), np.zeros(0, np.float32)
+    return ptr, np.ascontiguousarray(ids), np.ascontiguousarray(w)
+
+
+def swmd_wmd_pairs(corpus: Corpus, queries, targets, lam: float, max_iter: int, tol: float = 0.0,
+                   want_iters: bool = False):
+    """1-to-1 WMD (Table II): distance of queries[p] to targets[p], each an (ids, weights)
+    histogram over the corpus's vocabulary.  Returns float64[n] (and int32[n] x-updates)."""
+    if len(queries) != len(targets):
+        raise ValueError("swmd_wmd_pairs: as many queries as targets")
+    n = len(queries)
+    qp, qi, qw = _ragged(queries)
+    xp, xi, xw = _ragged(targets)
+    out = np.empty(n, np.float64)
+    its = np.empty(n, np.int32)
+    _err(lib().swmd_wmd_pairs(corpus.handle, n, qp.ctypes.data_as(P), qi.ctypes.data_as(P),
+                              qw.ctypes.data_as(P), xp.ctypes.data_as(P), xi.ctypes.data_as(P),
+                              xw.ctypes.data_as(P), float(lam), int(max_iter), float(tol),
+                              out.ctypes.data_as(P), its.ctypes.data_as(P)), "swmd_wmd_pairs")
+    return (out, its) if want_iters else out
+
+
+def swmd_wmd_pairs_device(corpus: Corpus, n_pairs: int, d_q_ptr, d_q_ids, d_r, d_x_ptr, d_x_ids,
+                          d_c, max_q_words: int, max_x_words: int, lam: float, max_iter: int,
+                          d_out, d_status, tol: float = 0.0, d_iters=None, stream=None):
+    """swmd_wmd_pairs on selected, normalised sides already in device memory."""
+    _err(lib().swmd_wmd_pairs_device(corpus.handle, int(n_pairs), _dptr(d_q_ptr), _dptr(d_q_ids),
+                                     _dptr(d_r), _dptr(d_x_ptr), _dptr(d_x_ids), _dptr(d_c),
+                                     int(max_q_words), int(max_x_words), float(lam),
+                                     int(max_iter), float(tol), _dptr(d_out), _dptr(d_iters),
+                                     _dptr(d_status), _stream(stream)), "swmd_wmd_pairs_device")
 
 
 class Server:

@@ -36,19 +36,6 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 namespace {
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 template <class T>
 int dev_alloc(T **p, size_t count, int64_t *bytes) {
     *p = nullptr;
@@ -77,6 +64,8 @@ void clear_graphs(swmd_corpus *c) {
 int status_to_code(int st) {
     if (st & (ST_BAD_ID | ST_BAD_R))
         return set_error(SWMD_EINVAL, "query id outside [0, V) or weight not finite and > 0");
+    if (st & ST_BAD_SIZE)
+        return set_error(SWMD_EINVAL, "a pair side is empty or above its declared size bound");
     if (st & ST_NUMERIC)
         return set_error(SWMD_ENUMERIC, "a NaN, an infinity or a vanished K^T u appeared");
     return SWMD_OK;
@@ -705,6 +694,8 @@ void swmd_destroy_corpus(swmd_corpus *c) {
         clear_graphs(c);
         free_slot(c->main);
         dev_free(c->batch_ws);
+        dev_free(c->pair_ws);
+        dev_free(c->pair_kws);
         dev_free(c->E);
         dev_free(c->used);
         dev_free(c->doc_ptr);

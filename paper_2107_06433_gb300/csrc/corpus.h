@@ -17,6 +17,21 @@
 namespace swmd {
 
 int set_error(int code, const char *fmt, ...);
+
+// Makes `dev` the current device for a scope and restores the caller's device after.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 int cuda_fail(cudaError_t e, const char *what);
 
 #define SWMD_CK(call)                                        \
@@ -101,6 +116,10 @@ struct swmd_corpus {
     swmd::Slot main;               // workspace of the single-query path
     void *batch_ws = nullptr;      // workspace of swmd_query_batch (grown on demand)
     size_t batch_ws_bytes = 0;
+    void *pair_ws = nullptr;       // swmd_wmd_pairs: packed pairs, results, status (grown on demand)
+    size_t pair_ws_bytes = 0;
+    float *pair_kws = nullptr;     // 1-to-1 pairs: per-block K and K.*M regions too large
+    size_t pair_kws_bytes = 0;     // for shared memory (grown on demand)
     int64_t base_bytes = 0;
 
     std::map<swmd::GraphKey, cudaGraphExec_t> graphs;
@@ -148,6 +167,26 @@ constexpr int kNumTileBudgets = 10;
 int build_tiles(swmd_corpus *c);
 // Builds the register-resident solver's warp task lists (at corpus creation).
 int build_tasks(swmd_corpus *c);
+// 1-to-1 pairs (pairs.cu): enqueues the distances of n_pairs selected, normalised
+// (query, target) pairs held in device memory; max_q / max_x bound every pair's sizes.
+struct PairJob {
+    int n_pairs;
+    const int64_t *q_ptr;
+    const int *q_ids;
+    const float *r;
+    const int64_t *x_ptr;
+    const int *x_ids;
+    const float *cx;
+    int max_q, max_x;
+    float lambda;
+    int t;
+    float tol;
+    double *out;
+    int *iters;     // may be NULL
+    int *status;
+};
+constexpr int kPairMaxWords = 4096;
+int enqueue_pairs(swmd_corpus *c, const PairJob &job, cudaStream_t st);
 // Effective resident settings for a layout: explicit options, else autotuned, else defaults.
 void resident_settings(swmd_corpus *c, int vrp, int kprec, int *solver, int *npl_want, int *split);
 

@@ -33,19 +33,6 @@ void *g_scratch_ptr[kMaxDevices] = {};
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 }  // namespace
 
 using namespace swmd;

@@ -5,6 +5,8 @@ import os
 import re
 import subprocess
 
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -31,7 +33,8 @@ def test_header_declares_the_boundary():
     for required in ("swmd_create_corpus", "swmd_destroy_corpus", "swmd_query",
                      "swmd_query_batch", "swmd_serve_start", "swmd_serve_submit",
                      "swmd_serve_wait", "swmd_serve_stats", "swmd_serve_stop", "swmd_last_error",
-                     "swmd_autotune", "swmd_query_noalloc"):
+                     "swmd_autotune", "swmd_query_noalloc", "swmd_wmd_pairs",
+                     "swmd_wmd_pairs_device"):
         assert required in names
 
 
@@ -125,3 +128,13 @@ def test_options_marshalling(lib):
     assert (o.path, o.k_precision, o.cost_split) == (swmd.PATH_FUSED, swmd.K_BF16, 1)
     assert abs(o.tol - 1e-6) < 1e-12
     assert swmd.swmd_default_options().tol == 0.0
+
+
+def test_pair_calls_check_arguments_before_the_gpu(lib):
+    """The 1-to-1 entry points refuse a NULL corpus and a negative pair count
+    without a CUDA call."""
+    z = ctypes.c_void_p()
+    assert lib.swmd_wmd_pairs(None, 1, z, z, z, z, z, z, 1.0, 15, 0.0, z, z) == swmd.SWMD_EINVAL
+    assert b"NULL corpus" in lib.swmd_last_error()
+    assert lib.swmd_wmd_pairs_device(None, 1, z, z, z, z, z, z, 8, 8, 1.0, 15, 0.0, z, z, z,
+                                     None) == swmd.SWMD_EINVAL
