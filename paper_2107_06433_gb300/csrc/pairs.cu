@@ -8,16 +8,17 @@
 // One block of 128 threads owns one pair at a time (a grid-stride loop over pairs)
 // and runs every step of Algorithm 1 for it on chip:
 //   cost   M[k][j] = ||E[q_k] - E[x_j]||_2 for the v_r x v_x block, tiled 4 KPT query
-//          words x 32 target words, embedding dimensions staged 32 at a time in
-//          shared memory (FP32, direct difference form, two-wide FMAs);
+//          words x 64 target words (two per lane), embedding dimensions staged 32 at
+//          a time in shared memory, the next chunk already in flight in registers
+//          while the current one is used (FP32, direct difference form, two-wide FMAs);
 //          K = exp(-lambda (M - m_j)) with the column shift m_j = min_k M[k][j]
 //          when the corpus uses it (an exact rescaling of column j), KM = K .* M;
 //          K and KM stay in shared memory when they fit, else in a per-block
 //          region of global memory that L1 holds;
 //   iterate v_j = c_j / (K^T u)_j (SDDMM, one thread per target word, the FP64
-//          guard below 2^-100 as on the 1-to-N path), y = K v (SpMM, threads over
-//          query words, target words split over groups and summed in a fixed
-//          order), u = r / y -- t times, or until max_k |u_k y_k - r_k| < tol;
+//          guard below 2^-100 as on the 1-to-N path), y = K v (SpMM, one warp per
+//          query word, lanes over target words, a fixed-order shuffle sum), u = r / y
+//          -- t times, or until max_k |u_k y_k - r_k| < tol;
 //   final  WMD = sum_j c_j (KM^T u)_j / (K^T u)_j, summed in FP64 in a fixed order.
 // K and KM are kept as [target word j][query word k] with an odd row stride, so the
 // SDDMM's lanes (over j) and the SpMM's lanes (over k) both read distinct banks.
@@ -34,7 +35,7 @@ namespace swmd {
 namespace {
 
 constexpr int kPT = 128;   // threads per block
-constexpr int kPJ = 32;    // target words per cost tile (one per lane)
+constexpr int kPJ = 64;    // target words per cost tile (two per lane)
 constexpr int kPD = 32;    // embedding dimensions per staged chunk
 // K and KM of the largest pair go to shared memory up to this many bytes
 constexpr size_t kPairSmemK = 48 * 1024;
@@ -69,7 +70,7 @@ __host__ __device__ inline PairLayout pair_layout(int max_q, int max_x, int tkk,
     int off = 64;   // 4 doubles of the final sum, 4 floats of the marginal error, a flag word
     L.u = take_floats(off, max_q);
     L.rr = take_floats(off, max_q);
-    L.red = take_floats(off, max_q > kPT ? max_q : kPT);
+    L.red = take_floats(off, max_q);
     L.v = take_floats(off, max_x);
     L.cw = take_floats(off, max_x);
     L.sq = take_floats(off, kPD * tkk);
@@ -85,20 +86,64 @@ __device__ __forceinline__ float2 sqdiff2(float2 q, float x, float2 acc) {
     return __ffma2_rn(t, t, acc);
 }
 
+// One d-chunk of the cost tile: kPJ target rows and TKK query rows, kPD dimensions,
+// as float4s per thread (rows of 8 float4, consecutive threads along a row).
+constexpr int kPX4 = kPJ * (kPD / 4) / kPT;   // float4s of target rows per thread
+template <int TKK>
+struct Chunk {
+    static constexpr int NQ = (TKK * (kPD / 4) + kPT - 1) / kPT;
+    float4 x[kPX4];
+    float4 q[NQ];
+};
+
+template <int TKK>
+__device__ __forceinline__ void load_chunk(Chunk<TKK> &c, const float *E, int d4, int d0,
+                                           const int *xid, int jt, int vx, const int *qid, int kt,
+                                           int vr, int tid) {
+    const int dl = min(kPD, d4 - d0);   // a multiple of 4
+#pragma unroll
+    for (int i = 0; i < kPX4; ++i) {
+        const int e = tid + i * kPT, row = e / (kPD / 4), seg = e % (kPD / 4);
+        c.x[i] = (jt + row < vx && 4 * seg < dl)
+                     ? __ldg(reinterpret_cast<const float4 *>(E + (long)xid[jt + row] * d4 + d0 + 4 * seg))
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < Chunk<TKK>::NQ; ++i) {
+        const int e = tid + i * kPT, row = e / (kPD / 4), seg = e % (kPD / 4);
+        c.q[i] = (e < TKK * (kPD / 4) && kt + row < vr && 4 * seg < dl)
+                     ? __ldg(reinterpret_cast<const float4 *>(E + (long)qid[kt + row] * d4 + d0 + 4 * seg))
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// Sx [kPJ][kPD + 1] (dimension fastest), Sq [kPD][TKK] (query word fastest)
+template <int TKK>
+__device__ __forceinline__ void store_chunk(const Chunk<TKK> &c, float *Sx, float *Sq, int tid) {
+#pragma unroll
+    for (int i = 0; i < kPX4; ++i) {
+        const int e = tid + i * kPT, row = e / (kPD / 4), seg = e % (kPD / 4);
+        float *dst = Sx + row * (kPD + 1) + 4 * seg;
+        dst[0] = c.x[i].x; dst[1] = c.x[i].y; dst[2] = c.x[i].z; dst[3] = c.x[i].w;
+    }
+#pragma unroll
+    for (int i = 0; i < Chunk<TKK>::NQ; ++i) {
+        const int e = tid + i * kPT, row = e / (kPD / 4), seg = e % (kPD / 4);
+        if (e < TKK * (kPD / 4)) {
+            float *dst = Sq + (4 * seg) * TKK + row;
+            dst[0] = c.q[i].x; dst[TKK] = c.q[i].y; dst[2 * TKK] = c.q[i].z; dst[3 * TKK] = c.q[i].w;
+        }
+    }
+}
+
 __device__ __forceinline__ float warp_min(float x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
     return x;
 }
 
-__device__ __forceinline__ float warp_max(float x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
-    return x;
-}
-
 template <int KPT, bool SMEMK>
-__global__ void __launch_bounds__(kPT, 6) k_pairs(const __grid_constant__ PairArgs a) {
+__global__ void __launch_bounds__(kPT, 4) k_pairs(const __grid_constant__ PairArgs a) {
     constexpr int TKK = 4 * KPT;   // query words per cost tile: KPT per warp
     extern __shared__ __align__(16) unsigned char smem[];
     const PairJob &J = a.job;
@@ -170,49 +215,43 @@ __global__ void __launch_bounds__(kPT, 6) k_pairs(const __grid_constant__ PairAr
         // ---- cost: M for the v_r x v_x block, written to KMb first
         for (int jt = 0; jt < vx; jt += kPJ) {
             for (int kt = 0; kt < vr; kt += TKK) {
-                float2 acc[KPT / 2];
+                float2 acc0[KPT / 2], acc1[KPT / 2];   // target words jt + lane, jt + 32 + lane
 #pragma unroll
-                for (int i = 0; i < KPT / 2; ++i) acc[i] = make_float2(0.f, 0.f);
+                for (int i = 0; i < KPT / 2; ++i) acc0[i] = acc1[i] = make_float2(0.f, 0.f);
+                Chunk<TKK> ch;
+                load_chunk<TKK>(ch, a.E, a.d4, 0, xid, jt, vx, qid, kt, vr, tid);
                 for (int d0 = 0; d0 < a.d4; d0 += kPD) {
-                    const int dl = min(kPD, a.d4 - d0);   // a multiple of 4
+                    const int dl = min(kPD, a.d4 - d0);
                     __syncthreads();   // the previous chunk's readers are done
-                    for (int e = tid; e < kPJ * (kPD / 4); e += kPT) {
-                        const int row = e / (kPD / 4), seg = e % (kPD / 4);
-                        float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (jt + row < vx && 4 * seg < dl)
-                            val = __ldg(reinterpret_cast<const float4 *>(
-                                a.E + (long)xid[jt + row] * a.d4 + d0 + 4 * seg));
-                        float *dst = Sx + row * (kPD + 1) + 4 * seg;
-                        dst[0] = val.x; dst[1] = val.y; dst[2] = val.z; dst[3] = val.w;
-                    }
-                    for (int e = tid; e < TKK * (kPD / 4); e += kPT) {
-                        const int row = e / (kPD / 4), seg = e % (kPD / 4);
-                        float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (kt + row < vr && 4 * seg < dl)
-                            val = __ldg(reinterpret_cast<const float4 *>(
-                                a.E + (long)qid[kt + row] * a.d4 + d0 + 4 * seg));
-                        float *dst = Sq + (4 * seg) * TKK + row;
-                        dst[0] = val.x; dst[TKK] = val.y; dst[2 * TKK] = val.z; dst[3 * TKK] = val.w;
-                    }
+                    store_chunk<TKK>(ch, Sx, Sq, tid);
                     __syncthreads();
-                    const float *sx = Sx + lane * (kPD + 1);
+                    if (d0 + kPD < a.d4)   // the next chunk is in flight during this one's FMAs
+                        load_chunk<TKK>(ch, a.E, a.d4, d0 + kPD, xid, jt, vx, qid, kt, vr, tid);
+                    const float *sx0 = Sx + lane * (kPD + 1);
+                    const float *sx1 = Sx + (lane + 32) * (kPD + 1);
                     const float *sq = Sq + w * KPT;
 #pragma unroll 4
                     for (int dd = 0; dd < dl; ++dd) {
-                        const float xv = sx[dd];
+                        const float x0 = sx0[dd], x1 = sx1[dd];
 #pragma unroll
-                        for (int i = 0; i < KPT / 2; ++i)
-                            acc[i] = sqdiff2(*reinterpret_cast<const float2 *>(sq + dd * TKK + 2 * i), xv,
-                                             acc[i]);
+                        for (int i = 0; i < KPT / 2; ++i) {
+                            const float2 q2 = *reinterpret_cast<const float2 *>(sq + dd * TKK + 2 * i);
+                            acc0[i] = sqdiff2(q2, x0, acc0[i]);
+                            acc1[i] = sqdiff2(q2, x1, acc1[i]);
+                        }
                     }
                 }
-                const int j = jt + lane;
-                if (j < vx) {
 #pragma unroll
-                    for (int i = 0; i < KPT / 2; ++i) {
-                        const int k = kt + w * KPT + 2 * i;
-                        if (k < vr) KMb[j * VRS + k] = sqrtf(acc[i].x);
-                        if (k + 1 < vr) KMb[j * VRS + k + 1] = sqrtf(acc[i].y);
+                for (int h = 0; h < 2; ++h) {
+                    const int j = jt + lane + 32 * h;
+                    if (j < vx) {
+#pragma unroll
+                        for (int i = 0; i < KPT / 2; ++i) {
+                            const int k = kt + w * KPT + 2 * i;
+                            const float2 m2 = h ? acc1[i] : acc0[i];
+                            if (k < vr) KMb[j * VRS + k] = sqrtf(m2.x);
+                            if (k + 1 < vr) KMb[j * VRS + k + 1] = sqrtf(m2.y);
+                        }
                     }
                 }
             }
@@ -234,11 +273,10 @@ __global__ void __launch_bounds__(kPT, 6) k_pairs(const __grid_constant__ PairAr
         __syncthreads();
 
         // ---- iterations
-        const int TK = vr <= 32 ? 32 : (vr <= 64 ? 64 : kPT);   // SpMM threads over k
-        const int G = kPT / TK;                                  // ... and groups over j
+        const bool conv = J.tol > 0.f;
         int it = 0;
         for (;;) {
-            if (!(J.tol > 0.f) && it == J.t) break;
+            if (!conv && it == J.t) break;
             // SDDMM: v_j = c_j / (K^T u)_j
             for (int j = tid; j < vx; j += kPT) {
                 const float *kr = Kb + j * VRS;
@@ -256,40 +294,36 @@ __global__ void __launch_bounds__(kPT, 6) k_pairs(const __grid_constant__ PairAr
                 v[j] = vj;
             }
             __syncthreads();
-            // SpMM: partial y_k over this thread's group of target words
-            {
-                const int g = tid / TK, kk = tid % TK;
-                for (int k = kk; k < vr; k += TK) {
-                    float part = 0.f;
-                    for (int j = g; j < vx; j += G) part = fmaf(Kb[j * VRS + k], v[j], part);
-                    red[g * TK + k] = part;
-                }
-            }
-            __syncthreads();
+            // SpMM y_k = sum_j K[k, j] v_j, one warp per query word; then x = K_over_r v,
+            // u = 1 / x, i.e. u_k = r_k / y_k -- at once, or after the stopping test
             float errl = 0.f;
-            for (int k = tid; k < vr; k += kPT) {
-                float y = red[k];
-                for (int g = 1; g < G; ++g) y += red[g * TK + k];
-                if (J.tol > 0.f) {
-                    const float e = fabsf(u[k] * y - rr[k]);
+            for (int k = w; k < vr; k += kPT / 32) {
+                float part = 0.f;
+                for (int j = lane; j < vx; j += 32) part = fmaf(Kb[j * VRS + k], v[j], part);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                if (conv) {
+                    const float e = fabsf(u[k] * part - rr[k]);
                     errl = fmaxf(errl, e <= FLT_MAX ? e : INFINITY);
+                    if (lane == 0) red[k] = part;
+                } else if (lane == 0) {
+                    const float nu = rr[k] / part;
+                    if (!(nu < INFINITY)) atomicOr(J.status, ST_NUMERIC);
+                    u[k] = nu;
                 }
-                red[k] = y;
             }
-            if (J.tol > 0.f) {
+            if (conv) {
                 // "while x changes" (Algorithm 1): stop once the row marginal of
                 // P = diag(u) K diag(v) is within tol of r, or after t updates
-                errl = warp_max(errl);
                 if (lane == 0) errw[w] = errl;
                 __syncthreads();
                 const float err = fmaxf(fmaxf(errw[0], errw[1]), fmaxf(errw[2], errw[3]));
                 if (err < J.tol || it == J.t) break;
-            }
-            // x = K_over_r v and u = 1 / x, i.e. u_k = r_k / y_k
-            for (int k = tid; k < vr; k += kPT) {
-                const float nu = rr[k] / red[k];
-                if (!(nu < INFINITY)) atomicOr(J.status, ST_NUMERIC);
-                u[k] = nu;
+                for (int k = tid; k < vr; k += kPT) {
+                    const float nu = rr[k] / red[k];
+                    if (!(nu < INFINITY)) atomicOr(J.status, ST_NUMERIC);
+                    u[k] = nu;
+                }
             }
             ++it;
             __syncthreads();
