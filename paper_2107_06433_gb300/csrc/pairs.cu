@@ -136,6 +136,19 @@ __device__ __forceinline__ void store_chunk(const Chunk<TKK> &c, float *Sx, floa
     }
 }
 
+// K^T[j] . u over the pair's query words: two interleaved partial sums (even and odd
+// k), added at the end -- a fixed order for every pair.
+__device__ __forceinline__ float dot_ku(const float *kr, const float *u, int vr) {
+    float s0 = 0.f, s1 = 0.f;
+    int k = 0;
+    for (; k + 1 < vr; k += 2) {
+        s0 = fmaf(kr[k], u[k], s0);
+        s1 = fmaf(kr[k + 1], u[k + 1], s1);
+    }
+    if (k < vr) s0 = fmaf(kr[k], u[k], s0);
+    return s0 + s1;
+}
+
 __device__ __forceinline__ float warp_min(float x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
@@ -218,6 +231,7 @@ __global__ void __launch_bounds__(kPT, 4) k_pairs(const __grid_constant__ PairAr
                 float2 acc0[KPT / 2], acc1[KPT / 2];   // target words jt + lane, jt + 32 + lane
 #pragma unroll
                 for (int i = 0; i < KPT / 2; ++i) acc0[i] = acc1[i] = make_float2(0.f, 0.f);
+                const bool two = jt + 32 < vx;   // block-uniform
                 Chunk<TKK> ch;
                 load_chunk<TKK>(ch, a.E, a.d4, 0, xid, jt, vx, qid, kt, vr, tid);
                 for (int d0 = 0; d0 < a.d4; d0 += kPD) {
@@ -230,14 +244,25 @@ __global__ void __launch_bounds__(kPT, 4) k_pairs(const __grid_constant__ PairAr
                     const float *sx0 = Sx + lane * (kPD + 1);
                     const float *sx1 = Sx + (lane + 32) * (kPD + 1);
                     const float *sq = Sq + w * KPT;
+                    if (two) {
 #pragma unroll 4
-                    for (int dd = 0; dd < dl; ++dd) {
-                        const float x0 = sx0[dd], x1 = sx1[dd];
+                        for (int dd = 0; dd < dl; ++dd) {
+                            const float x0 = sx0[dd], x1 = sx1[dd];
 #pragma unroll
-                        for (int i = 0; i < KPT / 2; ++i) {
-                            const float2 q2 = *reinterpret_cast<const float2 *>(sq + dd * TKK + 2 * i);
-                            acc0[i] = sqdiff2(q2, x0, acc0[i]);
-                            acc1[i] = sqdiff2(q2, x1, acc1[i]);
+                            for (int i = 0; i < KPT / 2; ++i) {
+                                const float2 q2 = *reinterpret_cast<const float2 *>(sq + dd * TKK + 2 * i);
+                                acc0[i] = sqdiff2(q2, x0, acc0[i]);
+                                acc1[i] = sqdiff2(q2, x1, acc1[i]);
+                            }
+                        }
+                    } else {   // the tile's second 32 target words are all past v_x
+#pragma unroll 4
+                        for (int dd = 0; dd < dl; ++dd) {
+                            const float x0 = sx0[dd];
+#pragma unroll
+                            for (int i = 0; i < KPT / 2; ++i)
+                                acc0[i] = sqdiff2(*reinterpret_cast<const float2 *>(sq + dd * TKK + 2 * i), x0,
+                                                  acc0[i]);
                         }
                     }
                 }
@@ -280,11 +305,10 @@ __global__ void __launch_bounds__(kPT, 4) k_pairs(const __grid_constant__ PairAr
             // SDDMM: v_j = c_j / (K^T u)_j
             for (int j = tid; j < vx; j += kPT) {
                 const float *kr = Kb + j * VRS;
-                float s = 0.f;
-                for (int k = 0; k < vr; ++k) s = fmaf(kr[k], u[k], s);
+                const float s = dot_ku(kr, u, vr);
                 float vj;
                 if (s >= 0x1p-100f) {
-                    vj = cw[j] / s;
+                    vj = __fdividef(cw[j], s);
                 } else {
                     double sd = 0.0;
                     for (int k = 0; k < vr; ++k) sd += (double)kr[k] * (double)u[k];
@@ -307,7 +331,7 @@ __global__ void __launch_bounds__(kPT, 4) k_pairs(const __grid_constant__ PairAr
                     errl = fmaxf(errl, e <= FLT_MAX ? e : INFINITY);
                     if (lane == 0) red[k] = part;
                 } else if (lane == 0) {
-                    const float nu = rr[k] / part;
+                    const float nu = __fdividef(rr[k], part);
                     if (!(nu < INFINITY)) atomicOr(J.status, ST_NUMERIC);
                     u[k] = nu;
                 }
@@ -320,7 +344,7 @@ __global__ void __launch_bounds__(kPT, 4) k_pairs(const __grid_constant__ PairAr
                 const float err = fmaxf(fmaxf(errw[0], errw[1]), fmaxf(errw[2], errw[3]));
                 if (err < J.tol || it == J.t) break;
                 for (int k = tid; k < vr; k += kPT) {
-                    const float nu = rr[k] / red[k];
+                    const float nu = __fdividef(rr[k], red[k]);
                     if (!(nu < INFINITY)) atomicOr(J.status, ST_NUMERIC);
                     u[k] = nu;
                 }
@@ -334,13 +358,9 @@ __global__ void __launch_bounds__(kPT, 4) k_pairs(const __grid_constant__ PairAr
         for (int j = tid; j < vx; j += kPT) {
             const float *kr = Kb + j * VRS;
             const float *mr = KMb + j * VRS;
-            float s = 0.f, sm = 0.f;
-            for (int k = 0; k < vr; ++k) {
-                s = fmaf(kr[k], u[k], s);
-                sm = fmaf(mr[k], u[k], sm);
-            }
+            const float s = dot_ku(kr, u, vr), sm = dot_ku(mr, u, vr);
             if (s >= 0x1p-100f) {
-                dsum += (double)(cw[j] * (sm / s));
+                dsum += (double)(cw[j] * __fdividef(sm, s));
             } else {
                 double sd = 0.0, md = 0.0;
                 for (int k = 0; k < vr; ++k) {
