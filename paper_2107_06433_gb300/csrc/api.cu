@@ -89,12 +89,15 @@ int alloc_slot(swmd_corpus *c, Slot &s, int max_vr, int kprec, bool with_v) {
     if ((rc = dev_alloc(&s.q_ids, vrp, &s.bytes))) return rc;
     if ((rc = dev_alloc(&s.r, vrp, &s.bytes))) return rc;
     if ((rc = dev_alloc(&s.qp, 1, &s.bytes))) return rc;
-    if ((rc = dev_alloc(&s.out, (size_t)std::max(c->Nl, 1), &s.bytes))) return rc;
-    if ((rc = dev_alloc(&s.status, 1, &s.bytes))) return rc;
+    // the distances and, right after them, the status word: one device-to-host copy
+    if ((rc = dev_alloc(&s.out, (size_t)std::max(c->Nl, 1) + 1, &s.bytes))) return rc;
+    s.status = reinterpret_cast<int *>(s.out + std::max(c->Nl, 1));
     if ((rc = dev_alloc(&s.conv, 1 + kMaxConvIters, &s.bytes))) return rc;
     SWMD_CK(cudaMemset(s.conv, 0, sizeof(unsigned) * (1 + kMaxConvIters)));
-    if ((rc = dev_alloc(&s.q_in, vrp, &s.bytes))) return rc;
-    if ((rc = dev_alloc(&s.r_in, vrp, &s.bytes))) return rc;
+    // the staged query ids and, right after them, its weights: one host-to-device copy
+    if ((rc = dev_alloc(&s.q_in, 2 * (size_t)vrp, &s.bytes))) return rc;
+    s.r_in = reinterpret_cast<float *>(s.q_in + vrp);
+    s.carved_io = true;
     SWMD_CK(cudaMemset(s.u, 0, (size_t)std::max(c->Nl, 1) * vrp * sizeof(float)));
     s.vrp_cap = vrp;
     s.kprec = kprec;
@@ -103,9 +106,12 @@ int alloc_slot(swmd_corpus *c, Slot &s, int max_vr, int kprec, bool with_v) {
 
 void free_slot(Slot &s) {
     dev_free(s.KT); dev_free(s.KMT); dev_free(s.u); dev_free(s.v); dev_free(s.q_ids);
-    dev_free(s.r); dev_free(s.qp); dev_free(s.out); dev_free(s.status); dev_free(s.q_in);
+    dev_free(s.r); dev_free(s.qp); dev_free(s.out); dev_free(s.q_in);
     dev_free(s.conv);
-    dev_free(s.r_in);
+    if (!s.carved_io) {   // else they live inside out / q_in
+        dev_free(s.status);
+        dev_free(s.r_in);
+    }
     s = Slot{};
 }
 
@@ -682,6 +688,11 @@ int swmd_create_corpus(int32_t V, int32_t N, int64_t nnz, const int64_t *row_ptr
     if ((rc = build_tasks(c))) return bail(rc);
     if ((rc = alloc_slot(c, c->main, opt.max_vr, opt.k_precision, opt.path == SWMD_PATH_PLAIN)))
         return bail(rc);
+    // pinned staging of swmd_query: the query (ids, weights) in, the distances and status out
+    c->h_io_in_bytes = sizeof(int32_t) * 2 * (size_t)c->main.vrp_cap;
+    if ((ce = cudaMallocHost(&c->h_io, c->h_io_in_bytes + sizeof(double) * ((size_t)std::max(Nl, 1) + 1))) !=
+        cudaSuccess)
+        return bail(cuda_fail(ce, "pinned staging buffer"));
     *out = c;
     return SWMD_OK;
 }
@@ -705,6 +716,7 @@ void swmd_destroy_corpus(swmd_corpus *c) {
         dev_free(c->doc_orig);
         dev_free(c->tiles_dev);
         dev_free(c->tasks_dev);
+        if (c->h_io) cudaFreeHost(c->h_io);
         if (c->stream) cudaStreamDestroy(c->stream);
     }
     delete c;
@@ -777,14 +789,21 @@ int swmd_query(swmd_corpus *c, const int32_t *h_word_ids, const float *h_weights
     DeviceGuard guard(c->device);
     Slot &s = c->main;
     cudaStream_t st = c->stream;
-    SWMD_CK(cudaMemcpyAsync(s.q_in, ids.data(), sizeof(int32_t) * vr, cudaMemcpyHostToDevice, st));
-    SWMD_CK(cudaMemcpyAsync(s.r_in, r.data(), sizeof(float) * vr, cudaMemcpyHostToDevice, st));
+    // one pinned copy in (ids at 0, weights at vrp_cap) and one out (distances, then the
+    // status word): the slot's q_in / r_in and out / status are laid out the same way
+    int32_t *h_in = static_cast<int32_t *>(c->h_io);
+    std::memcpy(h_in, ids.data(), sizeof(int32_t) * vr);
+    std::memcpy(h_in + s.vrp_cap, r.data(), sizeof(float) * vr);
+    SWMD_CK(cudaMemcpyAsync(s.q_in, h_in, sizeof(int32_t) * (size_t)(s.vrp_cap + vr),
+                            cudaMemcpyHostToDevice, st));
     if ((rc = enqueue_query(c, s, s.q_in, s.r_in, vr, lambda, max_iter, s.out, s.status, st, true)))
         return rc;
-    int h_status = 0;
-    SWMD_CK(cudaMemcpyAsync(h_out_dist, s.out, sizeof(double) * c->Nl, cudaMemcpyDeviceToHost, st));
-    SWMD_CK(cudaMemcpyAsync(&h_status, s.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    double *h_res = reinterpret_cast<double *>(static_cast<char *>(c->h_io) + c->h_io_in_bytes);
+    SWMD_CK(cudaMemcpyAsync(h_res, s.out, sizeof(double) * c->Nl + sizeof(int), cudaMemcpyDeviceToHost, st));
     SWMD_CK(cudaStreamSynchronize(st));
+    std::memcpy(h_out_dist, h_res, sizeof(double) * c->Nl);
+    int h_status = 0;
+    std::memcpy(&h_status, h_res + c->Nl, sizeof(int));
     return status_to_code(h_status);
 }
 

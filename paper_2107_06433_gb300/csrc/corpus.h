@@ -65,6 +65,7 @@ struct Slot {
     float *r_in = nullptr;
     int64_t bytes = 0;
     bool external = false;   // buffers managed by a server (never reallocated here)
+    bool carved_io = false;  // status follows out, r_in follows q_in (vrp_cap ints) in one allocation
     int cur_vrp = 0;         // padding of the K^T layout the last query / cost step wrote
     int cur_vr = 0;          // ... and the query size it was written for
     int last_t = 0;          // max_iter and path of the last query enqueued on the slot
@@ -121,6 +122,8 @@ struct swmd_corpus {
     float *pair_kws = nullptr;     // 1-to-1 pairs: per-block K and K.*M regions too large
     size_t pair_kws_bytes = 0;     // for shared memory (grown on demand)
     int64_t base_bytes = 0;
+    void *h_io = nullptr;          // pinned staging of swmd_query: [ids | weights] then [distances | status]
+    size_t h_io_in_bytes = 0;
 
     std::map<swmd::GraphKey, cudaGraphExec_t> graphs;
     std::map<std::vector<int64_t>, cudaGraphExec_t> batch_graphs;   // swmd_query_batch shapes
