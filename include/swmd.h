@@ -386,7 +386,9 @@ SWMD_API int swmd_autotune(swmd_corpus *corpus, int32_t v_r, int32_t reps, swmd_
  *   h_out[n_queries * N] (double, host): row i = the distances of query i.
  * Each query takes its own path (swmd_resolve_path).  The resident queries of one
  * K^T layout run as one batched cost launch and one batched solver launch (grid
- * row y = query y); the per-iteration queries run one after another.  The device
+ * row y = query y) on corpora under 20,000 documents, where one query leaves the
+ * GPU partly idle; on larger corpora, where one query fills it, they run one launch
+ * pair per query.  The per-iteration queries run one after another.  The device
  * work of the whole call is captured once per batch shape (the queries' paths and
  * sizes, the per-iteration queries' lambdas, max_iter) as a CUDA graph and replayed
  * on the next batch of that shape.  The workspace grows on demand (cudaMalloc) and

@@ -305,7 +305,8 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
 
     // Each query takes its own path (resolve_path: a function of v_r and the
     // tuning).  Resident queries of one layout run as one batched cost launch and
-    // one batched solver launch; per-iteration queries run one after another on
+    // one batched solver launch (on corpora of kAutoResidentDocs documents and more,
+    // as one launch pair per query); per-iteration queries run one after another on
     // the corpus's slot.
     std::vector<int> path((size_t)n_queries), vrp((size_t)n_queries, 0);
     std::map<int, std::vector<int>> groups;   // layout VRP -> resident queries
@@ -457,11 +458,20 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
                 const size_t g0 = gstart[gi].second;
                 const int ng = (int)groups[v].size();
                 const Mapping m = walk_mapping(c, v, SWMD_PATH_RESIDENT);
-                SWMD_CK(launch_cost_batch(cost_g[g0], v, kprec, ng,
-                                          reinterpret_cast<const CostArgs *>(ws + o_cost) + g0, st));
-                int rc = run_resident_batch(c, res_g[g0], m, kprec, ng,
-                                            reinterpret_cast<const ResidentArgs *>(ws + o_res) + g0, st);
-                if (rc) return rc;
+                // From kAutoResidentDocs documents up one query's launches fill the GPU
+                // many times over, and queries run side by side only compete for L2
+                // (each gathers its own K^T); there the group's queries run one after
+                // another (still one graph, no host round trips).  Smaller corpora run
+                // the group as one batched cost and one batched solver launch.
+                const int step = c->Nl >= kAutoResidentDocs ? 1 : ng;
+                for (int j0 = 0; j0 < ng; j0 += step) {
+                    const int nj = std::min(step, ng - j0);
+                    SWMD_CK(launch_cost_batch(cost_g[g0 + j0], v, kprec, nj,
+                                              reinterpret_cast<const CostArgs *>(ws + o_cost) + g0 + j0, st));
+                    int rc = run_resident_batch(c, res_g[g0 + j0], m, kprec, nj,
+                                                reinterpret_cast<const ResidentArgs *>(ws + o_res) + g0 + j0, st);
+                    if (rc) return rc;
+                }
             }
         }
         for (int i : others) {
