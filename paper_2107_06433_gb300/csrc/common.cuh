@@ -29,7 +29,6 @@ constexpr int ST_BAD_ID = 1;       // a query id outside [0, V)
 constexpr int ST_NUMERIC = 2;      // NaN / Inf / zero denominator
 constexpr int ST_GUARD = 4;        // the FP64 guard of K^T u was taken (informational)
 constexpr int ST_BAD_R = 8;        // a query weight that is not finite and > 0
-constexpr int ST_BAD_SIZE = 16;    // a 1-to-1 pair side outside its declared size bound
 
 // Query parameters read by the kernels from device memory, so that a captured
 // graph stays valid when lambda or v_r change.

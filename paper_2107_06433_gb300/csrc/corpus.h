@@ -189,6 +189,9 @@ struct PairJob {
     int *status;
 };
 constexpr int kPairMaxWords = 4096;
+// status bit of the pair kernel (beside the ST_* bits of common.cuh): a pair side
+// outside its declared size bound
+constexpr int ST_BAD_SIZE = 16;
 int enqueue_pairs(swmd_corpus *c, const PairJob &job, cudaStream_t st);
 // Effective resident settings for a layout: explicit options, else autotuned, else defaults.
 void resident_settings(swmd_corpus *c, int vrp, int kprec, int *solver, int *npl_want, int *split);

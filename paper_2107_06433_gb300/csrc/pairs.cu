@@ -247,21 +247,21 @@ __global__ void __launch_bounds__(kPT, 4) k_pairs(const __grid_constant__ PairAr
                     if (two) {
 #pragma unroll 4
                         for (int dd = 0; dd < dl; ++dd) {
-                            const float x0 = sx0[dd], x1 = sx1[dd];
+                            const float e0 = sx0[dd], e1 = sx1[dd];
 #pragma unroll
                             for (int i = 0; i < KPT / 2; ++i) {
                                 const float2 q2 = *reinterpret_cast<const float2 *>(sq + dd * TKK + 2 * i);
-                                acc0[i] = sqdiff2(q2, x0, acc0[i]);
-                                acc1[i] = sqdiff2(q2, x1, acc1[i]);
+                                acc0[i] = sqdiff2(q2, e0, acc0[i]);
+                                acc1[i] = sqdiff2(q2, e1, acc1[i]);
                             }
                         }
                     } else {   // the tile's second 32 target words are all past v_x
 #pragma unroll 4
                         for (int dd = 0; dd < dl; ++dd) {
-                            const float x0 = sx0[dd];
+                            const float e0 = sx0[dd];
 #pragma unroll
                             for (int i = 0; i < KPT / 2; ++i)
-                                acc0[i] = sqdiff2(*reinterpret_cast<const float2 *>(sq + dd * TKK + 2 * i), x0,
+                                acc0[i] = sqdiff2(*reinterpret_cast<const float2 *>(sq + dd * TKK + 2 * i), e0,
                                                   acc0[i]);
                         }
                     }
