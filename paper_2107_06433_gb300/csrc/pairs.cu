@@ -5,12 +5,13 @@
 // column c: a vocabulary word outside the target has c = 0, so it adds nothing to
 // x = K_over_r v or to the final sum, and dropping it is exact.
 //
-// One block of 128 threads owns one pair at a time (a grid-stride loop over pairs)
-// and runs every step of Algorithm 1 for it on chip:
+// One block of 256 threads (8 warps) owns one pair at a time (a grid-stride loop over
+// pairs) and runs every step of Algorithm 1 for it on chip:
 //   cost   M[k][j] = ||E[q_k] - E[x_j]||_2 for the v_r x v_x block, tiled 4 KPT query
-//          words x 64 target words (two per lane), embedding dimensions staged 32 at
-//          a time in shared memory, the next chunk already in flight in registers
-//          while the current one is used (FP32, direct difference form, two-wide FMAs);
+//          words x 64 target words (four warp rows of KPT query words, two warp columns
+//          of 32 target words), embedding dimensions staged 32 at a time in shared
+//          memory, the next chunk already in flight in registers while the current one
+//          is used (FP32, direct difference form, two-wide FMAs);
 //          K = exp(-lambda (M - m_j)) with the column shift m_j = min_k M[k][j]
 //          when the corpus uses it (an exact rescaling of column j), KM = K .* M;
 //          K and KM stay in shared memory when they fit, else in a per-block
@@ -34,7 +35,8 @@
 namespace swmd {
 namespace {
 
-constexpr int kPT = 128;   // threads per block
+constexpr int kPT = 256;   // threads per block
+constexpr int kPW = kPT / 32;   // warps per block
 constexpr int kPJ = 64;    // target words per cost tile (two per lane)
 constexpr int kPD = 32;    // embedding dimensions per staged chunk
 // K and KM of the largest pair go to shared memory up to this many bytes
@@ -67,7 +69,7 @@ __host__ __device__ inline int take_floats(int &off, int floats) {
 
 __host__ __device__ inline PairLayout pair_layout(int max_q, int max_x, int tkk, bool smemk) {
     PairLayout L;
-    int off = 64;   // 4 doubles of the final sum, 4 floats of the marginal error, a flag word
+    int off = 128;   // kPW doubles of the final sum, kPW floats of the marginal error, a flag word
     L.u = take_floats(off, max_q);
     L.rr = take_floats(off, max_q);
     L.red = take_floats(off, max_q);
@@ -156,14 +158,14 @@ __device__ __forceinline__ float warp_min(float x) {
 }
 
 template <int KPT, bool SMEMK>
-__global__ void __launch_bounds__(kPT, 4) k_pairs(const __grid_constant__ PairArgs a) {
-    constexpr int TKK = 4 * KPT;   // query words per cost tile: KPT per warp
+__global__ void __launch_bounds__(kPT, 2) k_pairs(const __grid_constant__ PairArgs a) {
+    constexpr int TKK = 4 * KPT;   // query words per cost tile: KPT per warp row
     extern __shared__ __align__(16) unsigned char smem[];
     const PairJob &J = a.job;
     const PairLayout L = pair_layout(J.max_q, J.max_x, TKK, SMEMK);
     double *dred = reinterpret_cast<double *>(smem);
-    float *errw = reinterpret_cast<float *>(smem + 32);
-    int *flag = reinterpret_cast<int *>(smem + 48);
+    float *errw = reinterpret_cast<float *>(smem + 8 * kPW);
+    int *flag = reinterpret_cast<int *>(smem + 12 * kPW);
     float *u = reinterpret_cast<float *>(smem + L.u);
     float *rr = reinterpret_cast<float *>(smem + L.rr);
     float *red = reinterpret_cast<float *>(smem + L.red);
@@ -180,6 +182,7 @@ __global__ void __launch_bounds__(kPT, 4) k_pairs(const __grid_constant__ PairAr
         KMb = Kb + a.kws_stride / 2;
     }
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int kg = w & 3, jh = w >> 2;   // cost tile: warp row (query words), warp column (target words)
     const float lam = J.lambda;
 
     for (int p = blockIdx.x; p < J.n_pairs; p += gridDim.x) {
@@ -228,10 +231,10 @@ __global__ void __launch_bounds__(kPT, 4) k_pairs(const __grid_constant__ PairAr
         // ---- cost: M for the v_r x v_x block, written to KMb first
         for (int jt = 0; jt < vx; jt += kPJ) {
             for (int kt = 0; kt < vr; kt += TKK) {
-                float2 acc0[KPT / 2], acc1[KPT / 2];   // target words jt + lane, jt + 32 + lane
+                float2 acc[KPT / 2];   // target word jt + 32 jh + lane, query words kt + kg KPT + ...
 #pragma unroll
-                for (int i = 0; i < KPT / 2; ++i) acc0[i] = acc1[i] = make_float2(0.f, 0.f);
-                const bool two = jt + 32 < vx;   // block-uniform
+                for (int i = 0; i < KPT / 2; ++i) acc[i] = make_float2(0.f, 0.f);
+                const bool busy = jt + 32 * jh < vx;   // warp-uniform: this warp column has words
                 Chunk<TKK> ch;
                 load_chunk<TKK>(ch, a.E, a.d4, 0, xid, jt, vx, qid, kt, vr, tid);
                 for (int d0 = 0; d0 < a.d4; d0 += kPD) {
@@ -241,42 +244,26 @@ __global__ void __launch_bounds__(kPT, 4) k_pairs(const __grid_constant__ PairAr
                     __syncthreads();
                     if (d0 + kPD < a.d4)   // the next chunk is in flight during this one's FMAs
                         load_chunk<TKK>(ch, a.E, a.d4, d0 + kPD, xid, jt, vx, qid, kt, vr, tid);
-                    const float *sx0 = Sx + lane * (kPD + 1);
-                    const float *sx1 = Sx + (lane + 32) * (kPD + 1);
-                    const float *sq = Sq + w * KPT;
-                    if (two) {
+                    if (busy) {
+                        const float *sx = Sx + (32 * jh + lane) * (kPD + 1);
+                        const float *sq = Sq + kg * KPT;
 #pragma unroll 4
                         for (int dd = 0; dd < dl; ++dd) {
-                            const float e0 = sx0[dd], e1 = sx1[dd];
-#pragma unroll
-                            for (int i = 0; i < KPT / 2; ++i) {
-                                const float2 q2 = *reinterpret_cast<const float2 *>(sq + dd * TKK + 2 * i);
-                                acc0[i] = sqdiff2(q2, e0, acc0[i]);
-                                acc1[i] = sqdiff2(q2, e1, acc1[i]);
-                            }
-                        }
-                    } else {   // the tile's second 32 target words are all past v_x
-#pragma unroll 4
-                        for (int dd = 0; dd < dl; ++dd) {
-                            const float e0 = sx0[dd];
+                            const float e0 = sx[dd];
 #pragma unroll
                             for (int i = 0; i < KPT / 2; ++i)
-                                acc0[i] = sqdiff2(*reinterpret_cast<const float2 *>(sq + dd * TKK + 2 * i), e0,
-                                                  acc0[i]);
+                                acc[i] = sqdiff2(*reinterpret_cast<const float2 *>(sq + dd * TKK + 2 * i), e0,
+                                                 acc[i]);
                         }
                     }
                 }
+                const int j = jt + 32 * jh + lane;
+                if (j < vx) {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int j = jt + lane + 32 * h;
-                    if (j < vx) {
-#pragma unroll
-                        for (int i = 0; i < KPT / 2; ++i) {
-                            const int k = kt + w * KPT + 2 * i;
-                            const float2 m2 = h ? acc1[i] : acc0[i];
-                            if (k < vr) KMb[j * VRS + k] = sqrtf(m2.x);
-                            if (k + 1 < vr) KMb[j * VRS + k + 1] = sqrtf(m2.y);
-                        }
+                    for (int i = 0; i < KPT / 2; ++i) {
+                        const int k = kt + kg * KPT + 2 * i;
+                        if (k < vr) KMb[j * VRS + k] = sqrtf(acc[i].x);
+                        if (k + 1 < vr) KMb[j * VRS + k + 1] = sqrtf(acc[i].y);
                     }
                 }
             }
@@ -341,7 +328,9 @@ __global__ void __launch_bounds__(kPT, 4) k_pairs(const __grid_constant__ PairAr
                 // P = diag(u) K diag(v) is within tol of r, or after t updates
                 if (lane == 0) errw[w] = errl;
                 __syncthreads();
-                const float err = fmaxf(fmaxf(errw[0], errw[1]), fmaxf(errw[2], errw[3]));
+                float err = errw[0];
+#pragma unroll
+                for (int i = 1; i < kPW; ++i) err = fmaxf(err, errw[i]);
                 if (err < J.tol || it == J.t) break;
                 for (int k = tid; k < vr; k += kPT) {
                     const float nu = __fdividef(rr[k], red[k]);
@@ -376,7 +365,9 @@ __global__ void __launch_bounds__(kPT, 4) k_pairs(const __grid_constant__ PairAr
         if (lane == 0) dred[w] = dsum;
         __syncthreads();
         if (tid == 0) {
-            const double dist = (dred[0] + dred[1]) + (dred[2] + dred[3]);
+            double dist = 0.0;
+#pragma unroll
+            for (int i = 0; i < kPW; ++i) dist += dred[i];
             if (!(fabs(dist) < INFINITY)) atomicOr(J.status, ST_NUMERIC);
             J.out[p] = dist;
             if (J.iters) J.iters[p] = it;
