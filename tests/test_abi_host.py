@@ -138,3 +138,15 @@ def test_pair_calls_check_arguments_before_the_gpu(lib):
     assert b"NULL corpus" in lib.swmd_last_error()
     assert lib.swmd_wmd_pairs_device(None, 1, z, z, z, z, z, z, 8, 8, 1.0, 15, 0.0, z, z, z,
                                      None) == swmd.SWMD_EINVAL
+
+
+def test_pair_binding_marshals_ragged_sides(lib):
+    """The binding's ragged packing of pair sides (pointer arrays and concatenated
+    ids / weights), and its length check, need no GPU."""
+    ptr, ids, w = swmd._ragged([([3, 1], [1.0, 2.0]), ([7], [5.0]), ([], [])])
+    np.testing.assert_array_equal(ptr, [0, 2, 3, 3])
+    np.testing.assert_array_equal(ids, [3, 1, 7])
+    np.testing.assert_array_equal(w, np.array([1.0, 2.0, 5.0], np.float32))
+    assert ids.dtype == np.int32 and w.dtype == np.float32 and ptr.dtype == np.int64
+    with pytest.raises(ValueError):
+        swmd.swmd_wmd_pairs(None, [([1], [1.0])], [], 1.0, 15)
