@@ -27,7 +27,10 @@ words, v_r=19, lambda=1, 15 iterations).  Inputs are synthetic (synth.py).
              fed by Poisson arrivals at 50, 200 and 1000 queries/s (v_r uniform in
              [4,128]): queries/s and p50/p99 latency, against the same queries run
              one at a time through swmd_query with FP32 K, and the BF16 error.
-  cpu_baseline  the FP64 oracle timed on the host cores on a bounded sample.
+  one_to_one the 1-to-1 pairs of Table II: the query against every document as
+             independent pairs, and a 100-candidate re-ranking set, beside the 1-to-N query.
+  cpu_baseline  the FP64 oracle timed on the host cores on a bounded sample, and on
+             one host thread (`single_core`).
 
 `--impl reference` times the oracle alone (the reference arm).  Under torchrun
 (N > 1) every rank holds its own 5,000-document partition (weak scaling, no
@@ -223,6 +226,19 @@ def time_oracle(E, C, qi, qw, lam, t, budget_s=12.0, max_runs=50):
         if el >= budget_s or runs >= max_runs:
             break
     return runs, el, oracle.get_threads()
+
+
+def time_oracle_one_core(E, C, qi, qw, lam, t, budget_s=6.0, max_runs=10):
+    """The same oracle on one host thread (restored afterwards)."""
+    import oracle
+    n0 = oracle.get_threads()
+    try:
+        oracle.set_threads(1)
+        runs, el, cores = time_oracle(E, C, qi, qw, lam, t, budget_s, max_runs)
+    finally:
+        oracle.set_threads(n0)
+    return {"value": C.N * runs / el, "unit": "WMD/s", "cores": cores,
+            "sample": f"{runs} whole queries, one thread"}
 
 
 def config_dict(w, C):
@@ -704,6 +720,7 @@ def main():
                                 "kind": "oracle",
                                 "sample": f"{runs} whole queries of the {w.name} workload "
                                           f"({C.N} documents each), sparse FP64 mode"}
+        line["cpu_baseline"]["single_core"] = time_oracle_one_core(E, C, qi, qw, lam, t)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:
