@@ -530,3 +530,35 @@ def test_pair_rejects_invalid_sides():
             oracle.wmd_pairs(E, [bad], [ok], 1.0, 3)
     with pytest.raises(oracle.OracleError):
         oracle.wmd_pairs(E, [ok], [ok], 0.0, 3)
+
+
+def test_pair_equals_column_on_random_instances():
+    """Property form of the Table II restriction: random vocabularies, embeddings,
+    histograms with repeated ids and zero weights, lambda and t."""
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=40, deadline=None, derandomize=True)
+    @hyp.given(seed=st.integers(0, 2**31 - 1), lam=st.sampled_from([0.5, 1.0, 4.0, 20.0]),
+               t=st.integers(0, 12))
+    def check(seed, lam, t):
+        rng = np.random.default_rng(seed)
+        V = int(rng.integers(6, 40))
+        E = _unit_rows(rng, V, int(rng.integers(2, 9)))
+        nq, nx = int(rng.integers(1, 8)), int(rng.integers(1, 8))
+        qi = rng.integers(0, V, nq)
+        qw = rng.integers(0, 4, nq).astype(np.float32)
+        qw[0] = max(qw[0], 1.0)
+        xi = rng.integers(0, V, nx)
+        xw = rng.integers(0, 4, nx).astype(np.float32)
+        xw[0] = max(xw[0], 1.0)
+        doc = {}
+        for w_, c_ in zip(xi, xw):
+            if c_ > 0:
+                doc[int(w_)] = doc.get(int(w_), 0.0) + float(c_)
+        rp, col, val = _csr_from_docs(V, [doc])
+        full = oracle.wmd(E, rp, col, val.astype(np.float32), 1, qi, qw, lam, t)
+        pair = oracle.wmd_pairs(E, [(qi, qw)], [(xi, xw)], lam, t)
+        np.testing.assert_allclose(pair, full, rtol=1e-12)
+
+    check()
