@@ -30,7 +30,8 @@ words, v_r=19, lambda=1, 15 iterations).  Inputs are synthetic (synth.py).
   one_to_one the 1-to-1 pairs of Table II: the query against every document as
              independent pairs, and a 100-candidate re-ranking set, beside the 1-to-N query.
   cpu_baseline  the FP64 oracle timed on the host cores on a bounded sample, and on
-             one host thread (`single_core`).
+             one host thread (`single_core`); the dense oracle on the 200-document
+             workload and on 64 documents of the paper-shaped one (`dense`).
 
 `--impl reference` times the oracle alone (the reference arm).  Under torchrun
 (N > 1) every rank holds its own 5,000-document partition (weak scaling, no
@@ -239,6 +240,42 @@ def time_oracle_one_core(E, C, qi, qw, lam, t, budget_s=6.0, max_runs=10):
         oracle.set_threads(n0)
     return {"value": C.N * runs / el, "unit": "WMD/s", "cores": cores,
             "sample": f"{runs} whole queries, one thread"}
+
+
+def first_documents_csr(C, n):
+    """The V x n CSR of the corpus's first n documents (columns 0..n-1)."""
+    end = int(C.doc_ptr[n])
+    words = np.asarray(C.word_ids[:end], np.int64)
+    docs = np.repeat(np.arange(n, dtype=np.int32), np.diff(np.asarray(C.doc_ptr[:n + 1])))
+    order = np.lexsort((docs, words))
+    rp = np.zeros(C.V + 1, np.int64)
+    np.cumsum(np.bincount(words, minlength=C.V), out=rp[1:])
+    return rp, docs[order], np.asarray(C.vals[:end], np.float32)[order]
+
+
+def time_oracle_dense(synth, budget_s=4.0):
+    """The dense oracle (Algorithm 1 with dense matrices, as Table I runs it) on the
+    200-document workload and on the first 64 documents of the paper-shaped one."""
+    import oracle
+    out = {}
+    for name, ndocs in (("tiny", None), ("paper", 64)):
+        E, C, (qi, qw) = synth.make(name)
+        w = synth.WORKLOADS[name]
+        if ndocs is None:
+            rp, col, val = C.csr()
+            ndocs = C.N
+        else:
+            rp, col, val = first_documents_csr(C, ndocs)
+        runs, t0 = 0, time.perf_counter()
+        while True:
+            oracle.wmd(E, rp, col, val, ndocs, qi, qw, w.lam, w.max_iter, "dense")
+            runs += 1
+            el = time.perf_counter() - t0
+            if el >= budget_s or runs >= 20:
+                break
+        out[name] = {"value": ndocs * runs / el, "unit": "WMD/s", "cores": oracle.get_threads(),
+                     "sample": f"{runs} queries against {ndocs} documents, dense FP64 mode"}
+    return out
 
 
 def config_dict(w, C):
@@ -721,6 +758,7 @@ def main():
                                 "sample": f"{runs} whole queries of the {w.name} workload "
                                           f"({C.N} documents each), sparse FP64 mode"}
         line["cpu_baseline"]["single_core"] = time_oracle_one_core(E, C, qi, qw, lam, t)
+        line["cpu_baseline"]["dense"] = time_oracle_dense(synth)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:
