@@ -757,8 +757,13 @@ def main():
                                 "kind": "oracle",
                                 "sample": f"{runs} whole queries of the {w.name} workload "
                                           f"({C.N} documents each), sparse FP64 mode"}
-        line["cpu_baseline"]["single_core"] = time_oracle_one_core(E, C, qi, qw, lam, t)
-        line["cpu_baseline"]["dense"] = time_oracle_dense(synth)
+        # supplementary oracle timings: a failure here is recorded, not fatal to the line
+        for key, fn in (("single_core", lambda: time_oracle_one_core(E, C, qi, qw, lam, t)),
+                        ("dense", lambda: time_oracle_dense(synth))):
+            try:
+                line["cpu_baseline"][key] = fn()
+            except Exception as exc:   # noqa: BLE001
+                line["cpu_baseline"][key] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:
