@@ -23,6 +23,14 @@ def main():
               "(V=2000, d=64, N=200, v_r=8, lambda=1, t=15), seed 210706433")
     np.savetxt(os.path.join(HERE, "tiny_wmd.txt"), wmd, fmt="%.17g", header=header)
 
+    # 1-to-1 pairs (Table II): document j as the query, document j + 1 as the target
+    docs = [(C.word_ids[C.doc_ptr[j]:C.doc_ptr[j + 1]], C.vals[C.doc_ptr[j]:C.doc_ptr[j + 1]])
+            for j in range(51)]
+    pairs = oracle.wmd_pairs(E, docs[:50], docs[1:51], 2.0, 10)
+    header = ("1-to-1 Sinkhorn WMD, FP64 oracle (cost over the target's words): workload 'tiny', "
+              "pair j = (document j, document j+1), j < 50, lambda=2, t=10, seed 210706433")
+    np.savetxt(os.path.join(HERE, "tiny_pairs.txt"), pairs, fmt="%.17g", header=header)
+
 
 if __name__ == "__main__":
     main()

@@ -562,3 +562,15 @@ def test_pair_equals_column_on_random_instances():
         np.testing.assert_allclose(pair, full, rtol=1e-12)
 
     check()
+
+
+def test_golden_tiny_pairs(tiny):
+    """Regression against the stored oracle output of 50 document-to-document pairs."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "tiny_pairs.txt")
+    ref = np.loadtxt(path)
+    E, C, _ = tiny
+    docs = [(C.word_ids[C.doc_ptr[j]:C.doc_ptr[j + 1]], C.vals[C.doc_ptr[j]:C.doc_ptr[j + 1]])
+            for j in range(51)]
+    got = oracle.wmd_pairs(E, docs[:50], docs[1:51], 2.0, 10)
+    np.testing.assert_allclose(got, ref, rtol=1e-12)
