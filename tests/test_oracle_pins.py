@@ -574,3 +574,21 @@ def test_golden_tiny_pairs(tiny):
             for j in range(51)]
     got = oracle.wmd_pairs(E, docs[:50], docs[1:51], 2.0, 10)
     np.testing.assert_allclose(got, ref, rtol=1e-12)
+
+
+@pytest.mark.parametrize("t", [0, 1, 6])
+def test_pair_convergence_mode_capped_at_t_is_the_fixed_t_result(t):
+    """With a tolerance no iteration reaches, the convergence mode runs exactly its cap
+    of t x-updates (through the sparse routine) and must equal the fixed-t result
+    (through the dense routine)."""
+    rng = np.random.default_rng(31)
+    V = 50
+    E = _unit_rows(rng, V, 7)
+    # two or more words on each side: a single-word side meets its marginal exactly
+    # after one update, which would stop the convergence mode early (correctly)
+    A = [(rng.choice(V, n, replace=False), rng.integers(1, 5, n).astype(np.float32)) for n in (2, 3, 6)]
+    B = [(rng.choice(V, n, replace=False), rng.integers(1, 5, n).astype(np.float32)) for n in (4, 2, 9)]
+    fixed = oracle.wmd_pairs(E, A, B, 2.0, t)
+    capped, its = oracle.wmd_pairs(E, A, B, 2.0, t, tol=1e-300, want_iters=True)
+    assert np.all(its == t)
+    np.testing.assert_allclose(capped, fixed, rtol=1e-13)
