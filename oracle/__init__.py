@@ -1,4 +1,5 @@
-"""FP64 CPU oracle of Sinkhorn WMD (arXiv 2107.06433, Algorithm 1; Algorithms 2-3).
+"""FP64 CPU oracle of Sinkhorn WMD (arXiv 2107.06433, Algorithm 1; Algorithms 2-3;
+the 1-to-1 variant of Section III-E, Table II).
 
 TEST INFRASTRUCTURE.  Only the tests, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` may import this package.  The CUDA product path never

@@ -16,6 +16,8 @@
  *   - Algorithms 2 and 3 (Section III-B4): the sparse reformulation, an SDDMM
  *     that evaluates K^T u only at the nonzeros of c, followed by the transpose
  *     to CSC and the SpMM x = K_over_r v.
+ *   - Section III-E, Table II (right column): the 1-to-1 variant, one (query,
+ *     target) pair with the cost built over the target's words only.
  *
  * Readings of the paper taken here (each is listed with its reason in the design
  * notes of the repository):
