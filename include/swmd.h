@@ -62,9 +62,11 @@ extern "C" {
  *             u held on chip; legal because the documents (columns of c) are
  *             independent problems in Algorithm 1.
  *   AUTO:     RESIDENT or FUSED for each query: the choice swmd_autotune measured
- *             for its v_r, else RESIDENT for corpora under 20,000 documents or v_r
- *             up to 24, FUSED otherwise (on large corpora the per-iteration walk
- *             is faster for wide queries).  The choice depends only on v_r and
+ *             for its v_r, else RESIDENT when the resident solver is the
+ *             column-split one (swmd_options.solver 4, the default on corpora of
+ *             documents up to 32 words), else RESIDENT for corpora under 20,000
+ *             documents or v_r up to 24 and FUSED otherwise (on large corpora the
+ *             per-iteration walk beats the other resident solvers for wide queries).  The choice depends only on v_r and
  *             the tuning, so a query's result is the same alone, batched or served. */
 #define SWMD_PATH_FUSED 0
 #define SWMD_PATH_PLAIN 1
@@ -100,9 +102,14 @@ typedef struct swmd_options {
                               in about 100 KB of shared memory) */
     int32_t cost_split;    /* cost kernel: threads sharing one word's embedding row
                               (1, 2 or 4; 0 = 2, or 1 from 65,536 used words up) */
-    int32_t solver;        /* resident path kernel: 0 = automatic, 1 = K^T rows in registers
-                              (v_r <= 32), 2 = rows staged in shared memory, 3 = rows
-                              re-gathered from L2 each iteration */
+    int32_t solver;        /* resident path kernel: 0 = automatic (4 when every document has
+                              at most 32 words, else 1 for v_r <= 32 and 2 above),
+                              1 = K^T rows in registers, whole rows per lane (v_r <= 32),
+                              2 = rows staged in shared memory, 3 = rows re-gathered from
+                              L2 each iteration, 4 = K^T rows in registers split by columns
+                              over a team of VRP / 4 lanes (documents of at most 32 words;
+                              v_r padded to a power of two from 16 to 128; on a corpus with
+                              longer documents 4 acts as 0) */
     float tol;             /* 0 (default): exactly max_iter x-updates, as the paper's
                               experiments run.  > 0: Algorithm 1's "while x changes": the
                               fused per-iteration path stops after the x-update in which
@@ -352,7 +359,7 @@ SWMD_API int swmd_debug_read(swmd_corpus *corpus, int32_t what, int32_t v_r, voi
 
 /* ------------------------------------------------------------------ autotuning */
 typedef struct swmd_tune_result {
-    int32_t vrp;           /* layout tuned (VRP of the resident path for v_r) */
+    int32_t vrp;           /* the resident layout of the chosen solver (VRP for v_r) */
     int32_t solver;        /* chosen resident solver (see swmd_options.solver) */
     int32_t nnz_per_lane;  /* chosen rows of K^T per lane (register solver) */
     int32_t cost_split;    /* chosen threads per word of the cost kernel */
@@ -364,11 +371,11 @@ typedef struct swmd_tune_result {
 } swmd_tune_result;
 
 /* Times the resident-path kernels of this corpus for queries of v_r words over
- * the candidate lane mappings (register solver rows per lane; shared-memory
- * solver; threads per word of the cost kernel), each `reps` times (>= 1) with
- * CUDA events on a query of v_r distinct words, and keeps the fastest for this
- * layout: later queries with the same VRP and K precision use it unless
- * swmd_options fixes the field.  On a corpus with SWMD_PATH_AUTO it also times the
+ * the candidate solvers and lane mappings (column-split register solver; register
+ * solver rows per lane; shared-memory solver; threads per word of the cost
+ * kernel), each `reps` times (>= 1) with CUDA events on a query of v_r distinct
+ * words, and keeps the fastest: later queries of v_r words with the same K
+ * precision use it unless swmd_options fixes the field.  On a corpus with SWMD_PATH_AUTO it also times the
  * per-iteration fused path and records, for this v_r, whichever path was faster.
  * The corpus's path must be SWMD_PATH_RESIDENT or SWMD_PATH_AUTO.  Synchronous;
  * allocates nothing beyond the corpus's workspace; call it before serving from the
@@ -422,10 +429,16 @@ SWMD_API void swmd_default_serve_config(swmd_serve_config *cfg);
 
 /* Starts a serving thread over a resident corpus.  Requests are admitted into
  * device batches as memory (K, K.*M and u of each query) frees up, and a batch
- * runs while later requests queue (continuous batching).  cfg may be NULL. */
+ * runs while later requests queue (continuous batching).  cfg may be NULL.
+ * SWMD_ENOMEM if memory_budget is below the bytes one query of max_vr words needs.
+ * While a server is attached, swmd_autotune and swmd_corpus_set_options on its
+ * corpus are refused (SWMD_EINVAL): a request's path and layout are resolved once,
+ * when it is admitted. */
 SWMD_API int swmd_serve_start(swmd_corpus *corpus, const swmd_serve_config *cfg, swmd_server **out);
 
-/* Queues one query (host arrays copied during the call).  *ticket identifies it. */
+/* Queues one query (host arrays copied during the call).  *ticket identifies it.
+ * SWMD_ENOMEM (and the request is counted as rejected) when queue_capacity requests
+ * are already pending; SWMD_ESTOPPED once swmd_serve_stop has begun. */
 SWMD_API int swmd_serve_submit(swmd_server *srv, const int32_t *h_ids, const float *h_weights,
                       int32_t n_words, float lambda, int32_t max_iter, uint64_t *ticket);
 
@@ -437,7 +450,8 @@ SWMD_API int swmd_serve_wait(swmd_server *srv, uint64_t ticket, double *h_out_di
 SWMD_API int swmd_serve_stats(swmd_server *srv, swmd_serve_stats_t *out);
 
 /* Stops the server after finishing in-flight batches; pending requests fail
- * with SWMD_ESTOPPED.  Frees the server. */
+ * with SWMD_ESTOPPED, and threads blocked in swmd_serve_wait on them return that
+ * code before the server is freed.  No call may use the server after this returns. */
 SWMD_API int swmd_serve_stop(swmd_server *srv);
 
 #ifdef __cplusplus

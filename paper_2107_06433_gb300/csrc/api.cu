@@ -50,9 +50,12 @@ void dev_free(void *p) {
     if (p) cudaFree(p);
 }
 
-int max_vrp_of(int max_vr) { return vrp_for(max_vr, 8); }
-
 }  // namespace
+
+// Every layout a query of up to max_vr words may take: the resident solvers' tight
+// padding, the per-iteration walks' power of two >= 4 and the column-split
+// solver's power of two >= 16 all fit.
+int max_vrp_of(int max_vr) { return std::max(vrp_for(max_vr, 8), cols_vrp(max_vr)); }
 
 void clear_graphs(swmd_corpus *c) {
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
@@ -115,6 +118,8 @@ void free_slot(Slot &s) {
     s = Slot{};
 }
 
+int tight_vrp(int vr) { return vrp_for(vr, vr <= 32 ? 1 : (vr <= 64 ? 2 : 4)); }
+
 static bool pow2_times4(int v) { return v >= 4 && v <= 128 && ((v / 4) & (v / 4 - 1)) == 0 && v % 4 == 0; }
 
 // Padding VRP of the K^T / KM^T / u layout for a query of vr words on `path`:
@@ -132,7 +137,9 @@ int layout_vrp(swmd_corpus *c, int vr, int path) {
         while (v < vr) v *= 2;
         return v;
     }
-    return vrp_for(vr, vr <= 32 ? 1 : (vr <= 64 ? 2 : 4));
+    // the column-split register solver takes power-of-two layouts of 16 to 128
+    if (resident_solver(c, vr, c->opt.k_precision) == kSolverCols) return cols_vrp(vr);
+    return tight_vrp(vr);
 }
 
 // Kernel mapping for walking a layout of padding vrp: p = 0 selects the sliced
@@ -162,6 +169,9 @@ int resolve_path(swmd_corpus *c, int vr) {
     if (c->opt.tol > 0.f) return SWMD_PATH_FUSED;   // the convergence mode's path
     auto it = c->tuned_path.find(std::make_pair(vr, c->opt.k_precision));
     if (it != c->tuned_path.end()) return it->second;
+    // the column-split register solver keeps every document's rows on chip for all
+    // iterations: faster than the per-iteration walk at every width it takes
+    if (resident_solver(c, vr, c->opt.k_precision) == kSolverCols) return SWMD_PATH_RESIDENT;
     return (c->Nl < kAutoResidentDocs || vr <= kAutoResidentVr) ? SWMD_PATH_RESIDENT : SWMD_PATH_FUSED;
 }
 
@@ -256,22 +266,73 @@ int build_tasks(swmd_corpus *c) {
         cudaError_t e = cudaMemcpy(c->tasks_dev, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(e, "copy tasks");
     }
+    // Column-split solver: per layout, runs of up to 32 / (lanes per document)
+    // consecutive documents of one bucket (documents are in decreasing length, so a bucket's
+    // documents are contiguous).  Only when every document fits a bucket.
+    if (c->Nl == 0 || c->len_sorted[0] > kColMaxLen) return SWMD_OK;
+    std::vector<int4> cols;
+    for (int li = 0; li < kColLayouts; ++li) {
+        const int vrp = 16 << li;
+        c->col_off[li] = (int)cols.size();
+        int d = 0;
+        while (d < c->Nl) {
+            const int b = cols_bucket(c->len_sorted[d], vrp);
+            const int per_warp = 32 / cols_team(b, vrp);
+            int k = 0;
+            while (d + k < c->Nl && k < per_warp && cols_bucket(c->len_sorted[d + k], vrp) == b) ++k;
+            cols.push_back(make_int4(d, k, b, 0));
+            d += k;
+        }
+        c->col_count[li] = (int)cols.size() - c->col_off[li];
+    }
+    bytes = 0;
+    if ((rc = dev_alloc(&c->col_tasks_dev, cols.size(), &bytes))) return rc;
+    c->base_bytes += bytes;
+    cudaError_t e = cudaMemcpy(c->col_tasks_dev, cols.data(), sizeof(int4) * cols.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "copy column-split tasks");
     return SWMD_OK;
 }
 
-void resident_settings(swmd_corpus *c, int vrp, int kprec, int *solver, int *npl_want, int *split) {
+void resident_settings(swmd_corpus *c, int vr, int kprec, int *solver, int *npl_want, int *split) {
     int s = 0, n = 0, cs = 0;
-    auto it = c->tuned_resident.find(std::make_pair(vrp, kprec));
+    auto it = c->tuned_resident.find(std::make_pair(vr, kprec));
     if (it != c->tuned_resident.end()) std::tie(s, n, cs) = it->second;
     *solver = c->opt.solver ? c->opt.solver : s;
     *npl_want = c->opt.nnz_per_lane ? c->opt.nnz_per_lane : n;
     *split = c->opt.cost_split ? c->opt.cost_split : cs;
 }
 
-int run_resident_batch(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kprec, int nq,
+int resident_solver(swmd_corpus *c, int vr, int kprec) {
+    int s = 0, n = 0, cs = 0;
+    resident_settings(c, vr, kprec, &s, &n, &cs);
+    if (s == kSolverAuto && c->col_tasks_dev) s = kSolverCols;
+    if (s == kSolverCols && !c->col_tasks_dev) s = kSolverAuto;
+    return s;
+}
+
+int run_resident_batch(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kprec, int vr, int nq,
                        const ResidentArgs *d_batch, cudaStream_t st) {
     int solver = 0, npl_want = 0, split = 0;
-    resident_settings(c, m.vrp, kprec, &solver, &npl_want, &split);
+    resident_settings(c, vr, kprec, &solver, &npl_want, &split);
+    solver = resident_solver(c, vr, kprec);
+    if (solver == kSolverCols && m.vrp == cols_vrp(vr) && cols_supported(m.vrp)) {
+        const int li = cols_index(m.vrp);
+        ColArgs ca{};
+        ca.doc_ptr = c->doc_ptr;
+        ca.nz = c->nz;
+        ca.doc_orig = c->doc_orig;
+        ca.tasks = c->col_tasks_dev + c->col_off[li];
+        ca.n_tasks = c->col_count[li];
+        ca.kprec = kprec;
+        ca.q0 = ra;
+        ca.queries = d_batch;
+        cudaError_t e = launch_resident_cols(ca, m.vrp, c->sms, st, nq);
+        if (e != cudaSuccess)
+            return set_error(e == cudaErrorMemoryAllocation ? SWMD_ENOMEM : SWMD_ECUDA,
+                             "column-split resident solver (VRP %d): %s", m.vrp, cudaGetErrorString(e));
+        return SWMD_OK;
+    }
+    if (solver == kSolverCols) solver = kSolverAuto;   // another layout (explicit lane mapping)
     const int npl = regs_rows_per_lane(m.vrp, npl_want);
     if (c->tasks_dev && npl > 0 && (solver == 0 || solver == 1)) {
         TaskSet ts{c->tasks_dev + c->task_off[npl], c->task_count[npl], npl,
@@ -305,11 +366,11 @@ int run_resident_batch(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kp
     return SWMD_OK;
 }
 
-int run_resident(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kprec, cudaStream_t st) {
-    return run_resident_batch(c, ra, m, kprec, 1, nullptr, st);
+int run_resident(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kprec, int vr, cudaStream_t st) {
+    return run_resident_batch(c, ra, m, kprec, vr, 1, nullptr, st);
 }
 
-static int launch_sequence(swmd_corpus *c, Slot &s, Mapping m, int t, int path, int kprec,
+static int launch_sequence(swmd_corpus *c, Slot &s, Mapping m, int vr, int t, int path, int kprec,
                            int shift, cudaStream_t st) {
     CostArgs ca{};
     ca.E = c->E;
@@ -322,7 +383,7 @@ static int launch_sequence(swmd_corpus *c, Slot &s, Mapping m, int t, int path, 
     ca.shift = shift;
     {
         int s_ = 0, n_ = 0, cs_ = 0;
-        resident_settings(c, m.vrp, kprec, &s_, &n_, &cs_);
+        resident_settings(c, vr, kprec, &s_, &n_, &cs_);
         ca.split = cs_;
     }
     ca.KT = s.KT;
@@ -347,7 +408,7 @@ static int launch_sequence(swmd_corpus *c, Slot &s, Mapping m, int t, int path, 
     if (path == SWMD_PATH_RESIDENT) {
         ResidentArgs ra{ia, t};
         ra.it.first = 1;
-        return run_resident(c, ra, m, kprec, st);
+        return run_resident(c, ra, m, kprec, vr, st);
     }
     ia.conv = s.conv;   // the final step records the x-updates applied
     if (c->opt.tol > 0.f) {
@@ -376,8 +437,8 @@ static int launch_sequence(swmd_corpus *c, Slot &s, Mapping m, int t, int path, 
 
 int enqueue_query(swmd_corpus *c, Slot &s, const int *d_ids, const float *d_r, int vr,
                   float lambda, int t, double *d_out, int *d_status, cudaStream_t st,
-                  bool allow_graph) {
-    const int path = resolve_path(c, vr);
+                  bool allow_graph, int path) {
+    if (path < 0) path = resolve_path(c, vr);
     const int kprec = c->opt.k_precision;
     if (c->opt.tol > 0.f && path != SWMD_PATH_FUSED)
         return set_error(SWMD_EINVAL, "tol > 0 (convergence mode) needs the fused per-iteration path");
@@ -397,16 +458,19 @@ int enqueue_query(swmd_corpus *c, Slot &s, const int *d_ids, const float *d_r, i
     SWMD_CK(launch_prep(s.qp, lambda, vr, c->V, d_ids, d_r, s.q_ids, s.r, s.vrp_cap, d_out,
                         d_status ? d_status : s.status, st));
     const int shift = c->opt.column_shift ? 1 : 0;
-    if (!(allow_graph && c->opt.use_graph)) return launch_sequence(c, s, m, t, path, kprec, shift, st);
+    if (!(allow_graph && c->opt.use_graph)) return launch_sequence(c, s, m, vr, t, path, kprec, shift, st);
 
-    GraphKey key{m.vrp, m.q, m.p, t, path, kprec, shift, (const void *)&s};
+    int solver_ = 0, npl_ = 0, split_ = 0;
+    resident_settings(c, vr, kprec, &solver_, &npl_, &split_);
+    if (path == SWMD_PATH_RESIDENT) solver_ = resident_solver(c, vr, kprec);
+    GraphKey key{m.vrp, m.q, m.p, t, path, kprec, shift, solver_, npl_, split_, (const void *)&s};
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
         // The launch sequence of a new shape is captured once on the corpus's own
         // stream and replayed on the caller's stream from then on.
         cudaGraph_t g = nullptr;
         SWMD_CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
-        int rc = launch_sequence(c, s, m, t, path, kprec, shift, c->stream);
+        int rc = launch_sequence(c, s, m, vr, t, path, kprec, shift, c->stream);
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         if (rc) {
             if (g) cudaGraphDestroy(g);
@@ -716,6 +780,7 @@ void swmd_destroy_corpus(swmd_corpus *c) {
         dev_free(c->doc_orig);
         dev_free(c->tiles_dev);
         dev_free(c->tasks_dev);
+        dev_free(c->col_tasks_dev);
         if (c->h_io) cudaFreeHost(c->h_io);
         if (c->stream) cudaStreamDestroy(c->stream);
     }
@@ -748,6 +813,8 @@ int swmd_corpus_set_options(swmd_corpus *c, const swmd_options *opt) {
         !(opt->tol >= 0.f) || std::isinf(opt->tol))
         return set_error(SWMD_EINVAL, "swmd_corpus_set_options: bad k_precision or path");
     std::lock_guard<std::mutex> lk(c->mu);
+    if (c->servers > 0)
+        return set_error(SWMD_EINVAL, "swmd_corpus_set_options: a server is attached to the corpus");
     c->opt.k_precision = opt->k_precision;
     c->opt.path = opt->path;
     c->opt.use_graph = opt->use_graph;
@@ -877,7 +944,7 @@ int swmd_step_cost(swmd_corpus *c, const int32_t *d_ids, const float *d_r, int32
     ca.shift = c->opt.column_shift ? 1 : 0;
     {
         int s_ = 0, n_ = 0, cs_ = 0;
-        resident_settings(c, m.vrp, c->opt.k_precision, &s_, &n_, &cs_);
+        resident_settings(c, v_r, c->opt.k_precision, &s_, &n_, &cs_);
         ca.split = cs_;
     }
     ca.KT = s.KT;
@@ -949,7 +1016,7 @@ int swmd_step_resident(swmd_corpus *c, int32_t v_r, int32_t max_iter, double *d_
     const Mapping m = walk_mapping(c, vrp, SWMD_PATH_RESIDENT);
     ResidentArgs ra{iter_args(c, s), max_iter};
     ra.it.out = d_out;
-    return run_resident(c, ra, m, c->opt.k_precision, st);
+    return run_resident(c, ra, m, c->opt.k_precision, v_r, st);
 }
 
 int swmd_get_mapping(swmd_corpus *c, int32_t v_r, int32_t path, int32_t *out3) {

@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 namespace swmd {
 
 // Bits of the device status word.
@@ -174,6 +176,13 @@ struct TaskSet {
     int max_len;   // longest document (sizes the per-warp overflow buffer)
 };
 int regs_rows_per_lane(int vrp, int want);
+// one translation unit per K precision (resident_regs_{fp32,bf16,fp16}.cu)
+cudaError_t launch_regs_fp32(const ResidentArgs &a, int vrp, const TaskSet &ts, int sms, cudaStream_t s,
+                             int nq, const ResidentArgs *batch);
+cudaError_t launch_regs_bf16(const ResidentArgs &a, int vrp, const TaskSet &ts, int sms, cudaStream_t s,
+                             int nq, const ResidentArgs *batch);
+cudaError_t launch_regs_fp16(const ResidentArgs &a, int vrp, const TaskSet &ts, int sms, cudaStream_t s,
+                             int nq, const ResidentArgs *batch);
 cudaError_t launch_resident_regs(const ResidentArgs &a, int vrp, int kprec, const TaskSet &ts,
                                  int sms, cudaStream_t s, int nq = 1,
                                  const ResidentArgs *d_batch = nullptr);
@@ -235,5 +244,102 @@ template <> struct KIO<__half> {
 };
 
 inline size_t kprec_bytes(int kprec) { return kprec == 0 ? 4 : 2; }
+
+// ---------------------------------------------------------------- launch settings
+// Launch settings of one kernel, kept per device and read under a lock.
+// cudaFuncSetAttribute applies to the current device only, and the occupancy a
+// grid is sized from depends on the device, so neither may be shared between the
+// GPUs one process drives.
+constexpr int kMaxDevices = 64;
+struct LaunchCache {
+    std::mutex mu;
+    size_t smem_set[kMaxDevices] = {};   // dynamic shared-memory limit raised to, per device
+    bool carve_set[kMaxDevices] = {};    // preferred carveout set on the device
+    int per_sm[kMaxDevices] = {};        // resident blocks per SM ...
+    size_t key[kMaxDevices] = {};        // ... measured for this (shared memory, threads)
+
+    // Blocks of `kern` per SM on the current device at `threads` threads and `smem`
+    // bytes of dynamic shared memory, raising the kernel's dynamic shared-memory
+    // limit on this device to `smem` first; carveout >= 0 also sets the
+    // preferred shared-memory carveout (percent) once per device (a hint: a refusal
+    // is ignored).
+    template <class K>
+    cudaError_t blocks_per_sm(K kern, int threads, size_t smem, int carveout, int *out) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+        std::lock_guard<std::mutex> lk(mu);
+        // (raised for any size above the last: the 48 KiB default covers static and
+        // dynamic shared memory together)
+        if (smem > smem_set[dev]) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            smem_set[dev] = smem;
+            key[dev] = 0;
+        }
+        if (carveout >= 0 && !carve_set[dev]) {
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carveout) !=
+                cudaSuccess)
+                (void)cudaGetLastError();
+            carve_set[dev] = true;
+            key[dev] = 0;
+        }
+        const size_t k = (smem << 12) + (size_t)threads + 1;   // threads < 4096
+        if (key[dev] != k) {
+            int n = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess || n < 1) {
+                (void)cudaGetLastError();
+                n = 1;
+            }
+            per_sm[dev] = n;
+            key[dev] = k;
+        }
+        *out = per_sm[dev];
+        return cudaSuccess;
+    }
+};
+
+// ---------------------------------------------------------------- column-split solver
+// Arguments of the column-split register solver (resident_cols.cu).  The per-query
+// fields come from a ResidentArgs (it.KT, it.KMT at a power-of-two VRP in 4..128,
+// it.r zero-padded to VRP, it.qp, it.out, t).
+struct ColArgs {
+    const int *doc_ptr;
+    const int2 *nz;
+    const int *doc_orig;
+    const int4 *tasks;     // (first document, documents, bucket, 0) warp tasks
+    int n_tasks;
+    int kprec;
+    ResidentArgs q0;                 // the query when `queries` is NULL
+    const ResidentArgs *queries;     // device array: grid row y runs queries[y]
+};
+// Documents longer than this are not held by the column-split solver.
+constexpr int kColMaxLen = 32;
+// Rows a document of `len` words occupies in the column-split solver for layout
+// `vrp` (the bucket: 8, 16, 24 or 32, a multiple of vrp / 4); 0 if too long.
+int cols_bucket(int len, int vrp);
+// A bucket of lmax rows is held by G row groups of Q = vrp / 4 lanes, each group
+// RL = lmax / G rows (a multiple of Q, at most 24, or 32 when Q = 32): documents
+// of 25..32 words use two groups of 16 rows.  cols_fits: the bucket exists for vrp.
+__host__ __device__ constexpr int cols_groups(int lmax, int vrp) {
+    return vrp / 4 >= 32 ? 1 : (lmax <= 24 ? 1 : 2);
+}
+__host__ __device__ constexpr bool cols_fits(int lmax, int vrp) {
+    return (lmax / cols_groups(lmax, vrp)) % (vrp / 4) == 0;
+}
+// Lanes that own one document of a bucket (G Q).
+__host__ __device__ constexpr int cols_team(int lmax, int vrp) { return cols_groups(lmax, vrp) * (vrp / 4); }
+bool cols_supported(int vrp);
+// The layout (VRP) the column-split solver uses for a query of vr words: the
+// power of two >= max(vr, 16).
+int cols_vrp(int vr);
+// Index of a column-split layout in the corpus's task lists (VRP 16, 32, 64, 128).
+inline int cols_index(int vrp) { return vrp == 16 ? 0 : vrp == 32 ? 1 : vrp == 64 ? 2 : 3; }
+constexpr int kColLayouts = 4;
+// Runs all t iterations and the final step for every document of the tasks;
+// nq > 1: grid rows y = 0..nq-1 run a.queries[y].
+cudaError_t launch_resident_cols(const ColArgs &a, int vrp, int sms, cudaStream_t s, int nq);
+
 
 }  // namespace swmd

@@ -73,7 +73,8 @@ struct Slot {
 };
 
 // Key of a captured launch sequence: everything baked into the launches.
-using GraphKey = std::tuple<int, int, int, int, int, int, int, const void *>;  // vrp,q,p,t,path,kprec,shift,slot
+// vrp, q, p, t, path, kprec, shift, resident solver, rows per lane, cost split, slot
+using GraphKey = std::tuple<int, int, int, int, int, int, int, int, int, int, const void *>;
 
 struct Segment {
     long d0, d1;   // documents [d0, d1) in internal order
@@ -113,6 +114,11 @@ struct swmd_corpus {
     int4 *tasks_dev = nullptr;
     int task_off[9] = {0};         // indexed by rows per lane (1..8)
     int task_count[9] = {0};
+    // warp tasks of the column-split register solver, one list per layout (VRP 16,
+    // 32, 64, 128); built only when no document has more than kColMaxLen words
+    int4 *col_tasks_dev = nullptr;
+    int col_off[swmd::kColLayouts] = {0};
+    int col_count[swmd::kColLayouts] = {0};
 
     swmd::Slot main;               // workspace of the single-query path
     void *batch_ws = nullptr;      // workspace of swmd_query_batch (grown on demand)
@@ -128,19 +134,25 @@ struct swmd_corpus {
     std::map<swmd::GraphKey, cudaGraphExec_t> graphs;
     std::map<std::vector<int64_t>, cudaGraphExec_t> batch_graphs;   // swmd_query_batch shapes
     std::map<std::tuple<int, int, int>, swmd::Mapping> tuned;  // (vr bucket, path, kprec)
-    // autotuned resident-path settings per (VRP, K precision): solver, rows per lane, cost split
+    // autotuned resident-path settings per (v_r, K precision): solver, rows per lane, cost split
     std::map<std::pair<int, int>, std::tuple<int, int, int>> tuned_resident;
     // autotuned path (RESIDENT or FUSED) per (v_r, K precision), used by SWMD_PATH_AUTO
     std::map<std::pair<int, int>, int> tuned_path;
     std::mutex mu;                 // serialises use of `main` and the graph cache
+    int servers = 0;               // servers attached (under mu): tuning and option changes wait
 };
 
 namespace swmd {
 
+// The K^T / u row length a workspace needs for queries of up to max_vr words.
+int max_vrp_of(int max_vr);
 int alloc_slot(swmd_corpus *c, Slot &s, int max_vr, int kprec, bool with_v);
 void free_slot(Slot &s);
 Mapping choose_mapping(swmd_corpus *c, int vr, int path);
 int layout_vrp(swmd_corpus *c, int vr, int path);
+// The tight resident layout (v_r padded to the solver's multiple of 4, 8 or 16)
+// of every resident solver but the column-split one.
+int tight_vrp(int vr);
 // The concrete path a query of vr words takes (resolves SWMD_PATH_AUTO).
 int resolve_path(swmd_corpus *c, int vr);
 // Corpora with fewer documents than this take the resident path under SWMD_PATH_AUTO
@@ -150,25 +162,36 @@ constexpr int kAutoResidentVr = 24;
 Mapping walk_mapping(swmd_corpus *c, int vrp, int path);
 // Enqueues a whole query whose ids / r are already in device memory (d_ids,
 // d_r), writing the distances to d_out and the status to d_status.
+// path >= 0: the path already resolved for this query (a server resolves it once,
+// at admission); -1: resolve_path.
 int enqueue_query(swmd_corpus *c, Slot &s, const int *d_ids, const float *d_r, int vr,
                   float lambda, int t, double *d_out, int *d_status, cudaStream_t st,
-                  bool allow_graph);
+                  bool allow_graph, int path = -1);
 int status_to_code(int st);
 // Destroys every captured graph of the corpus (single queries and batches).
 void clear_graphs(swmd_corpus *c);
-// Launches the all-iterations solver: the shared-memory tiled kernel when the
-// query's layout allows it, else the register-only resident walk.
-int run_resident(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kprec, cudaStream_t st);
-// The same for nq queries of one layout in one launch (d_batch: device array of
-// their arguments; `shape` is any one of them).
-int run_resident_batch(swmd_corpus *c, const ResidentArgs &shape, Mapping m, int kprec, int nq,
+// Launches the all-iterations solver of resident_solver (the register walk that
+// re-gathers rows from L2 when no other solver takes the layout).
+// vr: the query's words (it selects the solver, see resident_solver).
+int run_resident(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kprec, int vr, cudaStream_t st);
+// The same for nq queries of one layout and one solver in one launch (d_batch:
+// device array of their arguments; `shape` is any one of them, vr any one's size).
+int run_resident_batch(swmd_corpus *c, const ResidentArgs &shape, Mapping m, int kprec, int vr, int nq,
                        const ResidentArgs *d_batch, cudaStream_t st);
+// Resident solvers (swmd_options.solver).
+constexpr int kSolverAuto = 0, kSolverRegs = 1, kSolverTiled = 2, kSolverL2 = 3, kSolverCols = 4;
+// The solver a resident query of vr words runs: swmd_options.solver, else the
+// autotuned one, else the column-split register solver when the corpus allows it
+// (no document above kColMaxLen words), else kSolverAuto (register solver for
+// VRP <= 32, else the shared-memory tiled one).  Never kSolverCols on a corpus
+// without column-split tasks.
+int resident_solver(swmd_corpus *c, int vr, int kprec);
 constexpr int kTileBudgets[] = {64, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048};
 constexpr int kNumTileBudgets = 10;
 // (Re)builds the resident solver's tile sets for the corpus's current
 // tile_threads / nnz_per_lane (allocates: only at creation or on an option change).
 int build_tiles(swmd_corpus *c);
-// Builds the register-resident solver's warp task lists (at corpus creation).
+// Builds the register-resident solvers' warp task lists (at corpus creation).
 int build_tasks(swmd_corpus *c);
 // 1-to-1 pairs (pairs.cu): enqueues the distances of n_pairs selected, normalised
 // (query, target) pairs held in device memory; max_q / max_x bound every pair's sizes.
@@ -193,7 +216,8 @@ constexpr int kPairMaxWords = 4096;
 // outside its declared size bound
 constexpr int ST_BAD_SIZE = 16;
 int enqueue_pairs(swmd_corpus *c, const PairJob &job, cudaStream_t st);
-// Effective resident settings for a layout: explicit options, else autotuned, else defaults.
-void resident_settings(swmd_corpus *c, int vrp, int kprec, int *solver, int *npl_want, int *split);
+// Effective resident settings for a query of vr words: explicit options, else
+// autotuned, else defaults (0).
+void resident_settings(swmd_corpus *c, int vr, int kprec, int *solver, int *npl_want, int *split);
 
 }  // namespace swmd

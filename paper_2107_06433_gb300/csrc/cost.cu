@@ -44,9 +44,7 @@ __device__ __forceinline__ float storage_scale(float mmax) {
 }
 
 template <int KPT, int T, class KT_t>
-__global__ void __launch_bounds__(kCostThreads) k_cost(CostArgs a0, const CostArgs *batch) {
-    // one query per grid row when batched (batch[blockIdx.y]), else the argument
-    const CostArgs a = batch ? batch[blockIdx.y] : a0;
+__device__ __noinline__ void k_cost_body(const CostArgs &a) {
     constexpr int VRP = KPT * T;
     constexpr int ROW = KPT + 4;  // padded slice: T slices of a stage row in distinct banks
     static_assert(KPT % 4 == 0, "KPT must be a multiple of 4");
@@ -141,6 +139,13 @@ __global__ void __launch_bounds__(kCostThreads) k_cost(CostArgs a0, const CostAr
     }
 }
 
+template <int KPT, int T, class KT_t>
+__global__ void __launch_bounds__(kCostThreads) k_cost(const __grid_constant__ CostArgs a0, const CostArgs *batch) {
+    // one query per grid row when batched (batch[blockIdx.y]), else the argument
+    if (batch) k_cost_body<KPT, T, KT_t>(batch[blockIdx.y]);
+    else k_cost_body<KPT, T, KT_t>(a0);
+}
+
 // Query blocks of up to 32 words: the whole transposed query block Q^T[d4][VRP]
 // sits in shared memory (loaded once per persistent block).  TS adjacent threads
 // own one word and take its embedding row's float4 chunks in turn (chunk i goes
@@ -148,8 +153,7 @@ __global__ void __launch_bounds__(kCostThreads) k_cost(CostArgs a0, const CostAr
 // chunks per thread in flight (register double buffer); the main loop has no
 // barrier.  The TS partial sums are combined with shuffles at the end.
 template <int VRP, int TS, class KT_t>
-__global__ void __launch_bounds__(kCostThreads) k_cost_rows(CostArgs a0, const CostArgs *batch) {
-    const CostArgs a = batch ? batch[blockIdx.y] : a0;
+__device__ __noinline__ void k_cost_rows_body(const CostArgs &a) {
     static_assert(VRP % 4 == 0 && VRP <= 32, "VRP");
     static_assert(TS == 1 || TS == 2 || TS == 4, "TS");
     constexpr int PF = 4;   // float4 chunks per thread in flight
@@ -266,23 +270,20 @@ __global__ void __launch_bounds__(kCostThreads) k_cost_rows(CostArgs a0, const C
 }
 
 template <int VRP, int TS, class KT_t>
+__global__ void __launch_bounds__(kCostThreads) k_cost_rows(const __grid_constant__ CostArgs a0, const CostArgs *batch) {
+    // one query per grid row when batched (batch[blockIdx.y]), else the argument
+    if (batch) k_cost_rows_body<VRP, TS, KT_t>(batch[blockIdx.y]);
+    else k_cost_rows_body<VRP, TS, KT_t>(a0);
+}
+
+template <int VRP, int TS, class KT_t>
 cudaError_t run_rows(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *batch) {
     auto kern = k_cost_rows<VRP, TS, KT_t>;
     const size_t smem = (size_t)a.d4 * VRP * sizeof(float);
-    static size_t configured = 0;
-    static int per_sm = 0;
-    static size_t per_sm_smem = 0;
-    if (smem > 48 * 1024 && configured < smem) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
-    if (per_sm <= 0 || per_sm_smem != smem) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCostThreads, smem) != cudaSuccess ||
-            per_sm < 1)
-            { (void)cudaGetLastError(); per_sm = 1; }
-        per_sm_smem = smem;
-    }
+    static LaunchCache cache;
+    int per_sm = 1;
+    cudaError_t e = cache.blocks_per_sm(kern, kCostThreads, smem, -1, &per_sm);
+    if (e != cudaSuccess) return e;
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -27,7 +27,7 @@ constexpr size_t kScratchBytes = size_t(16) << 20;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
+using swmd::kMaxDevices;
 std::mutex g_lookup_mu;
 void *g_scratch_ptr[kMaxDevices] = {};
 
@@ -108,7 +108,7 @@ extern "C" int swmd_query_noalloc(swmd_corpus *c, const int32_t *d_ids, const fl
     ca.shift = c->opt.column_shift ? 1 : 0;
     {
         int s_ = 0, n_ = 0, cs_ = 0;
-        resident_settings(c, m.vrp, kprec, &s_, &n_, &cs_);
+        resident_settings(c, v_r, kprec, &s_, &n_, &cs_);
         ca.split = cs_;
     }
     ca.KT = KT;
@@ -126,5 +126,5 @@ extern "C" int swmd_query_noalloc(swmd_corpus *c, const int32_t *d_ids, const fl
     ia.N = c->Nl;
     ia.first = 1;
     ResidentArgs ra{ia, max_iter};
-    return run_resident(c, ra, m, kprec, st);
+    return run_resident(c, ra, m, kprec, v_r, st);
 }

@@ -1,0 +1,400 @@
+// a3 x t + a4 in one launch, each document's K^T rows held in registers and split
+// by columns across a team of lanes.
+//
+// Every column of c is an independent problem in Algorithm 1.  With A_j the
+// len_j x v_r matrix of the K^T rows of document j's words, one x-update is
+// s = A_j u_j, tau = c_j ./ s, acc = A_j^T tau, u_j = r ./ acc (the fused
+// SDDMM_SpMM of Section III-C, type 1), and the final step is
+// WMD_j = sum_w c_wj (KM^T[w] . u_j) / (K^T[w] . u_j) (type 2).  A_j does not
+// change between iterations, so it is gathered once and kept in registers.
+//
+// Lanes.  A team of Q = VRP / 4 lanes owns a document; lane q holds columns
+// [4q, 4q + 4) of every row of A_j (LMAX rows, the document's length rounded up
+// to its bucket, zero rows past the end), of u_j and of acc.  acc = A_j^T tau then
+// needs no exchange.  The dots s = A_j u_j are partial over the lane's columns and
+// are finished by a reduce-scatter over the team: after it lane q holds the full
+// dots of rows [qR, qR + R), R = LMAX / Q, computes their tau, and an all-gather
+// gives every lane all of tau.  Both are log2(Q) butterfly steps that move half of
+// the remaining values each (LMAX (1 - 1/Q) shuffles per lane and direction).  For
+// the butterfly to need no selects, lane q stores row block b ^ q (blocks of R
+// rows) in register block b: then at every step all lanes keep the same register
+// blocks and send the same others.  Rows are gathered in natural order (one
+// coalesced 16-byte slice per lane of each row) and put into that order once, by
+// log2(Q) passes of conditional swaps.
+//
+// Register row i is paired with register row i + LMAX/2 as a float2, so the dots
+// of two rows and the contributions of two rows to acc are one packed f32x2 FMA.
+//
+// A document's arithmetic depends on its own nonzeros and on its bucket (a
+// function of its length) only, so it gives the same bits alone, batched, served
+// or in any document range.
+#include "walk3.cuh"
+
+namespace swmd {
+namespace {
+
+constexpr int kColThreads = 128;
+constexpr int kColP = 4;   // K^T columns per lane
+
+// Four K^T values [4 idx4, 4 idx4 + 4) of the word-major layout, widened to float.
+__device__ __forceinline__ float4 load_slice(const void *base, int kprec, long idx4) {
+    if (kprec == 0) return __ldg(reinterpret_cast<const float4 *>(base) + idx4);
+    const uint2 raw = __ldg(reinterpret_cast<const uint2 *>(base) + idx4);
+    if (kprec == 1)
+        return make_float4(__uint_as_float(raw.x << 16), __uint_as_float(raw.x & 0xffff0000u),
+                           __uint_as_float(raw.y << 16), __uint_as_float(raw.y & 0xffff0000u));
+    __half2 a, b;
+    memcpy(&a, &raw.x, sizeof a);
+    memcpy(&b, &raw.y, sizeof b);
+    const float2 fa = __half22float2(a), fb = __half22float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
+// Row slices [4 idx4, 4 idx4 + 4) of the word-major layout for every register row
+// i of the lane (rows past the document's end read word 0: finite values whose
+// tau is masked to 0), widened to float.  One unrolled loop per storage type, so
+// all RL loads of a lane are in flight together.
+template <int VRP, int RL>
+__device__ __forceinline__ void gather_rows(float4 (&rv)[RL], const void *base, int kprec, const int (&wv)[RL],
+                                            int ql) {
+    constexpr long S4 = VRP / 4;
+    if (kprec == 0) {
+        const float4 *b = reinterpret_cast<const float4 *>(base) + ql;
+#pragma unroll
+        for (int i = 0; i < RL; ++i) rv[i] = __ldg(b + (long)wv[i] * S4);
+    } else {
+        const uint2 *b = reinterpret_cast<const uint2 *>(base) + ql;
+        uint2 raw[RL];
+#pragma unroll
+        for (int i = 0; i < RL; ++i) raw[i] = __ldg(b + (long)wv[i] * S4);
+        if (kprec == 1) {   // a bfloat16 is the upper half of the float with the same value
+#pragma unroll
+            for (int i = 0; i < RL; ++i)
+                rv[i] = make_float4(__uint_as_float(raw[i].x << 16), __uint_as_float(raw[i].x & 0xffff0000u),
+                                    __uint_as_float(raw[i].y << 16), __uint_as_float(raw[i].y & 0xffff0000u));
+        } else {
+#pragma unroll
+            for (int i = 0; i < RL; ++i) {
+                __half2 a, c;
+                memcpy(&a, &raw[i].x, sizeof a);
+                memcpy(&c, &raw[i].y, sizeof c);
+                const float2 fa = __half22float2(a), fc = __half22float2(c);
+                rv[i] = make_float4(fa.x, fa.y, fc.x, fc.y);
+            }
+        }
+    }
+}
+
+// Puts row block b ^ ql into register block b (blocks of R rows): conditional
+// swaps of whole rows, one pass per bit of ql.
+template <int RL, int Q, int R>
+__device__ __forceinline__ void permute_rows(float4 (&rv)[RL], int ql) {
+#pragma unroll
+    for (int bit = 1; bit < Q; bit <<= 1) {
+        const bool sw = (ql & bit) != 0;
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+            if ((i / R) & bit) continue;   // each pair of blocks once, from its lower block
+            const int j = i + bit * R;
+            const float4 x = rv[i], y = rv[j];
+            rv[i] = sw ? y : x;
+            rv[j] = sw ? x : y;
+        }
+    }
+}
+
+// Partial dots of every register row with the lane's slice of u.
+template <int RL>
+__device__ __forceinline__ void partial_dots(const float4 (&rv)[RL], const float (&u)[kColP], float (&s)[RL]) {
+    const float2 u01 = make_float2(u[0], u[1]), u23 = make_float2(u[2], u[3]);
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+        float2 d = __fmul2_rn(make_float2(rv[i].x, rv[i].y), u01);
+        d = __ffma2_rn(make_float2(rv[i].z, rv[i].w), u23, d);
+        s[i] = d.x + d.y;
+    }
+}
+
+// Reduce-scatter over the Q lanes of a row group: afterwards s[0..R) hold the
+// group's full sums of the lane's own rows (register block 0).
+template <class T, int RL, int Q, int R>
+__device__ __forceinline__ void reduce_scatter(T (&s)[RL]) {
+#pragma unroll
+    for (int m = Q / 2; m >= 1; m >>= 1)
+#pragma unroll
+        for (int i = 0; i < m * R; ++i) s[i] += __shfl_xor_sync(kFull, s[i + m * R], m);
+}
+
+// All-gather over the Q lanes: tv[0..R) of every lane -> tv[i] for every register row.
+template <int RL, int Q, int R>
+__device__ __forceinline__ void all_gather(float (&tv)[RL]) {
+#pragma unroll
+    for (int m = 1; m < Q; m <<= 1)
+#pragma unroll
+        for (int i = 0; i < m * R; ++i) tv[m * R + i] = __shfl_xor_sync(kFull, tv[i], m);
+}
+
+// The FP64 guard for a K^T u below 2^-100 (rare, entered by the whole warp):
+// the lane's u slices are published in the warp's shared buffer `su` (lane l's
+// four values at 4 l), and the dot of an own row is recomputed in FP64 from the
+// stored row (the same, exactly widened values) and the team's whole u.
+__device__ __forceinline__ void publish_u(float *su, int lane, const float (&u)[kColP]) {
+    __syncwarp();
+    reinterpret_cast<float4 *>(su)[lane] = make_float4(u[0], u[1], u[2], u[3]);
+    __syncwarp();
+}
+template <int VRP>
+__device__ __forceinline__ double dot_fp64(const void *base, int kprec, int w, const float *su_team) {
+    double s = 0.0;
+#pragma unroll 4
+    for (int c = 0; c < VRP / 4; ++c) {
+        const float4 k4 = load_slice(base, kprec, (long)w * (VRP / 4) + c);
+        s = fma((double)k4.x, (double)su_team[4 * c], s);
+        s = fma((double)k4.y, (double)su_team[4 * c + 1], s);
+        s = fma((double)k4.z, (double)su_team[4 * c + 2], s);
+        s = fma((double)k4.w, (double)su_team[4 * c + 3], s);
+    }
+    return s;
+}
+
+// One task: up to 32 / (G Q) documents of one bucket (LMAX = G RL rows).  A team of
+// G row groups of Q lanes owns a document; group g holds rows [g RL, g RL + RL).
+// su: this warp's shared buffer (32 float4) for the FP64 guard.
+template <int VRP, int G, int RL>
+__device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &q, int4 tk, int lane,
+                                          float *su) {
+    constexpr int P = kColP, Q = VRP / P, R = RL / Q, TEAM = G * Q;
+    static_assert(Q >= 1 && Q <= 32 && (Q & (Q - 1)) == 0, "row groups of a power of two lanes");
+    static_assert(RL % Q == 0 && R >= 1 && TEAM <= 32 && (G & (G - 1)) == 0, "whole row blocks");
+    const int team = lane / TEAM, g = (lane / Q) % G, ql = lane % Q;
+    const bool has = team < tk.y;
+    const int doc = tk.x + team;
+    int beg = 0, len = 0;
+    if (has) {
+        beg = __ldg(a.doc_ptr + doc);
+        len = __ldg(a.doc_ptr + doc + 1) - beg;
+    }
+    const QParams *qp = q.it.qp;
+    const int vr = qp->vr;
+    const float u0 = qp->u0;
+    int *const status = qp->status;
+    const int2 *ent = a.nz + beg;
+    const int row0 = g * RL;                          // the group's first row
+    const float *su_team = su + 4 * (team * TEAM);    // the team's u, column-ordered (guard only)
+
+    // c of the rows this lane finishes (zero past the end: their tau is 0)
+    float cown[R];
+#pragma unroll
+    for (int o = 0; o < R; ++o) {
+        const int row = row0 + ql * R + o;
+        cown[o] = row < len ? __int_as_float(__ldg(&ent[row].y)) : 0.f;
+    }
+    float rr[P], u[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        const int col = ql * P + k;
+        rr[k] = __ldg(q.it.r + col);
+        u[k] = has && col < vr ? u0 : 0.f;
+    }
+    // the group's rows of K^T: word ids in natural order, all loads in flight at once
+    float4 rv[RL];
+    {
+        int wv[RL];
+#pragma unroll
+        for (int i = 0; i < RL; ++i) wv[i] = row0 + i < len ? __ldg(&ent[row0 + i].x) : 0;
+        gather_rows<VRP, RL>(rv, q.it.KT, a.kprec, wv, ql);
+    }
+    permute_rows<RL, Q, R>(rv, ql);
+
+    bool bad = false;
+    for (int it = 0; it < q.t; ++it) {
+        float tv[RL];
+        partial_dots<RL>(rv, u, tv);
+        reduce_scatter<float, RL, Q, R>(tv);
+        bool tiny = false;
+        float s_own[R];
+#pragma unroll
+        for (int o = 0; o < R; ++o) {
+            s_own[o] = tv[o];
+            const bool valid = cown[o] != 0.f;
+            tiny |= valid && !(tv[o] >= 0x1p-100f);
+            tv[o] = valid ? cown[o] * rcp_approx(tv[o]) : 0.f;
+        }
+        if (__any_sync(kFull, tiny)) {
+            SWMD_COLD_PATH();
+            publish_u(su, lane, u);
+#pragma unroll
+            for (int o = 0; o < R; ++o) {
+                if (cown[o] != 0.f && !(s_own[o] >= 0x1p-100f)) {
+                    const int w = __ldg(&ent[row0 + ql * R + o].x);
+                    const double sd = dot_fp64<VRP>(q.it.KT, a.kprec, w, su_team);
+                    tv[o] = sd > 0.0 ? (float)((double)cown[o] / sd) : 0.f;
+                    atomicOr(status, sd > 0.0 ? ST_GUARD : ST_NUMERIC);
+                }
+            }
+        }
+        all_gather<RL, Q, R>(tv);
+        float2 acc01 = make_float2(0.f, 0.f), acc23 = acc01;
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+            const float2 t2 = make_float2(tv[i], tv[i]);
+            acc01 = __ffma2_rn(make_float2(rv[i].x, rv[i].y), t2, acc01);
+            acc23 = __ffma2_rn(make_float2(rv[i].z, rv[i].w), t2, acc23);
+        }
+        // the row groups' partial sums (a + b = b + a: every group gets the same u)
+#pragma unroll
+        for (int m = Q; m < TEAM; m <<= 1) {
+            acc01.x += __shfl_xor_sync(kFull, acc01.x, m);
+            acc01.y += __shfl_xor_sync(kFull, acc01.y, m);
+            acc23.x += __shfl_xor_sync(kFull, acc23.x, m);
+            acc23.y += __shfl_xor_sync(kFull, acc23.y, m);
+        }
+        const float acc[P] = {acc01.x, acc01.y, acc23.x, acc23.y};
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            const int col = ql * P + k;
+            const bool live = has && col < vr;
+            const float nu = live ? rr[k] * rcp_approx(acc[k]) : 0.f;
+            bad |= live && !(nu < INFINITY);
+            u[k] = nu;
+        }
+    }
+
+    // final step: s = K^T[w].u and m = KM^T[w].u per nonzero, WMD = sum c m / s
+    float s_own[R];
+    bool tiny = false;
+    {
+        float tv[RL];
+        partial_dots<RL>(rv, u, tv);
+        reduce_scatter<float, RL, Q, R>(tv);
+#pragma unroll
+        for (int o = 0; o < R; ++o) {
+            s_own[o] = tv[o];
+            tiny |= cown[o] != 0.f && !(tv[o] >= 0x1p-100f);
+        }
+    }
+    {
+        int wv[RL];   // the word ids again (the registers were free during the iterations)
+#pragma unroll
+        for (int i = 0; i < RL; ++i) wv[i] = row0 + i < len ? __ldg(&ent[row0 + i].x) : 0;
+        gather_rows<VRP, RL>(rv, q.it.KMT, a.kprec, wv, ql);
+    }
+    permute_rows<RL, Q, R>(rv, ql);
+    double dist = 0.0;
+    {
+        float tv[RL];
+        partial_dots<RL>(rv, u, tv);
+        reduce_scatter<float, RL, Q, R>(tv);
+#pragma unroll
+        for (int o = 0; o < R; ++o)
+            if (cown[o] != 0.f && s_own[o] >= 0x1p-100f) dist += (double)(cown[o] * (tv[o] * rcp_approx(s_own[o])));
+    }
+    if (__any_sync(kFull, tiny)) {
+        SWMD_COLD_PATH();
+        publish_u(su, lane, u);
+#pragma unroll
+        for (int o = 0; o < R; ++o) {
+            if (cown[o] != 0.f && !(s_own[o] >= 0x1p-100f)) {
+                const int w = __ldg(&ent[row0 + ql * R + o].x);
+                const double sd = dot_fp64<VRP>(q.it.KT, a.kprec, w, su_team);
+                const double md = dot_fp64<VRP>(q.it.KMT, a.kprec, w, su_team);
+                dist += (double)cown[o] * (md / sd);
+                atomicOr(status, sd > 0.0 ? ST_GUARD : ST_NUMERIC);
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 1; m < TEAM; m <<= 1) dist += __shfl_xor_sync(kFull, dist, m);
+    if (bad) atomicOr(status, ST_NUMERIC);
+    if (has && g == 0 && ql == 0) {
+        if (!(fabs(dist) < INFINITY)) atomicOr(status, ST_NUMERIC);
+        double *const out = q.it.out ? q.it.out : qp->out;
+        out[__ldg(a.doc_orig + doc)] = dist;
+    }
+}
+
+// One block's share of the tasks for one query.
+template <int VRP>
+__device__ __forceinline__ void cols_block(const ColArgs &a, const ResidentArgs &q) {
+    __shared__ __align__(16) float s_u[kColThreads * 4];   // per warp: 32 lanes x 4 values of u
+    const int lane = threadIdx.x & 31;
+    float *su = s_u + 4 * (threadIdx.x & ~31);
+    const long gwarp = ((long)blockIdx.x * kColThreads + threadIdx.x) >> 5;
+    const long nwarps = ((long)gridDim.x * kColThreads) >> 5;
+    for (long task = gwarp; task < a.n_tasks; task += nwarps) {
+        const int4 tk = __ldg(a.tasks + task);   // first document, documents, bucket
+        switch (tk.z) {
+            case 8:
+                if constexpr (cols_fits(8, VRP)) cols_task<VRP, 1, 8>(a, q, tk, lane, su);
+                break;
+            case 16:
+                if constexpr (cols_fits(16, VRP)) cols_task<VRP, cols_groups(16, VRP), 16 / cols_groups(16, VRP)>(a, q, tk, lane, su);
+                break;
+            case 24:
+                if constexpr (cols_fits(24, VRP)) cols_task<VRP, 1, 24>(a, q, tk, lane, su);
+                break;
+            default:
+                cols_task<VRP, cols_groups(32, VRP), 32 / cols_groups(32, VRP)>(a, q, tk, lane, su);
+                break;
+        }
+    }
+}
+
+// BATCHED: grid row y runs a.queries[y] (a device array); else the query is the
+// kernel argument a.q0.  Two kernels, so neither selects between the two sources.
+template <int VRP, bool BATCHED>
+__global__ void __launch_bounds__(kColThreads) k_resident_cols(const __grid_constant__ ColArgs a) {
+    if constexpr (BATCHED) cols_block<VRP>(a, a.queries[blockIdx.y]);
+    else cols_block<VRP>(a, a.q0);
+}
+
+template <int VRP, bool BATCHED>
+cudaError_t run_cols_k(const ColArgs &a, int sms, int nq, cudaStream_t s) {
+    auto kern = k_resident_cols<VRP, BATCHED>;
+    static LaunchCache cache;
+    int per_sm = 1;
+    cudaError_t e = cache.blocks_per_sm(kern, kColThreads, 0, -1, &per_sm);
+    if (e != cudaSuccess) return e;
+    long blocks = ((long)a.n_tasks + kColThreads / 32 - 1) / (kColThreads / 32);
+    long cap = nq == 1 ? (long)sms * per_sm : ((long)sms * per_sm * 2 + nq - 1) / nq;
+    if (cap < 1) cap = 1;
+    if (blocks > cap) blocks = cap;
+    if (blocks > 0) kern<<<dim3((unsigned)blocks, (unsigned)nq), kColThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int VRP>
+cudaError_t run_cols(const ColArgs &a, int sms, int nq, cudaStream_t s) {
+    return a.queries ? run_cols_k<VRP, true>(a, sms, nq, s) : run_cols_k<VRP, false>(a, sms, nq, s);
+}
+
+}  // namespace
+
+int cols_bucket(int len, int vrp) {
+    for (int lmax : {8, 16, 24, 32})
+        if (cols_fits(lmax, vrp) && lmax >= len) return lmax;
+    return 0;
+}
+
+// Layouts of 16 to 128 columns (teams of 4 to 32 lanes).  Narrower queries are
+// padded to 16 columns: with teams of one or two lanes a lane would hold the
+// tau of up to 32 rows besides the rows themselves, more than its registers.
+bool cols_supported(int vrp) { return vrp == 16 || vrp == 32 || vrp == 64 || vrp == 128; }
+
+int cols_vrp(int vr) {
+    int v = 16;
+    while (v < vr) v *= 2;
+    return v;
+}
+
+cudaError_t launch_resident_cols(const ColArgs &a, int vrp, int sms, cudaStream_t s, int nq) {
+    switch (vrp) {
+        case 16: return run_cols<16>(a, sms, nq, s);
+        case 32: return run_cols<32>(a, sms, nq, s);
+        case 64: return run_cols<64>(a, sms, nq, s);
+        case 128: return run_cols<128>(a, sms, nq, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace swmd

@@ -52,11 +52,7 @@ template <> __device__ __forceinline__ float4 ld4<__half>(const __half *p, int i
 }
 
 template <int VRP, int Q, class KT_t>
-__global__ void __launch_bounds__(kTileThreads) k_resident_tiled(ResidentArgs ra0, const ResidentArgs *batch,
-                                                                 const int *tiles, int n_tiles, int NT,
-                                                                 int npl) {
-    // one query per grid row when batched (batch[blockIdx.y]), else the argument
-    const ResidentArgs ra = batch ? batch[blockIdx.y] : ra0;
+__device__ __noinline__ void k_resident_tiled_body(const ResidentArgs &ra, const int *tiles, int n_tiles, int NT, int npl) {
     constexpr int S = VRP / Q;
     constexpr int C = S / 4;
     constexpr int ROWB = VRP * (int)sizeof(KT_t);          // bytes of one row
@@ -285,28 +281,23 @@ __global__ void __launch_bounds__(kTileThreads) k_resident_tiled(ResidentArgs ra
 }
 
 template <int VRP, int Q, class KT_t>
+__global__ void __launch_bounds__(kTileThreads)
+k_resident_tiled(const __grid_constant__ ResidentArgs ra0, const ResidentArgs *batch, const int *tiles,
+                 int n_tiles, int NT, int npl) {
+    // one query per grid row when batched (batch[blockIdx.y]), else the argument
+    if (batch) k_resident_tiled_body<VRP, Q, KT_t>(batch[blockIdx.y], tiles, n_tiles, NT, npl);
+    else k_resident_tiled_body<VRP, Q, KT_t>(ra0, tiles, n_tiles, NT, npl);
+}
+
+template <int VRP, int Q, class KT_t>
 cudaError_t run_tiled(const ResidentArgs &a, const TileSet &ts, int sms, cudaStream_t s, int nq,
                       const ResidentArgs *batch) {
     auto kern = k_resident_tiled<VRP, Q, KT_t>;
     const size_t smem = tiled_smem_bytes(VRP, (int)sizeof(KT_t), ts.nt);
-    static int configured_smem = 0;
-    static int per_sm = 0;
-    static size_t per_sm_key = 0;
-    if (configured_smem < (int)smem) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        if (e != cudaSuccess) return e;
-        configured_smem = (int)smem;
-        per_sm = 0;
-    }
-    const size_t key = smem * 1024 + (size_t)ts.threads;
-    if (per_sm <= 0 || per_sm_key != key) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ts.threads, smem) != cudaSuccess ||
-            per_sm < 1)
-            { (void)cudaGetLastError(); per_sm = 1; }
-        per_sm_key = key;
-    }
+    static LaunchCache cache;
+    int per_sm = 1;
+    cudaError_t e = cache.blocks_per_sm(kern, ts.threads, smem, 100, &per_sm);
+    if (e != cudaSuccess) return e;
     int blocks = nq == 1 ? sms * per_sm : (sms * per_sm * 2 + nq - 1) / nq;
     if (blocks < 1) blocks = 1;
     if (blocks > ts.n_tiles) blocks = ts.n_tiles;

@@ -80,6 +80,8 @@ struct Request {
     int vr = 0;
     float lambda = 1.f;
     int t = 0;
+    int path = -1;   // resolved once, at admission
+    int vrp = 0;     // its K^T layout
     double t_submit = 0, t_done = 0;
     int state = 0;  // 0 queued, 1 running, 2 finished
     int code = SWMD_OK;
@@ -125,6 +127,7 @@ struct swmd_server {
     // statistics
     std::vector<double> lat_ms;
     int64_t completed = 0, rejected = 0, batches = 0, admitted = 0;
+    int waiters = 0;   // threads inside swmd_serve_wait (swmd_serve_stop frees only at 0)
     double t_first = -1, t_last = -1;
 };
 
@@ -151,9 +154,8 @@ void finish(swmd_server *S, ServerSlot &sl, int code, const std::string &err) {
 int launch_on_slot(swmd_server *S, ServerSlot &sl) {
     swmd_corpus *c = S->c;
     auto &R = *sl.req;
-    const int path = resolve_path(c, R.vr);
-    const Mapping m = choose_mapping(c, R.vr, path);
-    const size_t kbytes = (size_t)c->Vu * m.vrp * kprec_bytes(c->opt.k_precision);
+    const int path = R.path;
+    const size_t kbytes = (size_t)c->Vu * R.vrp * kprec_bytes(c->opt.k_precision);
     char *p = static_cast<char *>(sl.arena_ptr);
     auto carve = [&](size_t n) {
         char *q = p;
@@ -162,7 +164,7 @@ int launch_on_slot(swmd_server *S, ServerSlot &sl) {
     };
     sl.ws.KT = carve(kbytes);
     sl.ws.KMT = carve(kbytes);
-    sl.ws.u = path != SWMD_PATH_RESIDENT ? (float *)carve((size_t)c->Nl * m.vrp * sizeof(float)) : nullptr;
+    sl.ws.u = path != SWMD_PATH_RESIDENT ? (float *)carve((size_t)c->Nl * R.vrp * sizeof(float)) : nullptr;
     sl.ws.v_elems = path == SWMD_PATH_PLAIN ? std::max(c->nnz, c->slice_total) : 0;
     sl.ws.v = path == SWMD_PATH_PLAIN ? (float *)carve((size_t)sl.ws.v_elems * sizeof(float)) : nullptr;
     std::memcpy(sl.h_q, R.ids.data(), sizeof(int32_t) * R.vr);
@@ -173,7 +175,7 @@ int launch_on_slot(swmd_server *S, ServerSlot &sl) {
     {
         std::lock_guard<std::mutex> lk(c->mu);
         rc = enqueue_query(c, sl.ws, sl.ws.q_in, sl.ws.r_in, R.vr, R.lambda, R.t, sl.ws.out,
-                           sl.ws.status, sl.stream, false);
+                           sl.ws.status, sl.stream, false, path);
     }
     if (rc) return rc;
     SWMD_CK(cudaMemcpyAsync(sl.h_out, sl.ws.out, sizeof(double) * c->Nl, cudaMemcpyDeviceToHost, sl.stream));
@@ -199,9 +201,12 @@ void worker_main(swmd_server *S) {
             for (auto &sl : S->slots) {
                 if (sl.req || S->pending.empty()) continue;
                 auto R = S->pending.front();
-                const int rpath = resolve_path(S->c, R->vr);
-                const Mapping mp = choose_mapping(S->c, R->vr, rpath);
-                const size_t need = query_bytes(S->c, mp.vrp, rpath);
+                if (R->path < 0) {   // the path and layout, once (options cannot change while served)
+                    std::lock_guard<std::mutex> cl(S->c->mu);
+                    R->path = resolve_path(S->c, R->vr);
+                    R->vrp = choose_mapping(S->c, R->vr, R->path).vrp;
+                }
+                const size_t need = query_bytes(S->c, R->vrp, R->path);
                 void *mem = S->arena.alloc(need);
                 if (!mem) break;   // admission waits for memory to free up
                 S->pending.pop_front();
@@ -309,7 +314,9 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
     // as one launch pair per query); per-iteration queries run one after another on
     // the corpus's slot.
     std::vector<int> path((size_t)n_queries), vrp((size_t)n_queries, 0);
-    std::map<int, std::vector<int>> groups;   // layout VRP -> resident queries
+    // (layout VRP, solver, rows per lane, cost split) -> resident queries: everything
+    // a batched launch shares
+    std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
     std::vector<int> others;                  // per-iteration queries
     for (int32_t i = 0; i < n_queries; ++i) {
         path[i] = resolve_path(c, vrs[i]);
@@ -317,7 +324,9 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
             return set_error(SWMD_EINVAL, "tol > 0 (convergence mode) needs the fused per-iteration path");
         if (path[i] == SWMD_PATH_RESIDENT) {
             vrp[i] = layout_vrp(c, vrs[i], SWMD_PATH_RESIDENT);
-            groups[vrp[i]].push_back(i);
+            int s_ = 0, n_ = 0, cs_ = 0;
+            resident_settings(c, vrs[i], kprec, &s_, &n_, &cs_);
+            groups[std::make_tuple(vrp[i], resident_solver(c, vrs[i], kprec), n_, cs_)].push_back(i);
         } else {
             others.push_back(i);
         }
@@ -399,7 +408,7 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
         ca.shift = c->opt.column_shift ? 1 : 0;
         {
             int s_ = 0, n_ = 0, cs_ = 0;
-            resident_settings(c, vrp[i], kprec, &s_, &n_, &cs_);
+            resident_settings(c, vrs[i], kprec, &s_, &n_, &cs_);
             ca.split = cs_;
         }
         ca.KT = KT;
@@ -421,7 +430,7 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
     // launch reads element y of its slice)
     std::vector<CostArgs> cost_g;
     std::vector<ResidentArgs> res_g;
-    std::vector<std::pair<int, size_t>> gstart;   // (vrp, first index in the grouped arrays)
+    std::vector<std::pair<std::tuple<int, int, int, int>, size_t>> gstart;   // (group, first index in the grouped arrays)
     for (auto &g : groups) {
         gstart.emplace_back(g.first, cost_g.size());
         for (int i : g.second) {
@@ -454,9 +463,10 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
         if (!prep.empty()) {
             SWMD_CK(launch_prep_batch(reinterpret_cast<const PrepArgs *>(ws + o_prep), (int)prep.size(), c->V, st));
             for (size_t gi = 0; gi < gstart.size(); ++gi) {
-                const int v = gstart[gi].first;
+                const int v = std::get<0>(gstart[gi].first);
                 const size_t g0 = gstart[gi].second;
-                const int ng = (int)groups[v].size();
+                const std::vector<int> &members = groups[gstart[gi].first];
+                const int ng = (int)members.size();
                 const Mapping m = walk_mapping(c, v, SWMD_PATH_RESIDENT);
                 // From kAutoResidentDocs documents up one query's launches fill the GPU
                 // many times over, and queries run side by side only compete for L2
@@ -468,7 +478,7 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
                     const int nj = std::min(step, ng - j0);
                     SWMD_CK(launch_cost_batch(cost_g[g0 + j0], v, kprec, nj,
                                               reinterpret_cast<const CostArgs *>(ws + o_cost) + g0 + j0, st));
-                    int rc = run_resident_batch(c, res_g[g0 + j0], m, kprec, nj,
+                    int rc = run_resident_batch(c, res_g[g0 + j0], m, kprec, vrs[members[j0]], nj,
                                                 reinterpret_cast<const ResidentArgs *>(ws + o_res) + g0 + j0, st);
                     if (rc) return rc;
                 }
@@ -549,7 +559,7 @@ int swmd_serve_start(swmd_corpus *c, const swmd_serve_config *cfg_in, swmd_serve
         if (c->opt.path != SWMD_PATH_AUTO && p != c->opt.path) continue;
         if (c->opt.path == SWMD_PATH_AUTO && p == SWMD_PATH_PLAIN) continue;
         const Mapping mx = choose_mapping(c, c->opt.max_vr, p);
-        largest = std::max(largest, query_bytes(c, std::max(mx.vrp, vrp_for(c->opt.max_vr, 8)), p));
+        largest = std::max(largest, query_bytes(c, std::max(mx.vrp, max_vrp_of(c->opt.max_vr)), p));
     }
     if ((size_t)cfg.memory_budget < largest)
         return set_error(SWMD_ENOMEM, "swmd_serve_start: memory_budget %lld below one query of %d words (%zu bytes)",
@@ -575,7 +585,7 @@ int swmd_serve_start(swmd_corpus *c, const swmd_serve_config *cfg_in, swmd_serve
     if (e != cudaSuccess) return bail(cuda_fail(e, "swmd_serve_start: arena"));
     S->arena.init(S->arena_mem, (size_t)cfg.memory_budget);
     S->slots.resize((size_t)cfg.max_batch);
-    const int vrp = vrp_for(c->opt.max_vr, 8);
+    const int vrp = max_vrp_of(c->opt.max_vr);
     for (auto &sl : S->slots) {
         Slot &w = sl.ws;
         int64_t b = 0;
@@ -599,6 +609,10 @@ int swmd_serve_start(swmd_corpus *c, const swmd_serve_config *cfg_in, swmd_serve
         w.vrp_cap = vrp;
         w.kprec = c->opt.k_precision;
         w.external = true;
+    }
+    {
+        std::lock_guard<std::mutex> cl(c->mu);
+        ++c->servers;
     }
     S->worker = std::thread(worker_main, S);
     *out = S;
@@ -642,11 +656,17 @@ int swmd_serve_wait(swmd_server *S, uint64_t ticket, double *h_out_dist, int32_t
     if (it == S->table.end()) return set_error(SWMD_EINVAL, "swmd_serve_wait: unknown ticket %llu", (unsigned long long)ticket);
     auto R = it->second;
     auto ready = [&] { return R->state == 2; };
+    ++S->waiters;
+    bool ok = true;
     if (timeout_ms < 0) S->cv_done.wait(lk, ready);
-    else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+    else ok = S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+    --S->waiters;
+    S->cv_done.notify_all();   // a stopping server waits for the last waiter to leave
+    if (!ok)
         return set_error(SWMD_ETIMEDOUT, "swmd_serve_wait: ticket %llu not ready after %d ms",
                          (unsigned long long)ticket, timeout_ms);
-    S->table.erase(it);
+    auto again = S->table.find(ticket);   // another waiter of the same ticket may have taken it
+    if (again != S->table.end()) S->table.erase(again);
     if (!R->result.empty() && h_out_dist)
         std::memcpy(h_out_dist, R->result.data(), sizeof(double) * R->result.size());
     if (R->code) return set_error(R->code, "%s", R->err.c_str());
@@ -685,6 +705,16 @@ int swmd_serve_stop(swmd_server *S) {
         S->cv_work.notify_all();
     }
     if (S->worker.joinable()) S->worker.join();
+    {
+        // every pending request has failed with SWMD_ESTOPPED: let the threads blocked
+        // in swmd_serve_wait collect that before the server goes away
+        std::unique_lock<std::mutex> lk(S->m);
+        S->cv_done.wait(lk, [&] { return S->waiters == 0; });
+    }
+    {
+        std::lock_guard<std::mutex> cl(S->c->mu);
+        --S->c->servers;
+    }
     DeviceGuard guard(S->c->device);
     for (auto &sl : S->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);

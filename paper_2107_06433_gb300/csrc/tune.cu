@@ -69,6 +69,8 @@ int swmd_autotune(swmd_corpus *c, int32_t v_r, int32_t reps, swmd_tune_result *o
     if (c->Nl == 0) return SWMD_OK;
 
     std::lock_guard<std::mutex> lk(c->mu);
+    if (c->servers > 0)
+        return set_error(SWMD_EINVAL, "swmd_autotune: a server is attached to the corpus; tune before serving");
     DeviceGuard guard(c->device);
     Slot &s = c->main;
     cudaStream_t st = c->stream;
@@ -89,9 +91,9 @@ int swmd_autotune(swmd_corpus *c, int32_t v_r, int32_t reps, swmd_tune_result *o
     SWMD_CK(cudaMemcpyAsync(s.q_in, ids.data(), sizeof(int32_t) * v_r, cudaMemcpyHostToDevice, st));
     SWMD_CK(cudaMemcpyAsync(s.r_in, r.data(), sizeof(float) * v_r, cudaMemcpyHostToDevice, st));
 
-    const int vrp = layout_vrp(c, v_r, SWMD_PATH_RESIDENT);
     const int kprec = c->opt.k_precision;
-    const auto key = std::make_pair(vrp, kprec);
+    const auto key = std::make_pair(v_r, kprec);
+    const int tight = tight_vrp(v_r);   // the layout of the solvers other than the column-split one
 
     // time with every tunable field free and the resident path forced; the caller's
     // fields are put back after
@@ -117,15 +119,16 @@ int swmd_autotune(swmd_corpus *c, int32_t v_r, int32_t reps, swmd_tune_result *o
     float best_ms = timed(best);
     out->default_ms = best_ms;
     std::vector<std::tuple<int, int, int>> cands;
-    if (regs_rows_per_lane(vrp, 0) > 0)
+    if (c->col_tasks_dev) cands.emplace_back(kSolverCols, 0, 0);
+    if (regs_rows_per_lane(tight, 0) > 0)
         for (int npl : {1, 2, 3, 4, 8})
-            if (regs_rows_per_lane(vrp, npl) == npl) cands.emplace_back(1, npl, 0);
-    if (tiled_supported(vrp, kprec)) cands.emplace_back(2, 0, 0);
+            if (regs_rows_per_lane(tight, npl) == npl) cands.emplace_back(kSolverRegs, npl, 0);
+    if (tiled_supported(tight, kprec)) cands.emplace_back(kSolverTiled, 0, 0);
     for (auto &cfg : cands) {
         const float ms = timed(cfg);
         if (ms > 0.0f && (best_ms <= 0.0f || ms < best_ms)) best_ms = ms, best = cfg;
     }
-    if (vrp <= 32) {   // threads per word of the row-wise cost kernel
+    if (v_r <= 32) {   // threads per word of the row-wise cost kernel (layouts up to 32)
         for (int split : {1, 2, 4}) {
             auto cfg = std::make_tuple(std::get<0>(best), std::get<1>(best), split);
             const float ms = timed(cfg);
@@ -156,7 +159,7 @@ int swmd_autotune(swmd_corpus *c, int32_t v_r, int32_t reps, swmd_tune_result *o
 
     if (best_ms <= 0.0f && fused_ms <= 0.0f)
         return set_error(SWMD_ECUDA, "swmd_autotune: no configuration ran for v_r %d", v_r);
-    out->vrp = vrp;
+    out->vrp = layout_vrp(c, v_r, SWMD_PATH_RESIDENT);
     out->solver = std::get<0>(best);
     out->nnz_per_lane = std::get<1>(best);
     out->cost_split = std::get<2>(best);

@@ -390,18 +390,11 @@ __global__ void __launch_bounds__(kWalkThreads) k_resident(ResidentArgs ra) {
     X(96, 4, 4) X(96, 8, 4) X(112, 4, 4) X(128, 4, 4) X(128, 8, 4)
 
 template <class K>
-int walk_blocks(K kernel, int &per_sm_cache, long N, int G, int sms) {
-    if (per_sm_cache <= 0) {
-        int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWalkThreads, 0) !=
-                cudaSuccess || per_sm < 1) {
-            (void)cudaGetLastError();
-            per_sm = 1;
-        }
-        per_sm_cache = per_sm;
-    }
+int walk_blocks(K kernel, LaunchCache &cache, long N, int G, int sms) {
+    int per_sm = 1;
+    if (cache.blocks_per_sm(kernel, kWalkThreads, 0, -1, &per_sm) != cudaSuccess) per_sm = 1;
     const long need = (N * G + kWalkThreads - 1) / kWalkThreads;
-    const long cap = (long)sms * per_sm_cache;
+    const long cap = (long)sms * per_sm;
     const long b = need < cap ? need : cap;
     return (int)(b < 1 ? 1 : b);
 }
@@ -409,8 +402,8 @@ int walk_blocks(K kernel, int &per_sm_cache, long N, int G, int sms) {
 template <int VRP, int Q, int P, class KT_t, Kind KIND>
 cudaError_t run_walk(const IterArgs &a, int sms, cudaStream_t s) {
     auto kern = k_walk<VRP, Q, P, KT_t, KIND>;
-    static int per_sm = 0;
-    const int blocks = walk_blocks(kern, per_sm, a.N, P * Q, sms);
+    static LaunchCache cache;
+    const int blocks = walk_blocks(kern, cache, a.N, P * Q, sms);
     if (a.N > 0) kern<<<blocks, kWalkThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -440,8 +433,8 @@ cudaError_t dispatch_walk_prec(const IterArgs &a, Mapping m, int kprec, int sms,
 template <int VRP, int Q, int P, class KT_t>
 cudaError_t run_resident(const ResidentArgs &a, int sms, cudaStream_t s) {
     auto kern = k_resident<VRP, Q, P, KT_t>;
-    static int per_sm = 0;
-    const int blocks = walk_blocks(kern, per_sm, a.it.N, P * Q, sms);
+    static LaunchCache cache;
+    const int blocks = walk_blocks(kern, cache, a.it.N, P * Q, sms);
     if (a.it.N > 0) kern<<<blocks, kWalkThreads, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -462,16 +462,11 @@ __global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
 template <int VRP, class KT_t, Kind KIND, int NT, int MINB>
 cudaError_t run_walk3_v(const IterArgs &a, int sms, cudaStream_t s) {
     auto kern = k_walk3<VRP, KT_t, KIND, NT, MINB>;
-    static int per_sm = 0;
-    if (per_sm <= 0) {
-        // no shared memory: all of the SM's L1 for the gathered K^T rows
-        (void)cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, 0) != cudaSuccess ||
-            per_sm < 1) {
-            (void)cudaGetLastError();
-            per_sm = 1;
-        }
-    }
+    static LaunchCache cache;
+    int per_sm = 1;
+    // no shared memory: all of the SM's L1 for the gathered K^T rows (carveout 0)
+    cudaError_t e = cache.blocks_per_sm(kern, NT, 0, 0, &per_sm);
+    if (e != cudaSuccess) return e;
     constexpr int Q = W3<VRP, KT_t>::Q;
     const long groups = (long)a.n_slices * Q;
     const long need = (groups * 32 + NT - 1) / NT;

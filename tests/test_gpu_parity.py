@@ -366,7 +366,8 @@ def wide():
 
 def test_automatic_path_by_query_width(wide):
     E, C = wide
-    corpus = swmd.corpus_from_synth(E, C)
+    # the row-per-lane register solver: the automatic path then depends on the width
+    corpus = swmd.corpus_from_synth(E, C, solver=1)
     assert swmd.swmd_resolve_path(corpus, 8) == "resident"
     assert swmd.swmd_resolve_path(corpus, 64) == "fused"
     qs = [synth.query(np.random.default_rng(k), C.V, vr) for k, vr in enumerate((8, 64, 20, 40))]
@@ -387,7 +388,7 @@ def test_automatic_path_by_query_width(wide):
 
 def test_autotune_records_the_path(wide):
     E, C = wide
-    corpus = swmd.corpus_from_synth(E, C)
+    corpus = swmd.corpus_from_synth(E, C, solver=1)
     res = swmd.swmd_autotune(corpus, 48, 2)
     assert res["path"] in (swmd.PATH_RESIDENT, swmd.PATH_FUSED)
     assert swmd.swmd_resolve_path(corpus, 48) == {swmd.PATH_RESIDENT: "resident",
