@@ -143,6 +143,10 @@ def test_convergence_mode_matches_the_converged_oracle(paper):
     ref, ref_its = oracle.wmd_pairs(E, [(qi, qw)] * len(docs), docs, 1.0, 100000, tol=1e-12,
                                     want_iters=True)
     assert np.all(its < 2000) and np.all(its >= 1)
+    # each pair's distance is the one of exactly the x-updates it applied (FP32 bound)
+    for p, x in enumerate(docs):
+        exact = oracle.wmd_pairs(E, [(qi, qw)], [x], 1.0, int(its[p]))
+        assert rel_err(got[p:p + 1], exact) <= 1e-5, (p, int(its[p]))
     assert rel_err(got, ref) <= 1e-4
     # the rule stops where the oracle's does at the same tolerance, give or take rounding
     _, o_its = oracle.wmd_pairs(E, [(qi, qw)] * len(docs), docs, 1.0, 100000, tol=1e-6,

@@ -51,6 +51,27 @@ def test_stated_bounds_paper_shaped(paper, kprec, path, lam):
     assert err <= BOUND[kprec]
 
 
+@pytest.fixture(scope="module")
+def tiny():
+    E, C, (qi, qw) = synth.make("tiny")
+    rp, col, val = C.csr()
+    refs = {lam: oracle.wmd(E, rp, col, val, C.N, qi, qw, lam, 15) for lam in (1.0, 10.0)}
+    return E, C, qi, qw, refs
+
+
+@pytest.mark.parametrize("kprec", ["bf16", "fp16"])
+@pytest.mark.parametrize("path", ["resident", "fused", "plain"])
+@pytest.mark.parametrize("lam", [1.0, 10.0])
+def test_stated_bounds_tiny(tiny, kprec, path, lam):
+    """The 200-document workload (V = 2,000, d = 64, v_r = 8): the BF16 and FP16
+    bounds hold there too, on every path."""
+    E, C, qi, qw, refs = tiny
+    corpus = swmd.corpus_from_synth(E, C, path=path, k_precision=kprec)
+    err = rel_err(swmd.swmd_query(corpus, qi, qw, lam, 15), refs[lam])
+    print(f"tiny {kprec} {path} lambda={lam}: max relative error {err:.3e}")
+    assert err <= BOUND[kprec]
+
+
 def test_error_table_large_corpus_sampled():
     """1M documents (17.5M nonzeros), v_r = 32: every precision and lambda against
     the oracle on 200 sampled documents (each document is an independent problem, so

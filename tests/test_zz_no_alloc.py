@@ -62,3 +62,24 @@ def test_noalloc_refuses_a_query_larger_than_its_array(setup):
     with pytest.raises(swmd.SwmdError) as e:
         swmd.swmd_query_noalloc(corpus, d_ids, d_r, vr, 1.0, 15, out)
     assert e.value.code == swmd.SWMD_EINVAL and "scratch" in str(e.value)
+
+
+def test_noalloc_allocates_nothing(setup):
+    """The property the entry point exists for: after a first call on the device,
+    further calls leave the device's free memory and PyTorch's allocator counters
+    exactly where they were."""
+    torch, E, C, corpus = setup
+    qi, qw = synth.query(np.random.default_rng(3), C.V, 19)
+    d_ids, d_r, vr = _device_query(torch, C, qi, qw)
+    out = torch.empty(C.N, dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    swmd.swmd_query_noalloc(corpus, d_ids, d_r, vr, 1.0, 15, out, st)   # first call on the device
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    alloc0, reserved0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
+    for lam in (0.5, 1.0, 2.0, 4.0, 8.0):
+        swmd.swmd_query_noalloc(corpus, d_ids, d_r, vr, lam, 15, out, st)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0 and torch.cuda.memory_reserved() == reserved0
+    assert int(st.item()) == 0 and np.all(np.isfinite(out.cpu().numpy()))
