@@ -1,25 +1,23 @@
-"""Benchmark: Sinkhorn WMD of one query against a paper-shaped corpus on GB300.
+"""Benchmark: Sinkhorn WMD of one query against a corpus on GB300.
 
 One step = one whole query through the hot path (query staging, cost/kernel
 matrix, all Sinkhorn iterations and the final distances) over the resident corpus
-of the paper-shaped workload (V=100,000, d=300, 5,000 documents of 10-300 Zipf
-words, v_r=19, lambda=1, 15 iterations).  Inputs are synthetic (synth.py).
+of the 1,000,000-document workload (V=500,000, d=300, documents of 5-30 Zipf words,
+17.5M nonzeros, v_r=32, lambda=1, 15 iterations, FP32).  Inputs are synthetic
+(synth.py).
 
   value      WMD/s (documents x queries / device time), inputs resident in HBM,
-             L2 flushed (1 GiB write) before every timed step, outside the events; the
-             flush also keeps the GPU busy long enough that the host's launches of the
-             step are queued before the step starts (no host gap inside the events).
+             L2 flushed (1 GiB write) before every timed step, outside the events.
   e2e        WMD/s through swmd_query with host buffers: the query's ids and
              weights go host->device and the N distances device->host every step.
   roofline   the dominant kernel of a step: algorithmic bytes or flops per launch
              over its CUDA-event duration, against MEASURED_PEAKS.json; `traffic`
              from the committed ncu capture when it matches the current sources.
-  paths      the same query on the resident, fused (one launch per iteration) and
-             plain (separate SDDMM and SpMM launches) paths, and the per-iteration
-             fused vs plain kernels.
-  hbm_regime the per-iteration fused and plain kernels on the 1,000,000-document
-             workload (17.5M nonzeros, v_r=32), where c and u exceed L2, with FP32
-             and BF16 K: effective GB/s against the HBM peak; whole queries per path.
+  fused_iteration  the per-iteration fused SDDMM-SpMM and the plain SDDMM + SpMM
+             kernels on the same workload (FP32 and BF16 K): effective GB/s against
+             the HBM peak, and whole queries on each path (`hbm_regime`).
+  paper_shaped the 5,000-document paper-shaped workload (V=100,000, 10-300 words,
+             v_r=19): the whole query, its paths and the 1-to-1 pairs of Table II.
   batched    256 queries (v_r uniform in [4,64]) over 100,000 documents of 10-200
              words in one swmd_query_batch call after autotuning, FP32 and BF16 K,
              against the same queries one at a time.
@@ -27,15 +25,14 @@ words, v_r=19, lambda=1, 15 iterations).  Inputs are synthetic (synth.py).
              fed by Poisson arrivals at 50, 200 and 1000 queries/s (v_r uniform in
              [4,128]): queries/s and p50/p99 latency, against the same queries run
              one at a time through swmd_query with FP32 K, and the BF16 error.
-  one_to_one the 1-to-1 pairs of Table II: the query against every document as
-             independent pairs, and a 100-candidate re-ranking set, beside the 1-to-N query.
-  cpu_baseline  the FP64 oracle timed on the host cores on a bounded sample, and on
-             one host thread (`single_core`); the dense oracle on the 200-document
-             workload and on 64 documents of the paper-shaped one (`dense`).
+  cpu_baseline  the FP64 oracle timed on the host cores on whole queries of the
+             workload, and on one host thread on a document sample (`single_core`);
+             the dense oracle on the 200-document workload and on 64 documents of the
+             paper-shaped one (`dense`).
 
 `--impl reference` times the oracle alone (the reference arm).  Under torchrun
-(N > 1) every rank holds its own 5,000-document partition (weak scaling, no
-collective on the data path) and rank 0 prints the line.
+(N > 1) every rank holds its own partition of the workload's size (weak scaling,
+no collective on the data path) and rank 0 prints the line.
 """
 from __future__ import annotations
 
@@ -54,12 +51,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "paper"
+WORKLOAD = "large"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA), times the SM clock.
-SMS, FP32_LANES = 152, 128
+# FP32 CUDA-core peak: the device's SMs x 128 FP32 lanes x 2 flop (FMA), times the SM clock.
+FP32_LANES = 128
 
 
 def parse():
@@ -69,11 +66,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--path", default="resident", choices=["resident", "fused", "plain", "auto"])
+    ap.add_argument("--path", default="auto", choices=["resident", "fused", "plain", "auto"])
     ap.add_argument("--kprec", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-paths", action="store_true")
-    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the per-iteration kernel section")
+    ap.add_argument("--no-paper", action="store_true", help="skip the paper-shaped section")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-pairs", action="store_true")
@@ -97,7 +95,8 @@ def load_peaks():
 
 # the kernel sources each measured traffic figure depends on
 KERNEL_SOURCES = {
-    "resident": ["common.cuh", "resident_regs.cu", "resident_tiled.cu", "walk.cuh", "walk_resident.cu"],
+    "resident": ["common.cuh", "resident_cols.cu", "resident_regs.cuh", "resident_tiled.cu", "walk.cuh",
+                 "walk3.cuh", "walk_resident.cu"],
     "cost": ["common.cuh", "cost.cu"],
     "fused": ["common.cuh", "walk.cuh", "walk3.cuh", "walk_fused.cu"],
     "plain": ["common.cuh", "walk.cuh", "walk3.cuh", "walk_plain.cu"],
@@ -229,17 +228,11 @@ def time_oracle(E, C, qi, qw, lam, t, budget_s=12.0, max_runs=50):
     return runs, el, oracle.get_threads()
 
 
-def time_oracle_one_core(E, C, qi, qw, lam, t, budget_s=6.0, max_runs=10):
-    """The same oracle on one host thread (restored afterwards)."""
-    import oracle
-    n0 = oracle.get_threads()
-    try:
-        oracle.set_threads(1)
-        runs, el, cores = time_oracle(E, C, qi, qw, lam, t, budget_s, max_runs)
-    finally:
-        oracle.set_threads(n0)
-    return {"value": C.N * runs / el, "unit": "WMD/s", "cores": cores,
-            "sample": f"{runs} whole queries, one thread"}
+def time_oracle_one_core(E, C, qi, qw, lam, t, n=20000, budget_s=6.0, max_runs=10):
+    """The same oracle on one host thread, on the first n documents (document_sample)."""
+    n, runs, el, cores = time_oracle_sample(E, C, qi, qw, lam, t, n, budget_s, max_runs, threads=1)
+    return {"value": n * runs / el, "unit": "WMD/s", "cores": cores,
+            "sample": f"{runs} queries against the first {n} documents, one thread, sparse FP64 mode"}
 
 
 def first_documents_csr(C, n):
@@ -251,6 +244,48 @@ def first_documents_csr(C, n):
     rp = np.zeros(C.V + 1, np.int64)
     np.cumsum(np.bincount(words, minlength=C.V), out=rp[1:])
     return rp, docs[order], np.asarray(C.vals[:end], np.float32)[order]
+
+
+def document_sample(E, C, qi, n):
+    """The first n documents as an oracle input over the words they and the query use:
+    (E rows of those words, V' x n CSR, query ids remapped).  Every document is an
+    independent problem in Algorithm 1 and a word no document holds adds nothing, so
+    the oracle gives these documents the same distances on the smaller vocabulary."""
+    n = min(n, C.N)
+    end = int(C.doc_ptr[n])
+    words = np.asarray(C.word_ids[:end], np.int64)
+    used = np.unique(np.concatenate([words, np.asarray(qi, np.int64)]))
+    remap = np.full(C.V, -1, np.int64)
+    remap[used] = np.arange(len(used))
+    w2 = remap[words]
+    docs = np.repeat(np.arange(n, dtype=np.int32), np.diff(np.asarray(C.doc_ptr[:n + 1])))
+    order = np.lexsort((docs, w2))
+    rp = np.zeros(len(used) + 1, np.int64)
+    np.cumsum(np.bincount(w2, minlength=len(used)), out=rp[1:])
+    return (np.ascontiguousarray(E[used]), rp, docs[order], np.asarray(C.vals[:end], np.float32)[order],
+            remap[np.asarray(qi, np.int64)].astype(np.int32), n)
+
+
+def time_oracle_sample(E, C, qi, qw, lam, t, n, budget_s, max_runs, threads=None):
+    """The sparse oracle on the first n documents (document_sample), repeated until
+    budget_s has passed; threads: host threads (None = all)."""
+    import oracle
+    Es, rp, col, val, qs, n = document_sample(E, C, qi, n)
+    n0 = oracle.get_threads()
+    try:
+        if threads:
+            oracle.set_threads(threads)
+        runs, t0 = 0, time.perf_counter()
+        while True:
+            oracle.wmd(Es, rp, col, val, n, qs, qw, lam, t, "sparse")
+            runs += 1
+            el = time.perf_counter() - t0
+            if el >= budget_s or runs >= max_runs:
+                break
+        cores = oracle.get_threads()
+    finally:
+        oracle.set_threads(n0)
+    return n, runs, el, cores
 
 
 def time_oracle_dense(synth, budget_s=4.0):
@@ -286,11 +321,10 @@ def config_dict(w, C):
 
 
 def reference_arm(args, budget_s=240.0):
-    """The oracle as the reference arm: exactly --steps steps, each one whole query
-    against a sample of the workload's documents: all of them when the steps fit the
-    time budget, else the first n, sized from a warm-up query.  (The oracle's cost
-    matrix spans the whole vocabulary whatever the sample, so a smaller sample lowers
-    its WMD/s.)"""
+    """The oracle as the reference arm: exactly --steps steps, each one query against a
+    sample of the workload's documents: all of them when the steps fit the time budget,
+    else the first n (document_sample: their words only), n sized from a warm-up query
+    on a sample."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
@@ -298,29 +332,31 @@ def reference_arm(args, budget_s=240.0):
     import oracle
     w = synth.WORKLOADS[args.workload]
     E, C, (qi, qw) = synth.make(w)
-    rp, col, val = C.csr()
     oracle.build()
     steps = max(int(args.steps), 1)
-    t0 = time.perf_counter()
-    oracle.wmd(E, rp, col, val, C.N, qi, qw, w.lam, w.max_iter)
-    t_query = time.perf_counter() - t0
-    n_docs = C.N
-    if steps * t_query > budget_s:
-        n_docs = max(16, min(C.N, int(C.N * budget_s / (steps * t_query))))
-    if n_docs < C.N:
-        rp, col, val = first_documents_csr(C, n_docs)
+    n0 = min(C.N, 20000)
+    n0, runs, el, _ = time_oracle_sample(E, C, qi, qw, w.lam, w.max_iter, n0, 0.0, 1)
+    per_doc = el / n0
+    n_docs = max(16, min(C.N, int(budget_s / (steps * per_doc))))
+    if n_docs >= C.N:
+        n_docs = C.N
+        rp, col, val = C.csr()
+        Es, qs = E, qi
+    else:
+        Es, rp, col, val, qs, n_docs = document_sample(E, C, qi, n_docs)
     for _ in range(max(args.warmup - 1, 0)):
-        oracle.wmd(E, rp, col, val, n_docs, qi, qw, w.lam, w.max_iter)
+        oracle.wmd(Es, rp, col, val, n_docs, qs, qw, w.lam, w.max_iter)
     times = []
     for _ in range(steps):
         t0 = time.perf_counter()
-        oracle.wmd(E, rp, col, val, n_docs, qi, qw, w.lam, w.max_iter)
+        oracle.wmd(Es, rp, col, val, n_docs, qs, qw, w.lam, w.max_iter)
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = n_docs * steps / total
     cores = oracle.get_threads()
-    sample = (f"{steps} whole queries of the {w.name} workload against "
-              f"{'all ' if n_docs == C.N else 'its first '}{n_docs} documents, sparse FP64 mode")
+    sample = (f"{steps} queries of the {w.name} workload against "
+              f"{'all ' if n_docs == C.N else 'its first '}{n_docs} documents"
+              f"{'' if n_docs == C.N else ' (cost matrix over their words)'}, sparse FP64 mode")
     line = {
         "impl": "reference", "metric": "WMDs/s", "value": value, "unit": "WMD/s",
         "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
@@ -365,7 +401,7 @@ def compare_paths(swmd, corpus, d_ids, d_r, d_out, d_status, flush, stream, vr, 
         res[path] = {"ms_per_query": ms, "wmds_per_s": C.N / (ms * 1e-3)}
     res["iteration_kernel"] = iteration_kernels(swmd, corpus, d_ids, d_r, d_status, flush, stream,
                                                 vr, lam, info, C, peaks, kb)
-    swmd.swmd_corpus_set_options(corpus, path="resident")
+    swmd.swmd_corpus_set_options(corpus, path="auto")
     return res
 
 
@@ -476,14 +512,10 @@ def one_to_one(swmd, torch, corpus, C, qi, qw, lam, t, flush, stream, d, alu_pea
     return res
 
 
-def hbm_regime(swmd, synth, torch, flush, stream, peaks):
-    """The per-iteration kernels where c and u exceed L2 (1M documents), in FP32
-    and BF16 K, and whole queries on each path."""
-    w = synth.WORKLOADS["large"]
-    E, C, (qi, qw) = synth.make(w)
-    corpus = swmd.corpus_from_synth(E, C, path="fused")
+def hbm_regime(swmd, torch, corpus, C, ids, r, w, flush, stream, peaks):
+    """The per-iteration fused and plain kernels where c and u exceed L2 (the
+    headline corpus), in FP32 and BF16 K, and whole queries on each path."""
     info = corpus.info()
-    ids, r = swmd.swmd_select(C.V, qi, qw)
     d_ids = torch.from_numpy(ids).cuda()
     d_r = torch.from_numpy(r).cuda()
     d_status = torch.zeros(1, dtype=torch.int32, device="cuda")
@@ -491,19 +523,54 @@ def hbm_regime(swmd, synth, torch, flush, stream, peaks):
     for kp, kb in (("fp32", 4), ("bf16", 2)):
         swmd.swmd_corpus_set_options(corpus, k_precision=kp)
         per[kp] = iteration_kernels(swmd, corpus, d_ids, d_r, d_status, flush, stream, len(ids),
-                                    w.lam, info, C, peaks, kb, reps=10, traffic_key=f"large:{kp}")
+                                    w.lam, info, C, peaks, kb, reps=10, traffic_key=f"{w.name}:{kp}")
     d_out = torch.empty(C.N, dtype=torch.float64, device="cuda")
     q = {}
-    for path, kp in (("resident", "fp32"), ("fused", "fp32"), ("auto", "fp32"), ("fused", "bf16"),
-                     ("auto", "bf16")):
+    for path, kp in (("resident", "fp32"), ("fused", "fp32"), ("plain", "fp32"), ("resident", "bf16"),
+                     ("fused", "bf16")):
         swmd.swmd_corpus_set_options(corpus, path=path, k_precision=kp)
         ms = time_query_device(swmd, torch, corpus, stream, flush, ids, r, w.lam, w.max_iter,
                                d_out, d_status)
-        q[f"{path}/{kp}"] = {"ms_per_query": ms, "wmds_per_s": C.N / (ms * 1e-3),
-                             "path_taken": swmd.swmd_resolve_path(corpus, len(ids))}
-    corpus.close()
-    return {"workload": "large", "documents": C.N, "nnz": info.nnz, "v_r": len(ids),
+        q[f"{path}/{kp}"] = {"ms_per_query": ms, "wmds_per_s": C.N / (ms * 1e-3)}
+    swmd.swmd_corpus_set_options(corpus, path="auto", k_precision="fp32")
+    q["resident_over_fused_fp32"] = q["fused/fp32"]["ms_per_query"] / q["resident/fp32"]["ms_per_query"]
+    return {"workload": w.name, "documents": C.N, "nnz": info.nnz, "v_r": len(ids),
             "l2": "flushed before every timed launch", "iteration_kernel": per, "query": q}
+
+
+def paper_shaped(swmd, synth, torch, flush, stream, peaks, alu_peak, rank):
+    """The paper-shaped workload (Section III-B2 statistics: V = 100,000, d = 300, 5,000
+    documents, v_r = 19): the whole query (automatic path), each path, the fused vs plain
+    iteration kernels and the 1-to-1 pairs of Table II."""
+    w = synth.WORKLOADS["paper"]
+    E, C, (qi, qw) = synth.make(w)
+    corpus = swmd.corpus_from_synth(E, C)
+    info = corpus.info()
+    ids, r = swmd.swmd_select(C.V, qi, qw)
+    vr = len(ids)
+    d_ids = torch.from_numpy(ids).cuda()
+    d_r = torch.from_numpy(r).cuda()
+    d_out = torch.empty(C.N, dtype=torch.float64, device="cuda")
+    d_status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ms = time_query_device(swmd, torch, corpus, stream, flush, ids, r, w.lam, w.max_iter, d_out,
+                           d_status, reps=50)
+    out_dev = d_out.cpu().numpy()
+    host = np.empty(C.N, np.float64)
+    for _ in range(3):
+        swmd.swmd_query(corpus, qi, qw, w.lam, w.max_iter, out=host)
+    reps, t0 = 200, time.perf_counter()
+    for _ in range(reps):
+        swmd.swmd_query(corpus, qi, qw, w.lam, w.max_iter, out=host)
+    e2e = C.N * reps / (time.perf_counter() - t0)
+    res = {"workload": w.name, "documents": C.N, "nnz": info.nnz, "v_r": vr,
+           "path": swmd.swmd_resolve_path(corpus, vr), "ms_per_query": ms,
+           "wmds_per_s": C.N / (ms * 1e-3), "e2e_wmds_per_s": e2e}
+    res["paths"] = compare_paths(swmd, corpus, d_ids, d_r, d_out, d_status, flush, stream, vr, w.lam,
+                                 w.max_iter, info, C, peaks, 4)
+    res["one_to_one"] = one_to_one(swmd, torch, corpus, C, qi, qw, w.lam, w.max_iter, flush, stream,
+                                   w.d, alu_peak, ms, out_dev)
+    corpus.close()
+    return res
 
 
 def batched(swmd, synth, torch):
@@ -550,12 +617,13 @@ def batched(swmd, synth, torch):
     return res
 
 
-def serving(swmd, synth, torch, rates=(50.0, 200.0, 1000.0), n=200):
+def serving(swmd, synth, torch, rates=(50.0, 200.0, 1000.0), n=200, E=None, C=None):
     """Poisson arrivals (v_r uniform in [4, 128]) into a server over the resident
     1,000,000-document corpus with BF16 K, against the same queries one at a time
-    through swmd_query with FP32 K."""
+    through swmd_query with FP32 K.  E, C: that workload's arrays if already made."""
     w = synth.WORKLOADS["large"]
-    E, C, _ = synth.make(w)
+    if E is None or C is None or C.N != w.N:
+        E, C, _ = synth.make(w)
     qs = synth.batch_queries(C.V, n, 4, 128, seed=synth.SEED + 1)
     res = {"workload": "large", "documents": C.N, "queries_per_rate": n, "v_r": "uniform 4-128",
            "lambda": 1.0, "max_iter": 15}
@@ -607,6 +675,7 @@ def main():
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     pg = None
     if world > 1:
         import torch.distributed as dist
@@ -682,7 +751,7 @@ def main():
     out_dev = d_out.cpu().numpy()
 
     # ---- e2e through the host API (host ids/weights in, host distances out)
-    e2e_steps = min(K, 500)
+    e2e_steps = min(K, 200)
     host_out = np.empty(C.N, np.float64)
     for _ in range(3):
         swmd.swmd_query(corpus, qi, qw, lam, t, out=host_out)
@@ -714,7 +783,7 @@ def main():
         sb = t * fused_iter_bytes(info.nnz, C.N, info.V_used, vrp, kb)
         sf = float(t + 1) * info.nnz * (4 * vr + 1)
         skey = f"{run_path}:{w.name}:{args.kprec}"
-    alu_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s at the sampled clock
+    alu_peak = sms * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s at the sampled clock
     if solve_avg >= cost_avg:
         name, key, dur, byts, flops = f"{run_path} solver (a3 x t + a4)", skey, solve_avg, sb, sf
     else:
@@ -725,7 +794,7 @@ def main():
         ach = flops / dur / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": ach / alu_peak, "traffic": traffic, "kernel": name,
-                "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x "
+                "peak_source": f"derived: {sms} SMs x {FP32_LANES} FP32 lanes x 2 flop x "
                                f"{sm_mhz:.0f} MHz (median sampled SM clock)",
                 "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": byts}
     else:
@@ -734,6 +803,11 @@ def main():
                 "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "kernel": name,
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes_per_launch": byts, "algorithmic_flops_per_launch": flops}
+
+    # ---- the per-iteration fused vs plain kernels on this workload (metric's HBM GB/s)
+    hbm = None
+    if rank == 0 and not args.no_large:
+        hbm = hbm_regime(swmd, torch, corpus, C, ids, r, w, flush, stream, peaks)
 
     line = {
         "metric": "WMDs/s", "value": C.N * world * K / (total_ms * 1e-3), "unit": "WMD/s",
@@ -745,27 +819,34 @@ def main():
         "e2e": {"value": C.N * world * e2e_steps / e2e_s, "unit": "WMD/s",
                 "h2d_bytes_per_step": int(len(qi) * 8), "d2h_bytes_per_step": int(C.N * 8 + 4)},
         "roofline": roof,
+    }
+    if hbm:
+        it = hbm["iteration_kernel"]
+        line["fused_iteration"] = {
+            kp: {"fused_us": 1e3 * it[kp]["fused"]["ms_per_iteration"], "fused_gbs": it[kp]["fused"]["gbs"],
+                 "fused_frac_of_hbm": it[kp]["fused"]["frac_of_hbm"],
+                 "plain_us": 1e3 * it[kp]["plain"]["ms_per_iteration"],
+                 "fusion_speedup": it[kp]["fusion_speedup"]} for kp in ("fp32", "bf16")}
+        line["fused_iteration"]["whole_query_ms"] = {k: v["ms_per_query"] for k, v in hbm["query"].items()
+                                                     if isinstance(v, dict)}
+    line |= {
         "kernels_ms": {"cost": statistics.mean(cost_ms), "solver": statistics.mean(solve_ms)},
         "gpu_launches": K * (3 if run_path == "resident" else
                              (2 + t * (2 if run_path == "plain" else 1) + 1)),
-        "clocks": clocks, "status": st,
+        "sms": sms, "clocks": clocks, "status": st,
     }
-    if rank == 0 and not args.no_paths:
-        line["paths"] = compare_paths(swmd, corpus, d_ids, d_r, d_out, d_status, flush, stream,
-                                      vr, lam, t, info, C, peaks, kb)
-    if rank == 0 and not args.no_pairs:
-        line["one_to_one"] = one_to_one(swmd, torch, corpus, C, qi, qw, lam, t, flush, stream, w.d,
-                                        alu_peak, total_ms / K, out_dev)
+    if hbm:
+        line["hbm_regime"] = hbm
     if rank == 0:
         corpus.close()
-    if rank == 0 and not args.no_large:
-        line["hbm_regime"] = hbm_regime(swmd, synth, torch, flush, stream, peaks)
+    if rank == 0 and not args.no_paper:
+        line["paper_shaped"] = paper_shaped(swmd, synth, torch, flush, stream, peaks, alu_peak, rank)
     if rank == 0 and not args.no_batch:
         line["batched"] = batched(swmd, synth, torch)
     if rank == 0 and not args.no_serve:
-        line["serving"] = serving(swmd, synth, torch)
+        line["serving"] = serving(swmd, synth, torch, E=E, C=C)
     if rank == 0 and not args.no_cpu_baseline:
-        runs, el, cores = time_oracle(E, C, qi, qw, lam, t)
+        runs, el, cores = time_oracle(E, C, qi, qw, lam, t, budget_s=12.0, max_runs=3)
         line["cpu_baseline"] = {"value": C.N * runs / el, "unit": "WMD/s", "cores": cores,
                                 "kind": "oracle",
                                 "sample": f"{runs} whole queries of the {w.name} workload "
