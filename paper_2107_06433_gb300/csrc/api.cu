@@ -277,7 +277,7 @@ int build_tasks(swmd_corpus *c) {
         int d = 0;
         while (d < c->Nl) {
             const int b = cols_bucket(c->len_sorted[d], vrp);
-            const int per_warp = 32 / cols_team(b, vrp);
+            const int per_warp = cols_docs_per_task(b, vrp);
             int k = 0;
             while (d + k < c->Nl && k < per_warp && cols_bucket(c->len_sorted[d + k], vrp) == b) ++k;
             cols.push_back(make_int4(d, k, b, 0));

@@ -319,17 +319,28 @@ constexpr int kColMaxLen = 32;
 // Rows a document of `len` words occupies in the column-split solver for layout
 // `vrp` (the bucket: 8, 16, 24 or 32, a multiple of vrp / 4); 0 if too long.
 int cols_bucket(int len, int vrp);
-// A bucket of lmax rows is held by G row groups of Q = vrp / 4 lanes, each group
-// RL = lmax / G rows (a multiple of Q, at most 24, or 32 when Q = 32): documents
-// of 25..32 words use two groups of 16 rows.  cols_fits: the bucket exists for vrp.
+constexpr int kColMaxRowsPerLane = 12;   // rows a lane holds with eight columns
+// Columns of every row a lane holds (P) and lanes of a row group (Q = vrp / P):
+// eight columns per lane, four for 128-column layouts.
+__host__ __device__ constexpr int cols_p(int vrp) { return vrp >= 128 ? 4 : 8; }
+__host__ __device__ constexpr int cols_q(int vrp) { return vrp / cols_p(vrp); }
+// A bucket of lmax rows is held by G row groups of Q lanes, each group RL = lmax / G
+// rows: the smallest power of two G with RL a multiple of Q and at most 12 (at most
+// 32 with four columns per lane), G Q <= 32 lanes; 0 when there is none (the bucket
+// does not exist for that layout).
 __host__ __device__ constexpr int cols_groups(int lmax, int vrp) {
-    return vrp / 4 >= 32 ? 1 : (lmax <= 24 ? 1 : 2);
+    for (int g = 1; g <= 8; g *= 2) {
+        const int rl = lmax / g, q = cols_q(vrp);
+        if (lmax % g == 0 && rl % q == 0 && rl <= (cols_p(vrp) == 8 ? kColMaxRowsPerLane : 32) && g * q <= 32)
+            return g;
+    }
+    return 0;
 }
-__host__ __device__ constexpr bool cols_fits(int lmax, int vrp) {
-    return (lmax / cols_groups(lmax, vrp)) % (vrp / 4) == 0;
-}
+__host__ __device__ constexpr bool cols_fits(int lmax, int vrp) { return cols_groups(lmax, vrp) > 0; }
 // Lanes that own one document of a bucket (G Q).
-__host__ __device__ constexpr int cols_team(int lmax, int vrp) { return cols_groups(lmax, vrp) * (vrp / 4); }
+__host__ __device__ constexpr int cols_team(int lmax, int vrp) { return cols_groups(lmax, vrp) * cols_q(vrp); }
+// Documents of a bucket one warp task holds (32 / cols_team).
+int cols_docs_per_task(int lmax, int vrp);
 bool cols_supported(int vrp);
 // The layout (VRP) the column-split solver uses for a query of vr words: the
 // power of two >= max(vr, 16).

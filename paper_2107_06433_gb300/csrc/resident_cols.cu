@@ -8,9 +8,10 @@
 // WMD_j = sum_w c_wj (KM^T[w] . u_j) / (K^T[w] . u_j) (type 2).  A_j does not
 // change between iterations, so it is gathered once and kept in registers.
 //
-// Lanes.  A team of Q = VRP / 4 lanes owns a document; lane q holds columns
-// [4q, 4q + 4) of every row of A_j (LMAX rows, the document's length rounded up
-// to its bucket, zero rows past the end), of u_j and of acc.  acc = A_j^T tau then
+// Lanes.  A row group of Q = VRP / P lanes (P = 8 columns per lane, 4 for
+// 128-column layouts) holds rows of A_j: lane q holds columns [P q, P q + P) of
+// every row of the group (LMAX rows in all, the document's length rounded up to
+// its bucket; rows past the end are masked), of u_j and of acc.  acc = A_j^T tau then
 // needs no exchange.  The dots s = A_j u_j are partial over the lane's columns and
 // are finished by a reduce-scatter over the team: after it lane q holds the full
 // dots of rows [qR, qR + R), R = LMAX / Q, computes their tau, and an all-gather
@@ -22,8 +23,10 @@
 // coalesced 16-byte slice per lane of each row) and put into that order once, by
 // log2(Q) passes of conditional swaps.
 //
-// Register row i is paired with register row i + LMAX/2 as a float2, so the dots
-// of two rows and the contributions of two rows to acc are one packed f32x2 FMA.
+// A document of up to 12 rows per lane (32 with P = 4) is one row group; longer
+// ones are G row groups (the team), whose partial acc are summed with shuffles.
+// Packed f32x2 FMAs work on column pairs of a row: a row's dot is P / 2 of them
+// plus one add, its contribution to acc another P / 2.
 //
 // A document's arithmetic depends on its own nonzeros and on its bucket (a
 // function of its length) only, so it gives the same bits alone, batched, served
@@ -34,7 +37,6 @@ namespace swmd {
 namespace {
 
 constexpr int kColThreads = 128;
-constexpr int kColP = 4;   // K^T columns per lane
 
 // Four K^T values [4 idx4, 4 idx4 + 4) of the word-major layout, widened to float.
 __device__ __forceinline__ float4 load_slice(const void *base, int kprec, long idx4) {
@@ -50,45 +52,64 @@ __device__ __forceinline__ float4 load_slice(const void *base, int kprec, long i
     return make_float4(fa.x, fa.y, fb.x, fb.y);
 }
 
-// Row slices [4 idx4, 4 idx4 + 4) of the word-major layout for every register row
-// i of the lane (rows past the document's end read word 0: finite values whose
-// tau is masked to 0), widened to float.  One unrolled loop per storage type, so
-// all RL loads of a lane are in flight together.
-template <int VRP, int RL>
-__device__ __forceinline__ void gather_rows(float4 (&rv)[RL], const void *base, int kprec, const int (&wv)[RL],
-                                            int ql) {
-    constexpr long S4 = VRP / 4;
-    if (kprec == 0) {
-        const float4 *b = reinterpret_cast<const float4 *>(base) + ql;
-#pragma unroll
-        for (int i = 0; i < RL; ++i) rv[i] = __ldg(b + (long)wv[i] * S4);
+// The 32-bit words of a stored 16-bit pair, widened (x: the lower element).
+__device__ __forceinline__ float2 widen2(uint32_t w, int kprec) {
+    if (kprec == 1) return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    __half2 h;
+    memcpy(&h, &w, sizeof h);
+    return __half22float2(h);
+}
+
+// P consecutive 32-bit words (P = 4 or 8) of the read-only path, one vector load.
+template <int P>
+__device__ __forceinline__ void ldg_words(const void *p, uint32_t (&w)[P]) {
+    if constexpr (P == 8) {
+        asm("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+            : "l"(p));
+    } else if constexpr (P == 4) {
+        asm("ld.global.nc.v4.b32 {%0,%1,%2,%3}, [%4];" : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "l"(p));
     } else {
-        const uint2 *b = reinterpret_cast<const uint2 *>(base) + ql;
-        uint2 raw[RL];
+        asm("ld.global.nc.v2.b32 {%0,%1}, [%2];" : "=r"(w[0]), "=r"(w[1]) : "l"(p));
+    }
+}
+
+// Columns [P ql, P ql + P) of the rows of words wv[i] (word-major layout of VRP
+// columns), widened to float.  Rows past the document's end read word 0: finite
+// values whose tau is masked to 0.  One unrolled loop per storage type, so all RL
+// loads of a lane are in flight together.
+template <int VRP, int P, int RL>
+__device__ __forceinline__ void gather_rows(float (&rv)[RL][P], const void *base, int kprec, const int (&wv)[RL],
+                                            int ql) {
+    if (kprec == 0) {
+        const float *b = reinterpret_cast<const float *>(base) + ql * P;
 #pragma unroll
-        for (int i = 0; i < RL; ++i) raw[i] = __ldg(b + (long)wv[i] * S4);
-        if (kprec == 1) {   // a bfloat16 is the upper half of the float with the same value
+        for (int i = 0; i < RL; ++i) {
+            uint32_t w[P];
+            ldg_words<P>(b + (long)wv[i] * VRP, w);
 #pragma unroll
-            for (int i = 0; i < RL; ++i)
-                rv[i] = make_float4(__uint_as_float(raw[i].x << 16), __uint_as_float(raw[i].x & 0xffff0000u),
-                                    __uint_as_float(raw[i].y << 16), __uint_as_float(raw[i].y & 0xffff0000u));
-        } else {
-#pragma unroll
-            for (int i = 0; i < RL; ++i) {
-                __half2 a, c;
-                memcpy(&a, &raw[i].x, sizeof a);
-                memcpy(&c, &raw[i].y, sizeof c);
-                const float2 fa = __half22float2(a), fc = __half22float2(c);
-                rv[i] = make_float4(fa.x, fa.y, fc.x, fc.y);
-            }
+            for (int k = 0; k < P; ++k) rv[i][k] = __uint_as_float(w[k]);
         }
+    } else {
+        const unsigned short *b = reinterpret_cast<const unsigned short *>(base) + ql * P;
+        uint32_t raw[RL][P / 2];
+#pragma unroll
+        for (int i = 0; i < RL; ++i) ldg_words<P / 2>(b + (long)wv[i] * VRP, raw[i]);
+#pragma unroll
+        for (int i = 0; i < RL; ++i)
+#pragma unroll
+            for (int k = 0; k < P / 2; ++k) {
+                const float2 f = widen2(raw[i][k], kprec);
+                rv[i][2 * k] = f.x;
+                rv[i][2 * k + 1] = f.y;
+            }
     }
 }
 
 // Puts row block b ^ ql into register block b (blocks of R rows): conditional
 // swaps of whole rows, one pass per bit of ql.
-template <int RL, int Q, int R>
-__device__ __forceinline__ void permute_rows(float4 (&rv)[RL], int ql) {
+template <int RL, int P, int Q, int R>
+__device__ __forceinline__ void permute_rows(float (&rv)[RL][P], int ql) {
 #pragma unroll
     for (int bit = 1; bit < Q; bit <<= 1) {
         const bool sw = (ql & bit) != 0;
@@ -96,21 +117,25 @@ __device__ __forceinline__ void permute_rows(float4 (&rv)[RL], int ql) {
         for (int i = 0; i < RL; ++i) {
             if ((i / R) & bit) continue;   // each pair of blocks once, from its lower block
             const int j = i + bit * R;
-            const float4 x = rv[i], y = rv[j];
-            rv[i] = sw ? y : x;
-            rv[j] = sw ? x : y;
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const float x = rv[i][k], y = rv[j][k];
+                rv[i][k] = sw ? y : x;
+                rv[j][k] = sw ? x : y;
+            }
         }
     }
 }
 
 // Partial dots of every register row with the lane's slice of u.
-template <int RL>
-__device__ __forceinline__ void partial_dots(const float4 (&rv)[RL], const float (&u)[kColP], float (&s)[RL]) {
-    const float2 u01 = make_float2(u[0], u[1]), u23 = make_float2(u[2], u[3]);
+template <int RL, int P>
+__device__ __forceinline__ void partial_dots(const float (&rv)[RL][P], const float (&u)[P], float (&s)[RL]) {
 #pragma unroll
     for (int i = 0; i < RL; ++i) {
-        float2 d = __fmul2_rn(make_float2(rv[i].x, rv[i].y), u01);
-        d = __ffma2_rn(make_float2(rv[i].z, rv[i].w), u23, d);
+        float2 d = __fmul2_rn(make_float2(rv[i][0], rv[i][1]), make_float2(u[0], u[1]));
+#pragma unroll
+        for (int k = 2; k < P; k += 2)
+            d = __ffma2_rn(make_float2(rv[i][k], rv[i][k + 1]), make_float2(u[k], u[k + 1]), d);
         s[i] = d.x + d.y;
     }
 }
@@ -135,12 +160,14 @@ __device__ __forceinline__ void all_gather(float (&tv)[RL]) {
 }
 
 // The FP64 guard for a K^T u below 2^-100 (rare, entered by the whole warp):
-// the lane's u slices are published in the warp's shared buffer `su` (lane l's
-// four values at 4 l), and the dot of an own row is recomputed in FP64 from the
-// stored row (the same, exactly widened values) and the team's whole u.
-__device__ __forceinline__ void publish_u(float *su, int lane, const float (&u)[kColP]) {
+// the lane's u slice is published in the warp's shared buffer `su` (lane l's P
+// values at P l), and the dot of an own row is recomputed in FP64 from the stored
+// row (the same, exactly widened values) and the team's whole u.
+template <int P>
+__device__ __forceinline__ void publish_u(float *su, int lane, const float (&u)[P]) {
     __syncwarp();
-    reinterpret_cast<float4 *>(su)[lane] = make_float4(u[0], u[1], u[2], u[3]);
+#pragma unroll
+    for (int k = 0; k < P; ++k) su[P * lane + k] = u[k];
     __syncwarp();
 }
 template <int VRP>
@@ -159,11 +186,11 @@ __device__ __forceinline__ double dot_fp64(const void *base, int kprec, int w, c
 
 // One task: up to 32 / (G Q) documents of one bucket (LMAX = G RL rows).  A team of
 // G row groups of Q lanes owns a document; group g holds rows [g RL, g RL + RL).
-// su: this warp's shared buffer (32 float4) for the FP64 guard.
+// su: this warp's shared buffer (32 P floats) for the FP64 guard.
 template <int VRP, int G, int RL>
 __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &q, int4 tk, int lane,
                                           float *su) {
-    constexpr int P = kColP, Q = VRP / P, R = RL / Q, TEAM = G * Q;
+    constexpr int P = cols_p(VRP), Q = VRP / P, R = RL / Q, TEAM = G * Q;
     static_assert(Q >= 1 && Q <= 32 && (Q & (Q - 1)) == 0, "row groups of a power of two lanes");
     static_assert(RL % Q == 0 && R >= 1 && TEAM <= 32 && (G & (G - 1)) == 0, "whole row blocks");
     const int team = lane / TEAM, g = (lane / Q) % G, ql = lane % Q;
@@ -180,7 +207,7 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
     int *const status = qp->status;
     const int2 *ent = a.nz + beg;
     const int row0 = g * RL;                          // the group's first row
-    const float *su_team = su + 4 * (team * TEAM);    // the team's u, column-ordered (guard only)
+    const float *su_team = su + P * (team * TEAM);    // the team's u, column-ordered (guard only)
 
     // c of the rows this lane finishes (zero past the end: their tau is 0)
     float cown[R];
@@ -197,19 +224,19 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
         u[k] = has && col < vr ? u0 : 0.f;
     }
     // the group's rows of K^T: word ids in natural order, all loads in flight at once
-    float4 rv[RL];
+    float rv[RL][P];
     {
         int wv[RL];
 #pragma unroll
         for (int i = 0; i < RL; ++i) wv[i] = row0 + i < len ? __ldg(&ent[row0 + i].x) : 0;
-        gather_rows<VRP, RL>(rv, q.it.KT, a.kprec, wv, ql);
+        gather_rows<VRP, P, RL>(rv, q.it.KT, a.kprec, wv, ql);
     }
-    permute_rows<RL, Q, R>(rv, ql);
+    permute_rows<RL, P, Q, R>(rv, ql);
 
     bool bad = false;
     for (int it = 0; it < q.t; ++it) {
         float tv[RL];
-        partial_dots<RL>(rv, u, tv);
+        partial_dots<RL, P>(rv, u, tv);
         reduce_scatter<float, RL, Q, R>(tv);
         bool tiny = false;
         float s_own[R];
@@ -222,7 +249,7 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
         }
         if (__any_sync(kFull, tiny)) {
             SWMD_COLD_PATH();
-            publish_u(su, lane, u);
+            publish_u<P>(su, lane, u);
 #pragma unroll
             for (int o = 0; o < R; ++o) {
                 if (cown[o] != 0.f && !(s_own[o] >= 0x1p-100f)) {
@@ -234,27 +261,29 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
             }
         }
         all_gather<RL, Q, R>(tv);
-        float2 acc01 = make_float2(0.f, 0.f), acc23 = acc01;
+        float2 acc[P / 2];
+#pragma unroll
+        for (int k = 0; k < P / 2; ++k) acc[k] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < RL; ++i) {
             const float2 t2 = make_float2(tv[i], tv[i]);
-            acc01 = __ffma2_rn(make_float2(rv[i].x, rv[i].y), t2, acc01);
-            acc23 = __ffma2_rn(make_float2(rv[i].z, rv[i].w), t2, acc23);
+#pragma unroll
+            for (int k = 0; k < P / 2; ++k)
+                acc[k] = __ffma2_rn(make_float2(rv[i][2 * k], rv[i][2 * k + 1]), t2, acc[k]);
         }
         // the row groups' partial sums (a + b = b + a: every group gets the same u)
 #pragma unroll
-        for (int m = Q; m < TEAM; m <<= 1) {
-            acc01.x += __shfl_xor_sync(kFull, acc01.x, m);
-            acc01.y += __shfl_xor_sync(kFull, acc01.y, m);
-            acc23.x += __shfl_xor_sync(kFull, acc23.x, m);
-            acc23.y += __shfl_xor_sync(kFull, acc23.y, m);
-        }
-        const float acc[P] = {acc01.x, acc01.y, acc23.x, acc23.y};
+        for (int m = Q; m < TEAM; m <<= 1)
+#pragma unroll
+            for (int k = 0; k < P / 2; ++k) {
+                acc[k].x += __shfl_xor_sync(kFull, acc[k].x, m);
+                acc[k].y += __shfl_xor_sync(kFull, acc[k].y, m);
+            }
 #pragma unroll
         for (int k = 0; k < P; ++k) {
             const int col = ql * P + k;
             const bool live = has && col < vr;
-            const float nu = live ? rr[k] * rcp_approx(acc[k]) : 0.f;
+            const float nu = live ? rr[k] * rcp_approx((k & 1) ? acc[k / 2].y : acc[k / 2].x) : 0.f;
             bad |= live && !(nu < INFINITY);
             u[k] = nu;
         }
@@ -265,7 +294,7 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
     bool tiny = false;
     {
         float tv[RL];
-        partial_dots<RL>(rv, u, tv);
+        partial_dots<RL, P>(rv, u, tv);
         reduce_scatter<float, RL, Q, R>(tv);
 #pragma unroll
         for (int o = 0; o < R; ++o) {
@@ -277,13 +306,13 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
         int wv[RL];   // the word ids again (the registers were free during the iterations)
 #pragma unroll
         for (int i = 0; i < RL; ++i) wv[i] = row0 + i < len ? __ldg(&ent[row0 + i].x) : 0;
-        gather_rows<VRP, RL>(rv, q.it.KMT, a.kprec, wv, ql);
+        gather_rows<VRP, P, RL>(rv, q.it.KMT, a.kprec, wv, ql);
     }
-    permute_rows<RL, Q, R>(rv, ql);
+    permute_rows<RL, P, Q, R>(rv, ql);
     double dist = 0.0;
     {
         float tv[RL];
-        partial_dots<RL>(rv, u, tv);
+        partial_dots<RL, P>(rv, u, tv);
         reduce_scatter<float, RL, Q, R>(tv);
 #pragma unroll
         for (int o = 0; o < R; ++o)
@@ -291,7 +320,7 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
     }
     if (__any_sync(kFull, tiny)) {
         SWMD_COLD_PATH();
-        publish_u(su, lane, u);
+        publish_u<P>(su, lane, u);
 #pragma unroll
         for (int o = 0; o < R; ++o) {
             if (cown[o] != 0.f && !(s_own[o] >= 0x1p-100f)) {
@@ -316,22 +345,23 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
 // One block's share of the tasks for one query.
 template <int VRP>
 __device__ __forceinline__ void cols_block(const ColArgs &a, const ResidentArgs &q) {
-    __shared__ __align__(16) float s_u[kColThreads * 4];   // per warp: 32 lanes x 4 values of u
+    constexpr int P = cols_p(VRP);
+    __shared__ __align__(16) float s_u[kColThreads * P];   // per warp: 32 lanes x P values of u
     const int lane = threadIdx.x & 31;
-    float *su = s_u + 4 * (threadIdx.x & ~31);
+    float *su = s_u + P * (threadIdx.x & ~31);
     const long gwarp = ((long)blockIdx.x * kColThreads + threadIdx.x) >> 5;
     const long nwarps = ((long)gridDim.x * kColThreads) >> 5;
     for (long task = gwarp; task < a.n_tasks; task += nwarps) {
         const int4 tk = __ldg(a.tasks + task);   // first document, documents, bucket
         switch (tk.z) {
             case 8:
-                if constexpr (cols_fits(8, VRP)) cols_task<VRP, 1, 8>(a, q, tk, lane, su);
+                if constexpr (cols_fits(8, VRP)) cols_task<VRP, cols_groups(8, VRP), 8 / cols_groups(8, VRP)>(a, q, tk, lane, su);
                 break;
             case 16:
                 if constexpr (cols_fits(16, VRP)) cols_task<VRP, cols_groups(16, VRP), 16 / cols_groups(16, VRP)>(a, q, tk, lane, su);
                 break;
             case 24:
-                if constexpr (cols_fits(24, VRP)) cols_task<VRP, 1, 24>(a, q, tk, lane, su);
+                if constexpr (cols_fits(24, VRP)) cols_task<VRP, cols_groups(24, VRP), 24 / cols_groups(24, VRP)>(a, q, tk, lane, su);
                 break;
             default:
                 cols_task<VRP, cols_groups(32, VRP), 32 / cols_groups(32, VRP)>(a, q, tk, lane, su);
@@ -342,8 +372,13 @@ __device__ __forceinline__ void cols_block(const ColArgs &a, const ResidentArgs 
 
 // BATCHED: grid row y runs a.queries[y] (a device array); else the query is the
 // kernel argument a.q0.  Two kernels, so neither selects between the two sources.
+// Four blocks of 128 threads per SM (at most 128 registers a thread): the gathers
+// of one warp's rows are hidden by the arithmetic of the others, which measured
+// faster than fewer, spill-free warps.  128-column layouts hold 32 rows of four
+// columns per lane and take three blocks (168 registers).
+constexpr int cols_min_blocks(int vrp) { return vrp >= 128 ? 3 : 4; }
 template <int VRP, bool BATCHED>
-__global__ void __launch_bounds__(kColThreads) k_resident_cols(const __grid_constant__ ColArgs a) {
+__global__ void __launch_bounds__(kColThreads, cols_min_blocks(VRP)) k_resident_cols(const __grid_constant__ ColArgs a) {
     if constexpr (BATCHED) cols_block<VRP>(a, a.queries[blockIdx.y]);
     else cols_block<VRP>(a, a.q0);
 }
@@ -375,6 +410,8 @@ int cols_bucket(int len, int vrp) {
         if (cols_fits(lmax, vrp) && lmax >= len) return lmax;
     return 0;
 }
+
+int cols_docs_per_task(int lmax, int vrp) { return 32 / cols_team(lmax, vrp); }
 
 // Layouts of 16 to 128 columns (teams of 4 to 32 lanes).  Narrower queries are
 // padded to 16 columns: with teams of one or two lanes a lane would hold the
