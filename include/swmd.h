@@ -117,6 +117,11 @@ typedef struct swmd_options {
                               marginal of P against r) falls below tol; max_iter (at most
                               4096) caps it.  SWMD_PATH_AUTO then takes the fused path;
                               the resident and plain paths refuse tol > 0 (SWMD_EINVAL). */
+    int32_t queries_per_tile; /* swmd_query_batch and the server, column-split solver:
+                              queries of one layout that share a (query group, document
+                              task) tile of the one-launch multi-query walk; 0 = the
+                              swmd_autotune_batch choice, else as many (1..8) as keep
+                              their K^T and KM^T within a quarter of the L2 cache */
 } swmd_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -385,6 +390,28 @@ typedef struct swmd_tune_result {
 SWMD_API int swmd_autotune(swmd_corpus *corpus, int32_t v_r, int32_t reps, swmd_tune_result *out);
 
 /* ------------------------------------------------------------------ batch */
+typedef struct swmd_batch_tune_result {
+    int32_t layouts;        /* column-split layouts (VRP values) the batch holds */
+    int32_t vrp[4];         /* those layouts ... */
+    int32_t queries_per_tile[4];   /* ... and the tile size chosen for each */
+    float default_ms;       /* the batch with the default tile sizes */
+    float best_ms;          /* the batch with the chosen ones */
+    int32_t candidates;     /* batches timed */
+} swmd_batch_tune_result;
+
+/* Times swmd_query_batch on this batch (arguments as in swmd_query_batch; the
+ * distances are discarded) for every queries_per_tile candidate (1, 2, 4, 8) of the
+ * column-split layouts it holds, `reps` times each (>= 1), and keeps the fastest
+ * for each layout and K precision: later batches use it unless
+ * swmd_options.queries_per_tile fixes it.  Synchronous; refused while a server is
+ * attached.  The tile size changes which queries share a tile, never a distance's
+ * bits.  The paper has no counterpart (Section III-D's hierarchical threading was
+ * chosen by hand). */
+SWMD_API int swmd_autotune_batch(swmd_corpus *corpus, int32_t n_queries, const int64_t *q_ptr,
+                                 const int32_t *h_word_ids, const float *h_weights,
+                                 const float *h_lambdas, int32_t max_iter, int32_t reps,
+                                 swmd_batch_tune_result *out);
+
 /* Several queries at once (Section III-D notes that many source documents can
  * run together; the paper's multi-query experiment, Section V):
  *   q_ptr[n_queries+1] (int64, host): query i is entries q_ptr[i]..q_ptr[i+1]-1
@@ -392,10 +419,13 @@ SWMD_API int swmd_autotune(swmd_corpus *corpus, int32_t v_r, int32_t reps, swmd_
  *   h_lambdas[n_queries] (float, host): lambda of each query.
  *   h_out[n_queries * N] (double, host): row i = the distances of query i.
  * Each query takes its own path (swmd_resolve_path).  The resident queries of one
- * K^T layout run as one batched cost launch and one batched solver launch (grid
- * row y = query y) on corpora under 20,000 documents, where one query leaves the
- * GPU partly idle; on larger corpora, where one query fills it, they run one launch
- * pair per query.  The per-iteration queries run one after another.  The device
+ * K^T layout and solver run as one batched cost launch and one solver launch.
+ * With the column-split solver that launch walks (query group, document task)
+ * tiles: a group is swmd_options.queries_per_tile queries (or the autotuned or
+ * L2-sized number), a task's nonzeros are read from DRAM once per group, and the
+ * groups follow one another inside the launch.  The other resident solvers run
+ * the group's queries as grid rows on corpora under 20,000 documents and one
+ * launch pair per query above.  The per-iteration queries run one after another.  The device
  * work of the whole call is captured once per batch shape (the queries' paths and
  * sizes, the per-iteration queries' lambdas, max_iter) as a CUDA graph and replayed
  * on the next batch of that shape.  The workspace grows on demand (cudaMalloc) and

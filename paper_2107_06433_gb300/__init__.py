@@ -41,7 +41,8 @@ class swmd_options(ctypes.Structure):
                 ("team_lanes", ctypes.c_int32), ("lanes_per_nz", ctypes.c_int32),
                 ("tile_threads", ctypes.c_int32), ("nnz_per_lane", ctypes.c_int32),
                 ("tile_nnz", ctypes.c_int32), ("cost_split", ctypes.c_int32),
-                ("solver", ctypes.c_int32), ("tol", ctypes.c_float)]
+                ("solver", ctypes.c_int32), ("tol", ctypes.c_float),
+                ("queries_per_tile", ctypes.c_int32)]
 
 
 class swmd_corpus_info(ctypes.Structure):
@@ -69,6 +70,12 @@ class swmd_tune_result(ctypes.Structure):
                 ("nnz_per_lane", ctypes.c_int32), ("cost_split", ctypes.c_int32),
                 ("default_ms", ctypes.c_float), ("best_ms", ctypes.c_float),
                 ("candidates", ctypes.c_int32), ("path", ctypes.c_int32)]
+
+
+class swmd_batch_tune_result(ctypes.Structure):
+    _fields_ = [("layouts", ctypes.c_int32), ("vrp", ctypes.c_int32 * 4),
+                ("queries_per_tile", ctypes.c_int32 * 4), ("default_ms", ctypes.c_float),
+                ("best_ms", ctypes.c_float), ("candidates", ctypes.c_int32)]
 
 
 _lib = None
@@ -99,6 +106,8 @@ _SIGS = {
     "swmd_debug_read": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P]),
     "swmd_query_batch": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P, ctypes.c_int32, P]),
     "swmd_autotune": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P]),
+    "swmd_autotune_batch": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P, ctypes.c_int32,
+                                           ctypes.c_int32, P]),
     "swmd_resolve_path": (ctypes.c_int, [P, ctypes.c_int32, P]),
     "swmd_last_iterations": (ctypes.c_int, [P, P]),
     "swmd_wmd_pairs": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P, P, P, ctypes.c_float,
@@ -350,21 +359,38 @@ def swmd_debug_read(corpus: Corpus, what: str, v_r: int = 0) -> np.ndarray:
     return out
 
 
-def swmd_query_batch(corpus: Corpus, queries, lambdas, max_iter: int) -> np.ndarray:
-    """queries: list of (ids, weights).  Returns float64[n_queries, N]."""
+def _batch_arrays(queries, lambdas):
     n = len(queries)
     q_ptr = np.zeros(n + 1, np.int64)
     for i, (qi, _) in enumerate(queries):
         q_ptr[i + 1] = q_ptr[i] + len(qi)
     ids = np.concatenate([np.asarray(q[0], np.int32) for q in queries]) if n else np.zeros(0, np.int32)
     ws = np.concatenate([np.asarray(q[1], np.float32) for q in queries]) if n else np.zeros(0, np.float32)
-    lam, plam = _np(np.broadcast_to(np.asarray(lambdas, np.float32), (n,)), np.float32)
-    ids, pids = _np(ids, np.int32)
-    ws, pws = _np(ws, np.float32)
+    lam = np.ascontiguousarray(np.broadcast_to(np.asarray(lambdas, np.float32), (n,)), np.float32)
+    return n, q_ptr, np.ascontiguousarray(ids, np.int32), np.ascontiguousarray(ws, np.float32), lam
+
+
+def swmd_query_batch(corpus: Corpus, queries, lambdas, max_iter: int) -> np.ndarray:
+    """queries: list of (ids, weights).  Returns float64[n_queries, N]."""
+    n, q_ptr, ids, ws, lam = _batch_arrays(queries, lambdas)
     out = np.empty((n, corpus.N), np.float64)
-    _err(lib().swmd_query_batch(corpus.handle, n, q_ptr.ctypes.data_as(P), pids, pws, plam,
-                                int(max_iter), out.ctypes.data_as(P)), "swmd_query_batch")
+    _err(lib().swmd_query_batch(corpus.handle, n, q_ptr.ctypes.data_as(P), ids.ctypes.data_as(P),
+                                ws.ctypes.data_as(P), lam.ctypes.data_as(P), int(max_iter),
+                                out.ctypes.data_as(P)), "swmd_query_batch")
     return out
+
+
+def swmd_autotune_batch(corpus: Corpus, queries, lambdas, max_iter: int, reps: int = 2) -> dict:
+    """Times swmd_query_batch on this batch for every queries-per-tile candidate of its
+    column-split layouts and keeps the fastest.  Returns the chosen tile sizes."""
+    n, q_ptr, ids, ws, lam = _batch_arrays(queries, lambdas)
+    res = swmd_batch_tune_result()
+    _err(lib().swmd_autotune_batch(corpus.handle, n, q_ptr.ctypes.data_as(P), ids.ctypes.data_as(P),
+                                   ws.ctypes.data_as(P), lam.ctypes.data_as(P), int(max_iter),
+                                   int(reps), ctypes.byref(res)), "swmd_autotune_batch")
+    k = res.layouts
+    return {"layouts": k, "vrp": list(res.vrp)[:k], "queries_per_tile": list(res.queries_per_tile)[:k],
+            "default_ms": res.default_ms, "best_ms": res.best_ms, "candidates": res.candidates}
 
 
 def swmd_autotune(corpus: Corpus, v_r: int, reps: int = 5) -> dict:

@@ -310,6 +310,15 @@ int resident_solver(swmd_corpus *c, int vr, int kprec) {
     return s;
 }
 
+int cols_queries_per_group(swmd_corpus *c, int vrp, int kprec) {
+    if (c->opt.queries_per_tile > 0) return std::min(c->opt.queries_per_tile, 64);
+    auto it = c->tuned_qpt.find(std::make_pair(vrp, kprec));
+    if (it != c->tuned_qpt.end()) return it->second;
+    const size_t per_query = 2 * (size_t)std::max(c->Vu, 1) * vrp * kprec_bytes(kprec);
+    const size_t fit = (c->l2_bytes / 4) / per_query;
+    return (int)std::max<size_t>(1, std::min<size_t>(8, fit));
+}
+
 int run_resident_batch(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kprec, int vr, int nq,
                        const ResidentArgs *d_batch, cudaStream_t st) {
     int solver = 0, npl_want = 0, split = 0;
@@ -326,6 +335,8 @@ int run_resident_batch(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kp
         ca.kprec = kprec;
         ca.q0 = ra;
         ca.queries = d_batch;
+        ca.nq = d_batch ? nq : 1;
+        ca.q_per_group = cols_queries_per_group(c, m.vrp, kprec);
         cudaError_t e = launch_resident_cols(ca, m.vrp, c->sms, st, nq);
         if (e != cudaSuccess)
             return set_error(e == cudaErrorMemoryAllocation ? SWMD_ENOMEM : SWMD_ECUDA,
@@ -586,7 +597,7 @@ int swmd_create_corpus(int32_t V, int32_t N, int64_t nnz, const int64_t *row_ptr
     if (opt.max_vr <= 0) opt.max_vr = 128;
     if (opt.max_vr > 128) return set_error(SWMD_EINVAL, "swmd_create_corpus: max_vr above 128");
     if (opt.k_precision < 0 || opt.k_precision > 2 || opt.path < 0 || opt.path > 3 || !(opt.tol >= 0.f) ||
-        std::isinf(opt.tol))
+        std::isinf(opt.tol) || opt.queries_per_tile < 0)
         return set_error(SWMD_EINVAL, "swmd_create_corpus: bad k_precision or path");
     int b = opt.doc_begin < 0 ? 0 : opt.doc_begin;
     int e = opt.doc_end < 0 ? N : opt.doc_end;
@@ -708,6 +719,10 @@ int swmd_create_corpus(int32_t V, int32_t N, int64_t nnz, const int64_t *row_ptr
     {
         cudaError_t ce = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
         if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaDeviceGetAttribute"));
+        int l2 = 0;
+        ce = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+        if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaDeviceGetAttribute"));
+        c->l2_bytes = (size_t)l2;
         ce = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
         if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamCreateWithFlags"));
     }
@@ -827,6 +842,7 @@ int swmd_corpus_set_options(swmd_corpus *c, const swmd_options *opt) {
     c->opt.cost_split = opt->cost_split;
     c->opt.solver = opt->solver;
     c->opt.tol = opt->tol;
+    c->opt.queries_per_tile = opt->queries_per_tile;
     clear_graphs(c);
     DeviceGuard guard(c->device);
     return build_tiles(c);

@@ -312,7 +312,9 @@ struct ColArgs {
     int n_tasks;
     int kprec;
     ResidentArgs q0;                 // the query when `queries` is NULL
-    const ResidentArgs *queries;     // device array: grid row y runs queries[y]
+    const ResidentArgs *queries;     // else: device array of nq queries of this layout, run
+    int nq;                          // in one launch over (group of q_per_group queries,
+    int q_per_group;                 // document task) tiles
 };
 // Documents longer than this are not held by the column-split solver.
 constexpr int kColMaxLen = 32;
@@ -320,19 +322,18 @@ constexpr int kColMaxLen = 32;
 // `vrp` (the bucket: 8, 16, 24 or 32, a multiple of vrp / 4); 0 if too long.
 int cols_bucket(int len, int vrp);
 constexpr int kColMaxRowsPerLane = 12;   // rows a lane holds with eight columns
-// Columns of every row a lane holds (P) and lanes of a row group (Q = vrp / P):
-// eight columns per lane, four for 128-column layouts.
-__host__ __device__ constexpr int cols_p(int vrp) { return vrp >= 128 ? 4 : 8; }
+// Columns of every row a lane holds (P = 8) and lanes of a row group (Q = vrp / P).
+__host__ __device__ constexpr int cols_p(int) { return 8; }
 __host__ __device__ constexpr int cols_q(int vrp) { return vrp / cols_p(vrp); }
 // A bucket of lmax rows is held by G row groups of Q lanes, each group RL = lmax / G
 // rows: the smallest power of two G with RL a multiple of Q and at most 12 (at most
-// 32 with four columns per lane), G Q <= 32 lanes; 0 when there is none (the bucket
-// does not exist for that layout).
+// Q when Q > 12: the 128-column layout's 16-lane groups hold 16 rows), G Q <= 32
+// lanes; 0 when there is none (the bucket does not exist for that layout).
 __host__ __device__ constexpr int cols_groups(int lmax, int vrp) {
     for (int g = 1; g <= 8; g *= 2) {
         const int rl = lmax / g, q = cols_q(vrp);
-        if (lmax % g == 0 && rl % q == 0 && rl <= (cols_p(vrp) == 8 ? kColMaxRowsPerLane : 32) && g * q <= 32)
-            return g;
+        const int cap = q > kColMaxRowsPerLane ? q : kColMaxRowsPerLane;
+        if (lmax % g == 0 && rl % q == 0 && rl <= cap && g * q <= 32) return g;
     }
     return 0;
 }
@@ -348,8 +349,8 @@ int cols_vrp(int vr);
 // Index of a column-split layout in the corpus's task lists (VRP 16, 32, 64, 128).
 inline int cols_index(int vrp) { return vrp == 16 ? 0 : vrp == 32 ? 1 : vrp == 64 ? 2 : 3; }
 constexpr int kColLayouts = 4;
-// Runs all t iterations and the final step for every document of the tasks;
-// nq > 1: grid rows y = 0..nq-1 run a.queries[y].
+// Runs all t iterations and the final step for every document of the tasks, for
+// a.q0, or (a.queries != NULL) for the a.nq = nq queries of a.queries in one launch.
 cudaError_t launch_resident_cols(const ColArgs &a, int vrp, int sms, cudaStream_t s, int nq);
 
 

@@ -138,6 +138,9 @@ struct swmd_corpus {
     std::map<std::pair<int, int>, std::tuple<int, int, int>> tuned_resident;
     // autotuned path (RESIDENT or FUSED) per (v_r, K precision), used by SWMD_PATH_AUTO
     std::map<std::pair<int, int>, int> tuned_path;
+    // autotuned queries per tile of the multi-query column-split walk per (VRP, K precision)
+    std::map<std::pair<int, int>, int> tuned_qpt;
+    size_t l2_bytes = 0;           // the device's L2 cache
     std::mutex mu;                 // serialises use of `main` and the graph cache
     int servers = 0;               // servers attached (under mu): tuning and option changes wait
 };
@@ -186,6 +189,10 @@ constexpr int kSolverAuto = 0, kSolverRegs = 1, kSolverTiled = 2, kSolverL2 = 3,
 // VRP <= 32, else the shared-memory tiled one).  Never kSolverCols on a corpus
 // without column-split tasks.
 int resident_solver(swmd_corpus *c, int vr, int kprec);
+// Queries per (query group, document task) tile of the multi-query column-split
+// walk for a layout: swmd_options.queries_per_tile, else the autotuned value, else
+// as many (1..8) as keep their K^T and KM^T within a quarter of L2.
+int cols_queries_per_group(swmd_corpus *c, int vrp, int kprec);
 constexpr int kTileBudgets[] = {64, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048};
 constexpr int kNumTileBudgets = 10;
 // (Re)builds the resident solver's tile sets for the corpus's current

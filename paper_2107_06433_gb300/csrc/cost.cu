@@ -43,6 +43,22 @@ __device__ __forceinline__ float storage_scale(float mmax) {
     return 1.f;
 }
 
+// Scratch place of the distance M[w][k] while a wide layout's cost is computed in
+// 32-column chunks: inside the word's own output rows, columns below vrp / 2 in
+// the K^T row and the others in the KM^T row, as FP32 (a row of vrp elements of
+// kbytes bytes holds vrp kbytes / 4 floats, at least vrp / 2).
+__device__ __forceinline__ float *cost_scratch(const CostArgs &a, long wi, int k, int vrp, int kbytes) {
+    const long stride = (long)vrp * kbytes / 4;
+    const int half = vrp / 2;
+    float *base = reinterpret_cast<float *>(k < half ? a.KT : a.KMT);
+    return base + wi * stride + (k < half ? k : k - half);
+}
+
+template <class KT_t> __device__ __forceinline__ KT_t to_k(float x);
+template <> __device__ __forceinline__ float to_k<float>(float x) { return x; }
+template <> __device__ __forceinline__ __nv_bfloat16 to_k<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <> __device__ __forceinline__ __half to_k<__half>(float x) { return __float2half_rn(x); }
+
 template <int KPT, int T, class KT_t>
 __device__ __noinline__ void k_cost_body(const CostArgs &a) {
     constexpr int VRP = KPT * T;
@@ -152,13 +168,17 @@ __global__ void __launch_bounds__(kCostThreads) k_cost(const __grid_constant__ C
 // to thread i mod TS, so the TS threads read consecutive 16-byte pieces), with 4
 // chunks per thread in flight (register double buffer); the main loop has no
 // barrier.  The TS partial sums are combined with shuffles at the end.
+// chunk >= 0: the query columns [32 chunk, 32 chunk + 32) of a wider layout of
+// vrp_full columns (VRP = 32): the distances M are written to the rows' scratch
+// (cost_scratch), to be turned into K and K.*M by k_cost_finish.
 template <int VRP, int TS, class KT_t>
-__device__ __noinline__ void k_cost_rows_body(const CostArgs &a) {
+__device__ __noinline__ void k_cost_rows_body(const CostArgs &a, int chunk, int vrp_full) {
     static_assert(VRP % 4 == 0 && VRP <= 32, "VRP");
     static_assert(TS == 1 || TS == 2 || TS == 4, "TS");
     constexpr int PF = 4;   // float4 chunks per thread in flight
     extern __shared__ __align__(16) float sQ[];   // sQ[dim * VRP + k] = E[q_k][dim], 0 for k >= v_r
-    const int vr = a.qp->vr;
+    const int col0 = chunk >= 0 ? VRP * chunk : 0;
+    const int vr = chunk >= 0 ? max(0, min(VRP, a.qp->vr - col0)) : a.qp->vr;
     const float lam = a.qp->lambda;
     const int d4 = a.d4;
     {
@@ -171,7 +191,7 @@ __device__ __noinline__ void k_cost_rows_body(const CostArgs &a) {
             const int c = i / VRP, k = i - c * VRP;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (k < vr) {
-                const int qid = __ldg(a.q_ids + k);
+                const int qid = __ldg(a.q_ids + col0 + k);
                 if (qid >= 0 && qid < a.V) v = __ldg(reinterpret_cast<const float4 *>(a.E + (size_t)qid * d4) + c);
             }
             sQ[(4 * c) * VRP + k] = v.x;
@@ -243,6 +263,16 @@ __device__ __noinline__ void k_cost_rows_body(const CostArgs &a) {
             m[2 * i + 1] = sqrtf(y);
         }
         if (!active) continue;
+        if (chunk >= 0) {
+            // this chunk's distances into the row's scratch (columns >= v_r: not read)
+#pragma unroll
+            for (int c = 0; c < VRP / 4; ++c) {
+                if (c % TS != t) continue;
+                float *dst = cost_scratch(a, wi, col0 + 4 * c, vrp_full, (int)sizeof(KT_t));
+                *reinterpret_cast<float4 *>(dst) = make_float4(m[4 * c], m[4 * c + 1], m[4 * c + 2], m[4 * c + 3]);
+            }
+            continue;
+        }
         float mn = INFINITY, mx = 0.f;
 #pragma unroll
         for (int k = 0; k < VRP; ++k)
@@ -270,14 +300,66 @@ __device__ __noinline__ void k_cost_rows_body(const CostArgs &a) {
 }
 
 template <int VRP, int TS, class KT_t>
-__global__ void __launch_bounds__(kCostThreads) k_cost_rows(const __grid_constant__ CostArgs a0, const CostArgs *batch) {
+__global__ void __launch_bounds__(kCostThreads) k_cost_rows(const __grid_constant__ CostArgs a0, const CostArgs *batch,
+                                                            int chunk, int vrp_full) {
     // one query per grid row when batched (batch[blockIdx.y]), else the argument
-    if (batch) k_cost_rows_body<VRP, TS, KT_t>(batch[blockIdx.y]);
-    else k_cost_rows_body<VRP, TS, KT_t>(a0);
+    if (batch) k_cost_rows_body<VRP, TS, KT_t>(batch[blockIdx.y], chunk, vrp_full);
+    else k_cost_rows_body<VRP, TS, KT_t>(a0, chunk, vrp_full);
+}
+
+// K and K.*M of the rows whose distances the chunked row kernel left in the
+// scratch: one warp per word, lane l takes columns l, l + 32, ...; the column's
+// minimum (shift) and maximum (FP16 scale) over the query words first.
+template <int VRP, class KT_t>
+__device__ __noinline__ void k_cost_finish_body(const CostArgs &a) {
+    constexpr int J = VRP / 32;
+    const int vr = a.qp->vr;
+    const float lam = a.qp->lambda;
+    const int lane = threadIdx.x & 31;
+    const long w0 = ((long)blockIdx.x * kCostThreads + threadIdx.x) >> 5;
+    const long nw = ((long)gridDim.x * kCostThreads) >> 5;
+    KT_t *KT = reinterpret_cast<KT_t *>(a.KT);
+    KT_t *KMT = reinterpret_cast<KT_t *>(a.KMT);
+    for (long wi = w0; wi < a.Vu; wi += nw) {
+        float m[J];
+        float mn = INFINITY, mx = 0.f;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int k = lane + 32 * j;
+            m[j] = *cost_scratch(a, wi, k, VRP, (int)sizeof(KT_t));
+            if (k < vr) {
+                mn = fminf(mn, m[j]);
+                mx = fmaxf(mx, m[j]);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        const float sh = (a.shift && mn < INFINITY) ? mn : 0.f;
+        const float bw = a.shift ? storage_scale<KT_t>(mx) : 1.f;
+        __syncwarp();   // every lane has read the row's scratch before it is overwritten
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int k = lane + 32 * j;
+            const float kk = (k < vr) ? expf(-lam * (m[j] - sh)) : 0.f;
+            KT[wi * VRP + k] = to_k<KT_t>(kk * bw);
+            KMT[wi * VRP + k] = to_k<KT_t>((kk * m[j]) * bw);
+        }
+        __syncwarp();
+    }
+}
+
+template <int VRP, class KT_t>
+__global__ void __launch_bounds__(kCostThreads) k_cost_finish(const __grid_constant__ CostArgs a0, const CostArgs *batch) {
+    if (batch) k_cost_finish_body<VRP, KT_t>(batch[blockIdx.y]);
+    else k_cost_finish_body<VRP, KT_t>(a0);
 }
 
 template <int VRP, int TS, class KT_t>
-cudaError_t run_rows(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *batch) {
+cudaError_t run_rows(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *batch, int chunk = -1,
+                     int vrp_full = 0) {
     auto kern = k_cost_rows<VRP, TS, KT_t>;
     const size_t smem = (size_t)a.d4 * VRP * sizeof(float);
     static LaunchCache cache;
@@ -292,7 +374,33 @@ cudaError_t run_rows(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *
     long cap = ((long)sms * per_sm + nq - 1) / nq;   // resident blocks shared by the queries
     if (cap < 1) cap = 1;
     if (blocks > cap) blocks = cap;
-    if (blocks > 0) kern<<<dim3((unsigned)blocks, (unsigned)nq), kCostThreads, smem, s>>>(a, batch);
+    if (blocks > 0) kern<<<dim3((unsigned)blocks, (unsigned)nq), kCostThreads, smem, s>>>(a, batch, chunk, vrp_full);
+    return cudaGetLastError();
+}
+
+// A layout wider than 32 columns: the row kernel on each 32-column chunk (distances
+// to the scratch), then the finishing pass over whole rows.
+template <int VRP, class KT_t>
+cudaError_t run_chunked(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *batch, int ts) {
+    for (int ch = 0; ch < VRP / 32; ++ch) {
+        cudaError_t e = ts == 2 ? run_rows<32, 2, KT_t>(a, s, nq, batch, ch, VRP)
+                      : ts == 4 ? run_rows<32, 4, KT_t>(a, s, nq, batch, ch, VRP)
+                                : run_rows<32, 1, KT_t>(a, s, nq, batch, ch, VRP);
+        if (e != cudaSuccess) return e;
+    }
+    auto kern = k_cost_finish<VRP, KT_t>;
+    static LaunchCache cache;
+    int per_sm = 1;
+    cudaError_t e = cache.blocks_per_sm(kern, kCostThreads, 0, -1, &per_sm);
+    if (e != cudaSuccess) return e;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long blocks = ((long)a.Vu * 32 + kCostThreads - 1) / kCostThreads;
+    long cap = ((long)sms * per_sm + nq - 1) / nq;
+    if (cap < 1) cap = 1;
+    if (blocks > cap) blocks = cap;
+    if (blocks > 0) kern<<<dim3((unsigned)blocks, (unsigned)nq), kCostThreads, 0, s>>>(a, batch);
     return cudaGetLastError();
 }
 
@@ -322,6 +430,10 @@ cudaError_t dispatch(const CostArgs &a, int vrp, cudaStream_t s, int nq, const C
 #undef SWMD_ROWS
             default: break;
         }
+    }
+    if ((vrp == 64 || vrp == 128) && (size_t)a.d4 * 32 * sizeof(float) <= 100 * 1024) {
+        const int ts = a.split == 1 || a.split == 2 || a.split == 4 ? a.split : (a.Vu >= 64 * 1024 ? 1 : 2);
+        return vrp == 64 ? run_chunked<64, KT_t>(a, s, nq, batch, ts) : run_chunked<128, KT_t>(a, s, nq, batch, ts);
     }
     switch (vrp) {
 #define SWMD_COST_T1(V) \

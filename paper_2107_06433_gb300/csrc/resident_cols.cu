@@ -8,8 +8,7 @@
 // WMD_j = sum_w c_wj (KM^T[w] . u_j) / (K^T[w] . u_j) (type 2).  A_j does not
 // change between iterations, so it is gathered once and kept in registers.
 //
-// Lanes.  A row group of Q = VRP / P lanes (P = 8 columns per lane, 4 for
-// 128-column layouts) holds rows of A_j: lane q holds columns [P q, P q + P) of
+// Lanes.  A row group of Q = VRP / 8 lanes holds rows of A_j: lane q holds columns [P q, P q + P) of
 // every row of the group (LMAX rows in all, the document's length rounded up to
 // its bucket; rows past the end are masked), of u_j and of acc.  acc = A_j^T tau then
 // needs no exchange.  The dots s = A_j u_j are partial over the lane's columns and
@@ -23,8 +22,9 @@
 // coalesced 16-byte slice per lane of each row) and put into that order once, by
 // log2(Q) passes of conditional swaps.
 //
-// A document of up to 12 rows per lane (32 with P = 4) is one row group; longer
-// ones are G row groups (the team), whose partial acc are summed with shuffles.
+// A document of up to 12 rows per lane (16 in 128-column layouts) is one row
+// group; longer ones are G row groups (the team), whose partial acc are summed with
+// shuffles.
 // Packed f32x2 FMAs work on column pairs of a row: a row's dot is P / 2 of them
 // plus one add, its contribution to acc another P / 2.
 //
@@ -342,65 +342,92 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
     }
 }
 
-// One block's share of the tasks for one query.
+// One document task for one query: the bucket's instantiation.
 template <int VRP>
-__device__ __forceinline__ void cols_block(const ColArgs &a, const ResidentArgs &q) {
+__device__ __forceinline__ void cols_dispatch(const ColArgs &a, const ResidentArgs &q, int4 tk, int lane, float *su) {
+    switch (tk.z) {
+        case 8:
+            if constexpr (cols_fits(8, VRP)) cols_task<VRP, cols_groups(8, VRP), 8 / cols_groups(8, VRP)>(a, q, tk, lane, su);
+            break;
+        case 16:
+            if constexpr (cols_fits(16, VRP)) cols_task<VRP, cols_groups(16, VRP), 16 / cols_groups(16, VRP)>(a, q, tk, lane, su);
+            break;
+        case 24:
+            if constexpr (cols_fits(24, VRP)) cols_task<VRP, cols_groups(24, VRP), 24 / cols_groups(24, VRP)>(a, q, tk, lane, su);
+            break;
+        default:
+            cols_task<VRP, cols_groups(32, VRP), 32 / cols_groups(32, VRP)>(a, q, tk, lane, su);
+            break;
+    }
+}
+
+// Four blocks of 128 threads per SM (at most 128 registers a thread): the gathers
+// of one warp's rows are hidden by the arithmetic of the others, which measured
+// faster than fewer, spill-free warps.  128-column layouts hold 16 rows of eight
+// columns per lane and take three blocks (168 registers).
+constexpr int cols_min_blocks(int vrp) { return vrp >= 128 ? 3 : 4; }
+
+// One query (the kernel argument a.q0): warps walk the document tasks.
+template <int VRP>
+__global__ void __launch_bounds__(kColThreads, cols_min_blocks(VRP)) k_resident_cols(const __grid_constant__ ColArgs a) {
     constexpr int P = cols_p(VRP);
     __shared__ __align__(16) float s_u[kColThreads * P];   // per warp: 32 lanes x P values of u
     const int lane = threadIdx.x & 31;
     float *su = s_u + P * (threadIdx.x & ~31);
     const long gwarp = ((long)blockIdx.x * kColThreads + threadIdx.x) >> 5;
     const long nwarps = ((long)gridDim.x * kColThreads) >> 5;
-    for (long task = gwarp; task < a.n_tasks; task += nwarps) {
-        const int4 tk = __ldg(a.tasks + task);   // first document, documents, bucket
-        switch (tk.z) {
-            case 8:
-                if constexpr (cols_fits(8, VRP)) cols_task<VRP, cols_groups(8, VRP), 8 / cols_groups(8, VRP)>(a, q, tk, lane, su);
-                break;
-            case 16:
-                if constexpr (cols_fits(16, VRP)) cols_task<VRP, cols_groups(16, VRP), 16 / cols_groups(16, VRP)>(a, q, tk, lane, su);
-                break;
-            case 24:
-                if constexpr (cols_fits(24, VRP)) cols_task<VRP, cols_groups(24, VRP), 24 / cols_groups(24, VRP)>(a, q, tk, lane, su);
-                break;
-            default:
-                cols_task<VRP, cols_groups(32, VRP), 32 / cols_groups(32, VRP)>(a, q, tk, lane, su);
-                break;
-        }
+    for (long task = gwarp; task < a.n_tasks; task += nwarps)
+        cols_dispatch<VRP>(a, a.q0, __ldg(a.tasks + task), lane, su);
+}
+
+// Many queries of one layout in one persistent launch: warps walk the tiles
+// (query group, document task) in group-major order -- the whole GPU works on one
+// group's K^T at a time (it stays in L2) and the next group starts while the last
+// tiles of this one finish.  A tile runs its task for every query of the group in
+// turn, so the task's nonzeros come from DRAM once for the group (later queries
+// re-read them from L1).  Each (query, document) computes exactly what the single
+// query does: the same bits.
+template <int VRP>
+__global__ void __launch_bounds__(kColThreads, cols_min_blocks(VRP)) k_resident_cols_multi(const __grid_constant__ ColArgs a) {
+    constexpr int P = cols_p(VRP);
+    __shared__ __align__(16) float s_u[kColThreads * P];
+    const int lane = threadIdx.x & 31;
+    float *su = s_u + P * (threadIdx.x & ~31);
+    const long gwarp = ((long)blockIdx.x * kColThreads + threadIdx.x) >> 5;
+    const long nwarps = ((long)gridDim.x * kColThreads) >> 5;
+    const long groups = (a.nq + a.q_per_group - 1) / a.q_per_group;
+    const long tiles = groups * a.n_tasks;
+    for (long tile = gwarp; tile < tiles; tile += nwarps) {
+        const long grp = tile / a.n_tasks;
+        const int4 tk = __ldg(a.tasks + (tile - grp * a.n_tasks));
+        const int q0 = (int)grp * a.q_per_group;
+        const int q1 = min(q0 + a.q_per_group, a.nq);
+        for (int qi = q0; qi < q1; ++qi) cols_dispatch<VRP>(a, a.queries[qi], tk, lane, su);
     }
-}
-
-// BATCHED: grid row y runs a.queries[y] (a device array); else the query is the
-// kernel argument a.q0.  Two kernels, so neither selects between the two sources.
-// Four blocks of 128 threads per SM (at most 128 registers a thread): the gathers
-// of one warp's rows are hidden by the arithmetic of the others, which measured
-// faster than fewer, spill-free warps.  128-column layouts hold 32 rows of four
-// columns per lane and take three blocks (168 registers).
-constexpr int cols_min_blocks(int vrp) { return vrp >= 128 ? 3 : 4; }
-template <int VRP, bool BATCHED>
-__global__ void __launch_bounds__(kColThreads, cols_min_blocks(VRP)) k_resident_cols(const __grid_constant__ ColArgs a) {
-    if constexpr (BATCHED) cols_block<VRP>(a, a.queries[blockIdx.y]);
-    else cols_block<VRP>(a, a.q0);
-}
-
-template <int VRP, bool BATCHED>
-cudaError_t run_cols_k(const ColArgs &a, int sms, int nq, cudaStream_t s) {
-    auto kern = k_resident_cols<VRP, BATCHED>;
-    static LaunchCache cache;
-    int per_sm = 1;
-    cudaError_t e = cache.blocks_per_sm(kern, kColThreads, 0, -1, &per_sm);
-    if (e != cudaSuccess) return e;
-    long blocks = ((long)a.n_tasks + kColThreads / 32 - 1) / (kColThreads / 32);
-    long cap = nq == 1 ? (long)sms * per_sm : ((long)sms * per_sm * 2 + nq - 1) / nq;
-    if (cap < 1) cap = 1;
-    if (blocks > cap) blocks = cap;
-    if (blocks > 0) kern<<<dim3((unsigned)blocks, (unsigned)nq), kColThreads, 0, s>>>(a);
-    return cudaGetLastError();
 }
 
 template <int VRP>
 cudaError_t run_cols(const ColArgs &a, int sms, int nq, cudaStream_t s) {
-    return a.queries ? run_cols_k<VRP, true>(a, sms, nq, s) : run_cols_k<VRP, false>(a, sms, nq, s);
+    static LaunchCache cache, cache_multi;
+    int per_sm = 1;
+    if (!a.queries) {
+        auto kern = k_resident_cols<VRP>;
+        cudaError_t e = cache.blocks_per_sm(kern, kColThreads, 0, -1, &per_sm);
+        if (e != cudaSuccess) return e;
+        long blocks = ((long)a.n_tasks + kColThreads / 32 - 1) / (kColThreads / 32);
+        if (blocks > (long)sms * per_sm) blocks = (long)sms * per_sm;
+        if (blocks > 0) kern<<<(unsigned)blocks, kColThreads, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    if (a.nq != nq || a.q_per_group < 1) return cudaErrorInvalidValue;
+    auto kern = k_resident_cols_multi<VRP>;
+    cudaError_t e = cache_multi.blocks_per_sm(kern, kColThreads, 0, -1, &per_sm);
+    if (e != cudaSuccess) return e;
+    const long tiles = (long)((nq + a.q_per_group - 1) / a.q_per_group) * a.n_tasks;
+    long blocks = (tiles + kColThreads / 32 - 1) / (kColThreads / 32);
+    if (blocks > (long)sms * per_sm) blocks = (long)sms * per_sm;
+    if (blocks > 0) kern<<<(unsigned)blocks, kColThreads, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace

@@ -82,6 +82,8 @@ struct Request {
     int t = 0;
     int path = -1;   // resolved once, at admission
     int vrp = 0;     // its K^T layout
+    int group = -1;  // >= 0: runs with the other requests of this key in one multi-query
+                     // launch (column-split solver: layout and cost split); -1: alone
     double t_submit = 0, t_done = 0;
     int state = 0;  // 0 queued, 1 running, 2 finished
     int code = SWMD_OK;
@@ -100,6 +102,17 @@ struct ServerSlot {
     std::shared_ptr<Request> req;
     size_t arena_bytes = 0;
     void *arena_ptr = nullptr;
+    int lane = -1;            // the batch lane running it (-1: its own stream)
+};
+
+// A stream on which a group of requests runs as one batched launch sequence, with
+// the device and pinned host copies of its per-query argument arrays.
+struct BatchLane {
+    cudaStream_t stream = nullptr;
+    char *d_args = nullptr;
+    char *h_args = nullptr;
+    size_t args_bytes = 0;
+    int outstanding = 0;      // members not yet finished (0: free)
 };
 
 size_t query_bytes(swmd_corpus *c, int vrp, int path) {
@@ -115,6 +128,7 @@ struct swmd_server {
     swmd_corpus *c = nullptr;
     swmd_serve_config cfg{};
     std::vector<ServerSlot> slots;
+    std::vector<BatchLane> lanes;
     Arena arena;
     char *arena_mem = nullptr;
     std::mutex m;
@@ -147,7 +161,98 @@ void finish(swmd_server *S, ServerSlot &sl, int code, const std::string &err) {
     S->t_last = R.t_done;
     if (sl.arena_ptr) S->arena.release(sl.arena_ptr, sl.arena_bytes);
     sl.arena_ptr = nullptr;
+    if (sl.lane >= 0) S->lanes[(size_t)sl.lane].outstanding--;
+    sl.lane = -1;
     sl.req.reset();
+}
+
+size_t up256(size_t n) { return (n + 255) & ~size_t(255); }
+size_t lane_args_bytes(int n) {
+    return up256(sizeof(PrepArgs) * n) + up256(sizeof(CostArgs) * n) + up256(sizeof(ResidentArgs) * n);
+}
+
+// Launches a group of admitted requests (one column-split layout and cost split) on
+// a batch lane: their queries are staged, then one batched parameter launch, one
+// batched cost launch and one multi-query solver launch run them all; each slot's
+// distances and status come back to its pinned staging and its event marks the end.
+int launch_group(swmd_server *S, int li, const std::vector<ServerSlot *> &members) {
+    swmd_corpus *c = S->c;
+    BatchLane &L = S->lanes[(size_t)li];
+    const int n = (int)members.size();
+    const int kprec = c->opt.k_precision;
+    const int vrp = members[0]->req->vrp;
+    const size_t kbytes = (size_t)c->Vu * vrp * kprec_bytes(kprec);
+    PrepArgs *hp = reinterpret_cast<PrepArgs *>(L.h_args);
+    CostArgs *hc = reinterpret_cast<CostArgs *>(L.h_args + up256(sizeof(PrepArgs) * n));
+    ResidentArgs *hr = reinterpret_cast<ResidentArgs *>(L.h_args + up256(sizeof(PrepArgs) * n) +
+                                                        up256(sizeof(CostArgs) * n));
+    const size_t off_c = up256(sizeof(PrepArgs) * n), off_r = off_c + up256(sizeof(CostArgs) * n);
+    int split = 0;
+    for (int i = 0; i < n; ++i) {
+        ServerSlot &sl = *members[i];
+        auto &R = *sl.req;
+        char *p = static_cast<char *>(sl.arena_ptr);
+        sl.ws.KT = p;
+        sl.ws.KMT = p + up256(kbytes);
+        sl.ws.u = nullptr;
+        sl.ws.v = nullptr;
+        sl.lane = li;
+        std::memcpy(sl.h_q, R.ids.data(), sizeof(int32_t) * R.vr);
+        std::memcpy(sl.h_r, R.r.data(), sizeof(float) * R.vr);
+        SWMD_CK(cudaMemcpyAsync(sl.ws.q_in, sl.h_q, sizeof(int32_t) * R.vr, cudaMemcpyHostToDevice, L.stream));
+        SWMD_CK(cudaMemcpyAsync(sl.ws.r_in, sl.h_r, sizeof(float) * R.vr, cudaMemcpyHostToDevice, L.stream));
+        PrepArgs &pa = hp[i];
+        pa = PrepArgs{};
+        pa.qp = sl.ws.qp;
+        pa.src_ids = sl.ws.q_in;
+        pa.src_r = sl.ws.r_in;
+        pa.q_ids = sl.ws.q_ids;
+        pa.r = sl.ws.r;
+        pa.out = sl.ws.out;
+        pa.status = sl.ws.status;
+        pa.lambda = R.lambda;
+        pa.vr = R.vr;
+        pa.vrp_cap = vrp;
+        int s_ = 0, n_ = 0;
+        resident_settings(c, R.vr, kprec, &s_, &n_, &split);
+        CostArgs &ca = hc[i];
+        ca = CostArgs{};
+        ca.E = c->E;
+        ca.d4 = c->d4;
+        ca.used = c->used;
+        ca.Vu = c->Vu;
+        ca.q_ids = sl.ws.q_ids;
+        ca.qp = sl.ws.qp;
+        ca.V = c->V;
+        ca.shift = c->opt.column_shift ? 1 : 0;
+        ca.split = split;
+        ca.KT = sl.ws.KT;
+        ca.KMT = sl.ws.KMT;
+        IterArgs ia{};
+        ia.doc_ptr = c->doc_ptr;
+        ia.nz = c->nz;
+        ia.KT = sl.ws.KT;
+        ia.KMT = sl.ws.KMT;
+        ia.r = sl.ws.r;
+        ia.doc_orig = c->doc_orig;
+        ia.qp = sl.ws.qp;
+        ia.N = c->Nl;
+        ia.first = 1;
+        hr[i] = ResidentArgs{ia, R.t};
+    }
+    SWMD_CK(cudaMemcpyAsync(L.d_args, L.h_args, lane_args_bytes(n), cudaMemcpyHostToDevice, L.stream));
+    SWMD_CK(launch_prep_batch(reinterpret_cast<const PrepArgs *>(L.d_args), n, c->V, L.stream));
+    SWMD_CK(launch_cost_batch(hc[0], vrp, kprec, n, reinterpret_cast<const CostArgs *>(L.d_args + off_c), L.stream));
+    const Mapping m = walk_mapping(c, vrp, SWMD_PATH_RESIDENT);
+    int rc = run_resident_batch(c, hr[0], m, kprec, members[0]->req->vr, n,
+                                reinterpret_cast<const ResidentArgs *>(L.d_args + off_r), L.stream);
+    if (rc) return rc;
+    for (ServerSlot *sl : members) {
+        SWMD_CK(cudaMemcpyAsync(sl->h_out, sl->ws.out, sizeof(double) * c->Nl, cudaMemcpyDeviceToHost, L.stream));
+        SWMD_CK(cudaMemcpyAsync(sl->h_status, sl->ws.status, sizeof(int), cudaMemcpyDeviceToHost, L.stream));
+        SWMD_CK(cudaEventRecord(sl->done, L.stream));
+    }
+    return SWMD_OK;
 }
 
 // Launches one admitted request on its slot.  Returns an SWMD code.
@@ -195,30 +300,70 @@ void worker_main(swmd_server *S) {
             S->cv_work.wait(lk);
             continue;
         }
-        // admit: fill free slots while the arena has room for the next request
+        // admit: fill free slots while the arena has room.  Requests on the
+        // column-split solver go to a free batch lane together with every pending
+        // request of the same group key (one multi-query launch); the others run
+        // alone on their slot's stream.
         std::vector<ServerSlot *> launched;
+        std::vector<std::pair<int, std::vector<ServerSlot *>>> groups;   // (lane, members)
         if (!S->stopping) {
-            for (auto &sl : S->slots) {
-                if (sl.req || S->pending.empty()) continue;
-                auto R = S->pending.front();
+            size_t next_slot = 0;
+            auto free_slot = [&]() -> ServerSlot * {
+                while (next_slot < S->slots.size() && S->slots[next_slot].req) ++next_slot;
+                return next_slot < S->slots.size() ? &S->slots[next_slot] : nullptr;
+            };
+            int lane = -1;
+            for (size_t li = 0; li < S->lanes.size(); ++li)
+                if (S->lanes[li].outstanding == 0) { lane = (int)li; break; }
+            int gkey = -1;
+            std::vector<ServerSlot *> members;
+            bool blocked = false;   // a request alone could not be admitted: keep FIFO order for them
+            for (auto it = S->pending.begin(); it != S->pending.end();) {
+                auto R = *it;
                 if (R->path < 0) {   // the path and layout, once (options cannot change while served)
                     std::lock_guard<std::mutex> cl(S->c->mu);
                     R->path = resolve_path(S->c, R->vr);
                     R->vrp = choose_mapping(S->c, R->vr, R->path).vrp;
+                    if (R->path == SWMD_PATH_RESIDENT &&
+                        resident_solver(S->c, R->vr, S->c->opt.k_precision) == kSolverCols) {
+                        int s_ = 0, n_ = 0, cs_ = 0;
+                        resident_settings(S->c, R->vr, S->c->opt.k_precision, &s_, &n_, &cs_);
+                        R->group = R->vrp * 8 + cs_;
+                    }
                 }
+                const bool grouped = R->group >= 0;
+                if (grouped && (lane < 0 || (gkey >= 0 && R->group != gkey))) { ++it; continue; }
+                if (!grouped && blocked) { ++it; continue; }
+                ServerSlot *sl = free_slot();
+                if (!sl) break;
                 const size_t need = query_bytes(S->c, R->vrp, R->path);
                 void *mem = S->arena.alloc(need);
-                if (!mem) break;   // admission waits for memory to free up
-                S->pending.pop_front();
-                sl.req = R;
-                sl.arena_ptr = mem;
-                sl.arena_bytes = need;
+                if (!mem) {   // admission waits for memory to free up
+                    if (grouped) { ++it; continue; }
+                    blocked = true;
+                    ++it;
+                    continue;
+                }
+                it = S->pending.erase(it);
+                sl->req = R;
+                sl->arena_ptr = mem;
+                sl->arena_bytes = need;
                 R->state = 1;
-                launched.push_back(&sl);
+                if (grouped) {
+                    gkey = R->group;
+                    members.push_back(sl);
+                } else {
+                    launched.push_back(sl);
+                }
+            }
+            if (!members.empty()) {
+                S->lanes[(size_t)lane].outstanding = (int)members.size();
+                groups.emplace_back(lane, members);
             }
         }
-        if (!launched.empty()) {
-            S->batches++;
+        if (!launched.empty() || !groups.empty()) {
+            S->batches += (int64_t)launched.size() + (int64_t)groups.size();
+            for (auto &g : groups) S->admitted += (int64_t)g.second.size();
             S->admitted += (int64_t)launched.size();
         }
         lk.unlock();
@@ -226,6 +371,17 @@ void worker_main(swmd_server *S) {
         for (auto *sl : launched) {
             const int rc = launch_on_slot(S, *sl);
             if (rc) failed.push_back({sl, rc});
+        }
+        for (auto &g : groups) {
+            int rc;
+            {
+                std::lock_guard<std::mutex> cl(S->c->mu);
+                rc = launch_group(S, g.first, g.second);
+            }
+            if (rc) {
+                cudaStreamSynchronize(S->lanes[(size_t)g.first].stream);
+                for (ServerSlot *sl : g.second) failed.push_back({sl, rc});
+            }
         }
         // poll in-flight slots
         std::vector<ServerSlot *> ready;
@@ -249,7 +405,7 @@ void worker_main(swmd_server *S) {
         if (!failed.empty() || !ready.empty()) S->cv_done.notify_all();
         bool busy = false;
         for (auto &sl : S->slots) busy |= (bool)sl.req;
-        if (busy && ready.empty() && launched.empty()) {
+        if (busy && ready.empty() && launched.empty() && groups.empty()) {
             lk.unlock();
             std::this_thread::sleep_for(std::chrono::microseconds(
                 std::max(5, std::min(S->cfg.max_wait_us, 200))));
@@ -473,7 +629,9 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
                 // (each gathers its own K^T); there the group's queries run one after
                 // another (still one graph, no host round trips).  Smaller corpora run
                 // the group as one batched cost and one batched solver launch.
-                const int step = c->Nl >= kAutoResidentDocs ? 1 : ng;
+                // The column-split solver walks the whole group in one launch (its
+                // tiles keep one query group's K^T in L2 at a time).
+                const int step = (c->Nl >= kAutoResidentDocs && std::get<1>(gstart[gi].first) != kSolverCols) ? 1 : ng;
                 for (int j0 = 0; j0 < ng; j0 += step) {
                     const int nj = std::min(step, ng - j0);
                     SWMD_CK(launch_cost_batch(cost_g[g0 + j0], v, kprec, nj,
@@ -577,6 +735,11 @@ int swmd_serve_start(swmd_corpus *c, const swmd_serve_config *cfg_in, swmd_serve
             if (sl.done) cudaEventDestroy(sl.done);
             cudaFreeHost(sl.h_q); cudaFreeHost(sl.h_r); cudaFreeHost(sl.h_out); cudaFreeHost(sl.h_status);
         }
+        for (auto &L : S->lanes) {
+            if (L.stream) cudaStreamDestroy(L.stream);
+            cudaFree(L.d_args);
+            cudaFreeHost(L.h_args);
+        }
         cudaFree(S->arena_mem);
         delete S;
         return code;
@@ -613,6 +776,14 @@ int swmd_serve_start(swmd_corpus *c, const swmd_serve_config *cfg_in, swmd_serve
     {
         std::lock_guard<std::mutex> cl(c->mu);
         ++c->servers;
+    }
+    S->lanes.resize(2);
+    for (auto &L : S->lanes) {
+        L.args_bytes = lane_args_bytes(cfg.max_batch);
+        e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaMalloc(&L.d_args, L.args_bytes);
+        if (e == cudaSuccess) e = cudaMallocHost(&L.h_args, L.args_bytes);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "swmd_serve_start: batch lane"));
     }
     S->worker = std::thread(worker_main, S);
     *out = S;
@@ -724,6 +895,14 @@ int swmd_serve_stop(swmd_server *S) {
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.done) cudaEventDestroy(sl.done);
         cudaFreeHost(sl.h_q); cudaFreeHost(sl.h_r); cudaFreeHost(sl.h_out); cudaFreeHost(sl.h_status);
+    }
+    for (auto &L : S->lanes) {
+        if (L.stream) {
+            cudaStreamSynchronize(L.stream);
+            cudaStreamDestroy(L.stream);
+        }
+        cudaFree(L.d_args);
+        cudaFreeHost(L.h_args);
     }
     cudaFree(S->arena_mem);
     delete S;

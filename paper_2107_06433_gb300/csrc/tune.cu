@@ -8,6 +8,7 @@
 // itself instead of fixed by hand (the paper picks its mappings by hand for each
 // machine, Sections IV-V).
 #include <algorithm>
+#include <chrono>
 #include <cstdint>
 #include <cstring>
 #include <set>
@@ -165,5 +166,90 @@ int swmd_autotune(swmd_corpus *c, int32_t v_r, int32_t reps, swmd_tune_result *o
     out->cost_split = std::get<2>(best);
     out->best_ms = chosen == SWMD_PATH_FUSED ? fused_ms : best_ms;
     out->path = chosen;
+    return SWMD_OK;
+}
+
+int swmd_autotune_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr, const int32_t *h_word_ids,
+                        const float *h_weights, const float *h_lambdas, int32_t max_iter, int32_t reps,
+                        swmd_batch_tune_result *out) {
+    if (!c || !out || n_queries < 1 || !q_ptr || !h_word_ids || !h_weights || !h_lambdas)
+        return set_error(SWMD_EINVAL, "swmd_autotune_batch: bad arguments");
+    if (reps < 1) return set_error(SWMD_EINVAL, "swmd_autotune_batch: reps must be >= 1");
+    std::memset(out, 0, sizeof(*out));
+    const int kprec = c->opt.k_precision;
+    // the column-split layouts the batch holds
+    std::set<int> layouts;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        if (c->servers > 0)
+            return set_error(SWMD_EINVAL, "swmd_autotune_batch: a server is attached to the corpus");
+        for (int32_t i = 0; i < n_queries; ++i) {
+            const int64_t n = q_ptr[i + 1] - q_ptr[i];
+            if (n < 1 || n > INT32_MAX) return set_error(SWMD_EINVAL, "swmd_autotune_batch: bad q_ptr");
+            std::vector<int32_t> ids((size_t)n);
+            std::vector<float> r((size_t)n);
+            int32_t vr = 0;
+            int rc = swmd_select(c->V, (int32_t)n, h_word_ids + q_ptr[i], h_weights + q_ptr[i], ids.data(),
+                                 r.data(), &vr);
+            if (rc) return rc;
+            if (vr > c->opt.max_vr) continue;   // swmd_query_batch reports it
+            if (resolve_path(c, vr) == SWMD_PATH_RESIDENT && resident_solver(c, vr, kprec) == kSolverCols)
+                layouts.insert(cols_vrp(vr));
+        }
+        for (int v : layouts) c->tuned_qpt.erase(std::make_pair(v, kprec));
+    }
+    std::vector<double> sink((size_t)n_queries * std::max(c->Nl, 1));
+    auto time_batch = [&]() -> float {
+        // the first call of a shape captures its graph: untimed
+        int rc = swmd_query_batch(c, n_queries, q_ptr, h_word_ids, h_weights, h_lambdas, max_iter, sink.data());
+        if (rc && rc != SWMD_ENUMERIC) return -1.0f;
+        std::vector<float> ms;
+        for (int k = 0; k < reps; ++k) {
+            const auto t0 = std::chrono::steady_clock::now();
+            rc = swmd_query_batch(c, n_queries, q_ptr, h_word_ids, h_weights, h_lambdas, max_iter, sink.data());
+            if (rc && rc != SWMD_ENUMERIC) return -1.0f;
+            ms.push_back(std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count());
+        }
+        std::sort(ms.begin(), ms.end());
+        return ms[ms.size() / 2];
+    };
+    auto set_tile = [&](int v, int qpt) {
+        std::lock_guard<std::mutex> lk(c->mu);
+        if (qpt > 0) c->tuned_qpt[std::make_pair(v, kprec)] = qpt;
+        else c->tuned_qpt.erase(std::make_pair(v, kprec));
+        clear_graphs(c);   // captured batches hold the tile size they were captured with
+    };
+    out->default_ms = time_batch();
+    ++out->candidates;
+    if (out->default_ms < 0.0f) return set_error(SWMD_ECUDA, "swmd_autotune_batch: %s", swmd_last_error());
+    float best_all = out->default_ms;
+    int li = 0;
+    for (int v : layouts) {
+        int best = 0;
+        float best_ms = best_all;
+        for (int qpt : {1, 2, 4, 8}) {
+            set_tile(v, qpt);
+            const float ms = time_batch();
+            ++out->candidates;
+            if (ms > 0.0f && ms < best_ms) best_ms = ms, best = qpt;
+        }
+        const int chosen = best > 0 ? best : 0;
+        set_tile(v, chosen);
+        {
+            std::lock_guard<std::mutex> lk(c->mu);
+            if (chosen == 0) {   // the default stood: record the size it resolved to
+                const int d = cols_queries_per_group(c, v, kprec);
+                c->tuned_qpt[std::make_pair(v, kprec)] = d;
+            }
+            if (li < 4) {
+                out->vrp[li] = v;
+                out->queries_per_tile[li] = cols_queries_per_group(c, v, kprec);
+            }
+        }
+        best_all = best_ms;
+        ++li;
+    }
+    out->layouts = li;
+    out->best_ms = best_all;
     return SWMD_OK;
 }

@@ -1,7 +1,7 @@
 """The column-split register solver against the FP64 oracle, through the C ABI.
 
 The solver keeps each document's K^T rows in registers for all t iterations, split
-by columns over a team of VRP / 4 lanes (resident_cols.cu).  It runs on corpora
+by columns over a team of VRP / 8 lanes, 4 for 128 columns (resident_cols.cu).  It runs on corpora
 whose documents have at most 32 words, in buckets of 8, 16, 24 or 32 rows; query
 layouts of 16, 32, 64 and 128 columns.  These tests cover every bucket and team
 size, ragged buckets (every document length 1..32), the iteration counts 0, 1 and
@@ -155,3 +155,51 @@ def test_large_workload_sampled():
     ref = oracle.wmd_pairs(E, [(qi, qw)] * len(sel), docs, 1.0, 15)
     assert rel_err(got[sel], ref) <= RTOL
     assert np.all(np.isfinite(got)) and np.all(got > 0)
+
+
+@pytest.mark.parametrize("qpt", [1, 3, 8])
+def test_multi_query_launch_equals_alone_bitwise(short_docs, qpt):
+    """swmd_query_batch runs each column-split layout group as one launch over (query
+    group, document task) tiles; every tile size gives the single queries' bits."""
+    E, C = short_docs
+    corpus = swmd.corpus_from_synth(E, C, path="resident", queries_per_tile=qpt)
+    qs = synth.batch_queries(C.V, 17, 1, 128, seed=60 + qpt)
+    lams = np.linspace(0.5, 3.0, len(qs)).astype(np.float32)
+    batch = swmd.swmd_query_batch(corpus, qs, lams, 15)
+    for i, (qi, qw) in enumerate(qs):
+        np.testing.assert_array_equal(batch[i], swmd.swmd_query(corpus, qi, qw, float(lams[i]), 15))
+    i = 5
+    assert rel_err(batch[i], oracle_wmd(E, C, qs[i][0], qs[i][1], float(lams[i]), 15)) <= RTOL
+
+
+def test_batch_autotuner_picks_a_tile_size(short_docs):
+    E, C = short_docs
+    corpus = swmd.corpus_from_synth(E, C, path="resident")
+    qs = synth.batch_queries(C.V, 12, 4, 40, seed=71)
+    res = swmd.swmd_autotune_batch(corpus, qs, 1.0, 15, reps=1)
+    assert res["layouts"] >= 1 and res["candidates"] >= 1 + 4 * res["layouts"]
+    assert all(q in (1, 2, 4, 8) for q in res["queries_per_tile"])
+    assert res["best_ms"] <= res["default_ms"] * 1.0001
+    batch = swmd.swmd_query_batch(corpus, qs, 1.0, 15)
+    for i in (0, 6, 11):
+        np.testing.assert_array_equal(batch[i], swmd.swmd_query(corpus, qs[i][0], qs[i][1], 1.0, 15))
+
+
+def test_large_workload_batch_and_server_equal_alone():
+    """Six queries of 4..128 words on the 1,000,000-document workload: one batch call
+    (one multi-query launch per layout) and the server (grouped launches) give each
+    query's single-query bits."""
+    E, C, _ = synth.make("large")
+    corpus = swmd.corpus_from_synth(E, C, k_precision="bf16")
+    qs = synth.batch_queries(C.V, 6, 4, 128, seed=91)
+    alone = [swmd.swmd_query(corpus, qi, qw, 1.0, 15) for qi, qw in qs]
+    batch = swmd.swmd_query_batch(corpus, qs, 1.0, 15)
+    for i in range(len(qs)):
+        np.testing.assert_array_equal(batch[i], alone[i])
+    srv = swmd.swmd_serve_start(corpus, max_batch=8, memory_budget=8 << 30)
+    tickets = [swmd.swmd_serve_submit(srv, qi, qw, 1.0, 15) for qi, qw in qs]
+    for tk, ref in zip(tickets, alone):
+        np.testing.assert_array_equal(swmd.swmd_serve_wait(srv, tk, 120000), ref)
+    st = swmd.swmd_serve_stats(srv)
+    srv.stop()
+    assert st["completed"] == len(qs)
