@@ -639,6 +639,14 @@ def serving(swmd, synth, torch, rates=(50.0, 200.0, 1000.0), n=200, E=None, C=No
     res["one_at_a_time_fp32"] = {"qps": one_qps, "p50_ms": float(np.percentile(lat, 50)),
                                  "p99_ms": float(np.percentile(lat, 99))}
     c16 = swmd.corpus_from_synth(E, C, k_precision="bf16")
+    lat16 = []
+    t0 = time.perf_counter()
+    for qi, qw in qs:
+        a = time.perf_counter()
+        swmd.swmd_query(c16, qi, qw, 1.0, 15)
+        lat16.append((time.perf_counter() - a) * 1e3)
+    res["one_at_a_time_bf16"] = {"qps": n / (time.perf_counter() - t0), "p50_ms": float(np.percentile(lat16, 50)),
+                                 "p99_ms": float(np.percentile(lat16, 99))}
     served = {}
     err = 0.0
     for rate in rates:

@@ -103,16 +103,20 @@ struct ServerSlot {
     size_t arena_bytes = 0;
     void *arena_ptr = nullptr;
     int lane = -1;            // the batch lane running it (-1: its own stream)
+    int lane_buf = -1;        // ... and the argument buffer of its group
 };
 
-// A stream on which a group of requests runs as one batched launch sequence, with
-// the device and pinned host copies of its per-query argument arrays.
+// A stream on which groups of requests run as batched launch sequences, one after
+// another in stream order.  Two argument buffers (device and pinned host copies of
+// the per-query argument arrays): a group can be queued behind the running one, so
+// the GPU does not wait while the host collects one group and stages the next.
+constexpr int kLaneDepth = 2;
 struct BatchLane {
     cudaStream_t stream = nullptr;
-    char *d_args = nullptr;
-    char *h_args = nullptr;
+    char *d_args[kLaneDepth] = {};
+    char *h_args[kLaneDepth] = {};
     size_t args_bytes = 0;
-    int outstanding = 0;      // members not yet finished (0: free)
+    int outstanding[kLaneDepth] = {};   // members of the group using each buffer (0: free)
 };
 
 size_t query_bytes(swmd_corpus *c, int vrp, int path) {
@@ -161,8 +165,9 @@ void finish(swmd_server *S, ServerSlot &sl, int code, const std::string &err) {
     S->t_last = R.t_done;
     if (sl.arena_ptr) S->arena.release(sl.arena_ptr, sl.arena_bytes);
     sl.arena_ptr = nullptr;
-    if (sl.lane >= 0) S->lanes[(size_t)sl.lane].outstanding--;
+    if (sl.lane >= 0) S->lanes[(size_t)sl.lane].outstanding[sl.lane_buf]--;
     sl.lane = -1;
+    sl.lane_buf = -1;
     sl.req.reset();
 }
 
@@ -175,16 +180,18 @@ size_t lane_args_bytes(int n) {
 // a batch lane: their queries are staged, then one batched parameter launch, one
 // batched cost launch and one multi-query solver launch run them all; each slot's
 // distances and status come back to its pinned staging and its event marks the end.
-int launch_group(swmd_server *S, int li, const std::vector<ServerSlot *> &members) {
+int launch_group(swmd_server *S, int li, int buf, const std::vector<ServerSlot *> &members) {
     swmd_corpus *c = S->c;
     BatchLane &L = S->lanes[(size_t)li];
+    char *const h_args = L.h_args[buf];
+    char *const d_args = L.d_args[buf];
     const int n = (int)members.size();
     const int kprec = c->opt.k_precision;
     const int vrp = members[0]->req->vrp;
     const size_t kbytes = (size_t)c->Vu * vrp * kprec_bytes(kprec);
-    PrepArgs *hp = reinterpret_cast<PrepArgs *>(L.h_args);
-    CostArgs *hc = reinterpret_cast<CostArgs *>(L.h_args + up256(sizeof(PrepArgs) * n));
-    ResidentArgs *hr = reinterpret_cast<ResidentArgs *>(L.h_args + up256(sizeof(PrepArgs) * n) +
+    PrepArgs *hp = reinterpret_cast<PrepArgs *>(h_args);
+    CostArgs *hc = reinterpret_cast<CostArgs *>(h_args + up256(sizeof(PrepArgs) * n));
+    ResidentArgs *hr = reinterpret_cast<ResidentArgs *>(h_args + up256(sizeof(PrepArgs) * n) +
                                                         up256(sizeof(CostArgs) * n));
     const size_t off_c = up256(sizeof(PrepArgs) * n), off_r = off_c + up256(sizeof(CostArgs) * n);
     int split = 0;
@@ -197,6 +204,7 @@ int launch_group(swmd_server *S, int li, const std::vector<ServerSlot *> &member
         sl.ws.u = nullptr;
         sl.ws.v = nullptr;
         sl.lane = li;
+        sl.lane_buf = buf;
         std::memcpy(sl.h_q, R.ids.data(), sizeof(int32_t) * R.vr);
         std::memcpy(sl.h_r, R.r.data(), sizeof(float) * R.vr);
         SWMD_CK(cudaMemcpyAsync(sl.ws.q_in, sl.h_q, sizeof(int32_t) * R.vr, cudaMemcpyHostToDevice, L.stream));
@@ -240,12 +248,12 @@ int launch_group(swmd_server *S, int li, const std::vector<ServerSlot *> &member
         ia.first = 1;
         hr[i] = ResidentArgs{ia, R.t};
     }
-    SWMD_CK(cudaMemcpyAsync(L.d_args, L.h_args, lane_args_bytes(n), cudaMemcpyHostToDevice, L.stream));
-    SWMD_CK(launch_prep_batch(reinterpret_cast<const PrepArgs *>(L.d_args), n, c->V, L.stream));
-    SWMD_CK(launch_cost_batch(hc[0], vrp, kprec, n, reinterpret_cast<const CostArgs *>(L.d_args + off_c), L.stream));
+    SWMD_CK(cudaMemcpyAsync(d_args, h_args, lane_args_bytes(n), cudaMemcpyHostToDevice, L.stream));
+    SWMD_CK(launch_prep_batch(reinterpret_cast<const PrepArgs *>(d_args), n, c->V, L.stream));
+    SWMD_CK(launch_cost_batch(hc[0], vrp, kprec, n, reinterpret_cast<const CostArgs *>(d_args + off_c), L.stream));
     const Mapping m = walk_mapping(c, vrp, SWMD_PATH_RESIDENT);
     int rc = run_resident_batch(c, hr[0], m, kprec, members[0]->req->vr, n,
-                                reinterpret_cast<const ResidentArgs *>(L.d_args + off_r), L.stream);
+                                reinterpret_cast<const ResidentArgs *>(d_args + off_r), L.stream);
     if (rc) return rc;
     for (ServerSlot *sl : members) {
         SWMD_CK(cudaMemcpyAsync(sl->h_out, sl->ws.out, sizeof(double) * c->Nl, cudaMemcpyDeviceToHost, L.stream));
@@ -305,16 +313,21 @@ void worker_main(swmd_server *S) {
         // request of the same group key (one multi-query launch); the others run
         // alone on their slot's stream.
         std::vector<ServerSlot *> launched;
-        std::vector<std::pair<int, std::vector<ServerSlot *>>> groups;   // (lane, members)
+        std::vector<std::pair<std::pair<int, int>, std::vector<ServerSlot *>>> groups;   // ((lane, buffer), members)
         if (!S->stopping) {
             size_t next_slot = 0;
             auto free_slot = [&]() -> ServerSlot * {
                 while (next_slot < S->slots.size() && S->slots[next_slot].req) ++next_slot;
                 return next_slot < S->slots.size() ? &S->slots[next_slot] : nullptr;
             };
-            int lane = -1;
-            for (size_t li = 0; li < S->lanes.size(); ++li)
-                if (S->lanes[li].outstanding == 0) { lane = (int)li; break; }
+            int lane = -1, lane_buf = -1;
+            for (size_t li = 0; li < S->lanes.size() && lane < 0; ++li)
+                for (int b = 0; b < kLaneDepth; ++b)
+                    if (S->lanes[li].outstanding[b] == 0) {
+                        lane = (int)li;
+                        lane_buf = b;
+                        break;
+                    }
             int gkey = -1;
             std::vector<ServerSlot *> members;
             bool blocked = false;   // a request alone could not be admitted: keep FIFO order for them
@@ -357,8 +370,8 @@ void worker_main(swmd_server *S) {
                 }
             }
             if (!members.empty()) {
-                S->lanes[(size_t)lane].outstanding = (int)members.size();
-                groups.emplace_back(lane, members);
+                S->lanes[(size_t)lane].outstanding[lane_buf] = (int)members.size();
+                groups.emplace_back(std::make_pair(lane, lane_buf), members);
             }
         }
         if (!launched.empty() || !groups.empty()) {
@@ -376,10 +389,10 @@ void worker_main(swmd_server *S) {
             int rc;
             {
                 std::lock_guard<std::mutex> cl(S->c->mu);
-                rc = launch_group(S, g.first, g.second);
+                rc = launch_group(S, g.first.first, g.first.second, g.second);
             }
             if (rc) {
-                cudaStreamSynchronize(S->lanes[(size_t)g.first].stream);
+                cudaStreamSynchronize(S->lanes[(size_t)g.first.first].stream);
                 for (ServerSlot *sl : g.second) failed.push_back({sl, rc});
             }
         }
@@ -737,8 +750,10 @@ int swmd_serve_start(swmd_corpus *c, const swmd_serve_config *cfg_in, swmd_serve
         }
         for (auto &L : S->lanes) {
             if (L.stream) cudaStreamDestroy(L.stream);
-            cudaFree(L.d_args);
-            cudaFreeHost(L.h_args);
+            for (int b = 0; b < kLaneDepth; ++b) {
+                cudaFree(L.d_args[b]);
+                cudaFreeHost(L.h_args[b]);
+            }
         }
         cudaFree(S->arena_mem);
         delete S;
@@ -777,12 +792,16 @@ int swmd_serve_start(swmd_corpus *c, const swmd_serve_config *cfg_in, swmd_serve
         std::lock_guard<std::mutex> cl(c->mu);
         ++c->servers;
     }
-    S->lanes.resize(2);
+    // One batch lane: a group of queries of one layout fills the GPU by itself, and
+    // two groups side by side would only slow each other down.
+    S->lanes.resize(1);
     for (auto &L : S->lanes) {
         L.args_bytes = lane_args_bytes(cfg.max_batch);
         e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaMalloc(&L.d_args, L.args_bytes);
-        if (e == cudaSuccess) e = cudaMallocHost(&L.h_args, L.args_bytes);
+        for (int b = 0; b < kLaneDepth && e == cudaSuccess; ++b) {
+            e = cudaMalloc(&L.d_args[b], L.args_bytes);
+            if (e == cudaSuccess) e = cudaMallocHost(&L.h_args[b], L.args_bytes);
+        }
         if (e != cudaSuccess) return bail(cuda_fail(e, "swmd_serve_start: batch lane"));
     }
     S->worker = std::thread(worker_main, S);
@@ -901,8 +920,10 @@ int swmd_serve_stop(swmd_server *S) {
             cudaStreamSynchronize(L.stream);
             cudaStreamDestroy(L.stream);
         }
-        cudaFree(L.d_args);
-        cudaFreeHost(L.h_args);
+        for (int b = 0; b < kLaneDepth; ++b) {
+            cudaFree(L.d_args[b]);
+            cudaFreeHost(L.h_args[b]);
+        }
     }
     cudaFree(S->arena_mem);
     delete S;
