@@ -17,7 +17,8 @@
  *     keep them.  Pointers named d_* are device pointers on the corpus's GPU,
  *     owned by the caller, that must stay valid until the stream work of the
  *     call has completed.
- *   - A corpus (and a server) owns every device allocation it makes.  Calls on
+ *   - A corpus (and a server) owns every device allocation it makes (through
+ *     swmd_set_allocator's functions when set, else cudaMalloc).  Calls on
  *     one corpus are not thread-safe unless stated; use one server or one
  *     corpus per thread.
  *   - `stream` arguments are cudaStream_t values passed as void*; NULL means the
@@ -123,6 +124,25 @@ typedef struct swmd_options {
                               swmd_autotune_batch choice, else as many (1..8) as keep
                               their K^T and KM^T within a quarter of the L2 cache */
 } swmd_options;
+
+/* ------------------------------------------------------------------ device memory */
+/* Device memory of corpora and servers.  By default the library takes it with
+ * cudaMalloc and returns it with cudaFree.  swmd_set_allocator makes every corpus
+ * created afterwards -- and that corpus's servers, batch and 1-to-1 pair workspaces
+ * -- take it from alloc(bytes, device, stream, user) and return it with
+ * release(ptr, bytes, device, stream, user) instead (the Python binding passes
+ * PyTorch's caching allocator).  alloc returns NULL when it cannot serve the
+ * request (the call then fails with SWMD_ENOMEM) and must return 256-byte aligned
+ * device memory of `device`; `stream` (a cudaStream_t) is the corpus's stream, on
+ * which the memory is used.  A corpus keeps the allocator it was created with until
+ * it is destroyed.  Both NULL restores cudaMalloc / cudaFree; one NULL is
+ * SWMD_EINVAL.  The library calls them from the calling thread of the entry point
+ * that allocates or frees (swmd_create_corpus, swmd_query_batch, swmd_wmd_pairs*,
+ * swmd_serve_start / _stop, swmd_destroy_corpus, and option changes that grow the
+ * workspace), never from a server's worker thread.  The paper has no counterpart. */
+typedef void *(*swmd_alloc_fn)(size_t bytes, int32_t device, void *stream, void *user);
+typedef void (*swmd_free_fn)(void *ptr, size_t bytes, int32_t device, void *stream, void *user);
+SWMD_API int swmd_set_allocator(swmd_alloc_fn alloc, swmd_free_fn release, void *user);
 
 /* Fills *opt with the defaults listed above. */
 SWMD_API void swmd_default_options(swmd_options *opt);
@@ -353,6 +373,18 @@ SWMD_API int swmd_wmd_pairs_device(swmd_corpus *corpus, int32_t n_pairs, const i
                                    const float *d_c, int32_t max_q_words, int32_t max_x_words,
                                    float lambda, int32_t max_iter, float tol, double *d_out,
                                    int32_t *d_iters, int32_t *d_status, void *stream);
+
+/* Debug builds only (the library built with build(debug=True), whose kernels check
+ * the corpus indices they follow and report one outside its array in the status
+ * word instead of reading there): overwrites the compact word id of one nonzero of
+ * the corpus's device copy with `value`, to test those checks from the host.
+ *   what 0: nonzero `index` (0 .. nnz-1) of the document-major copy (the resident
+ *   solvers read it); what 1: entry `index` of the sliced copy (the per-iteration
+ *   walks read it; its padding entries too).
+ * A later query whose kernels meet the planted id returns SWMD_EINVAL naming the
+ * failed bounds check.  Release builds return SWMD_EINVAL and change nothing.
+ * Synchronous.  A test hook: the paper has no counterpart. */
+SWMD_API int swmd_debug_plant(swmd_corpus *corpus, int32_t what, int64_t index, int32_t value);
 
 /* Copies a workspace array to host memory for inspection (tests):
  *   what 0: K^T  [V_used][v_r] as float (FP32/BF16/FP16 widened)

@@ -17,7 +17,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libswmd.so")
+# SWMD_DEBUG=1 loads the debug library (build(debug=True): kernels with bounds checks)
+LIB_PATH = os.path.join(_HERE, "_build_debug" if os.environ.get("SWMD_DEBUG") == "1" else "_build", "libswmd.so")
 
 SWMD_OK, SWMD_EINVAL, SWMD_ENOMEM, SWMD_ECUDA, SWMD_ETIMEDOUT, SWMD_ENUMERIC, SWMD_ESTOPPED = range(7)
 K_FP32, K_BF16, K_FP16 = 0, 1, 2
@@ -83,6 +84,7 @@ _lib = None
 P = ctypes.c_void_p
 _SIGS = {
     "swmd_default_options": (None, [P]),
+    "swmd_set_allocator": (ctypes.c_int, [P, P, P]),
     "swmd_last_error": (ctypes.c_char_p, []),
     "swmd_select": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, P, P, P, P, P]),
     "swmd_create_corpus": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, P, P, P,
@@ -103,6 +105,7 @@ _SIGS = {
     "swmd_partition_documents": (ctypes.c_int, [ctypes.c_int32, P, ctypes.c_int32, P]),
     "swmd_query_noalloc": (ctypes.c_int, [P, P, P, ctypes.c_int32, ctypes.c_float, ctypes.c_int32,
                                           P, P, P]),
+    "swmd_debug_plant": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32]),
     "swmd_debug_read": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P]),
     "swmd_query_batch": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, P, ctypes.c_int32, P]),
     "swmd_autotune": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P]),
@@ -166,6 +169,50 @@ def _stream(s):
     if isinstance(s, int):
         return P(s)
     return P(s.cuda_stream)
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.c_void_p,
+                             ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.c_void_p,
+                            ctypes.c_void_p)
+_allocator_refs = None   # keeps the C callbacks alive while the library may call them
+
+
+def swmd_set_allocator(alloc=None, release=None):
+    """Device memory of corpora created from now on: alloc(bytes, device, stream) -> int
+    pointer (0 on failure) and release(ptr, bytes, device, stream), Python callables;
+    both None restores cudaMalloc / cudaFree."""
+    global _allocator_refs
+    if alloc is None and release is None:
+        _err(lib().swmd_set_allocator(None, None, None), "swmd_set_allocator")
+        _allocator_refs = None
+        return
+
+    def c_alloc(nbytes, device, stream, user):
+        return int(alloc(int(nbytes), int(device), stream or 0)) or None
+
+    def c_free(ptr, nbytes, device, stream, user):
+        release(int(ptr), int(nbytes), int(device), stream or 0)
+
+    refs = (_ALLOC_FN(c_alloc), _FREE_FN(c_free)) if alloc is not None and release is not None else \
+        (_ALLOC_FN(c_alloc) if alloc is not None else None, _FREE_FN(c_free) if release is not None else None)
+    _err(lib().swmd_set_allocator(ctypes.cast(refs[0], P) if refs[0] else None,
+                                  ctypes.cast(refs[1], P) if refs[1] else None, None), "swmd_set_allocator")
+    _allocator_refs = refs
+
+
+def use_torch_allocator():
+    """Routes the library's device memory (corpora created from now on) through
+    PyTorch's caching allocator."""
+    import torch
+
+    def alloc(nbytes, device, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, device, stream)
+
+    def release(ptr, nbytes, device, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    swmd_set_allocator(alloc, release)
 
 
 def swmd_default_options(**kw) -> swmd_options:
@@ -343,6 +390,13 @@ def swmd_resolve_path(corpus: Corpus, v_r: int) -> str:
     out = ctypes.c_int32()
     _err(lib().swmd_resolve_path(corpus.handle, int(v_r), ctypes.byref(out)), "swmd_resolve_path")
     return _PATH_NAMES[out.value]
+
+
+def swmd_debug_plant(corpus: Corpus, what: str, index: int, value: int):
+    """Debug builds: overwrite the word id of one nonzero ("nz": document-major copy,
+    "slices": the sliced copy) to test the kernels' bounds checks."""
+    _err(lib().swmd_debug_plant(corpus.handle, {"nz": 0, "slices": 1}[what], int(index), int(value)),
+         "swmd_debug_plant")
 
 
 def swmd_debug_read(corpus: Corpus, what: str, v_r: int = 0) -> np.ndarray:

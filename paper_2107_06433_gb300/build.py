@@ -18,6 +18,12 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libswmd.so")
+# The debug library: the translation units whose kernels follow corpus indices (and
+# the C ABI layer, for its debug-only hook) compiled with SWMD_DEBUG_CHECKS=1, linked
+# with the release objects of the rest.
+DEBUG_BUILD = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(DEBUG_BUILD, "libswmd.so")
+DEBUG_SOURCES = ("api.cu", "resident_cols.cu", "walk_fused.cu", "walk_final.cu", "walk_plain.cu")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",
@@ -43,23 +49,30 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
-    os.makedirs(os.path.join(BUILD, "obj"), exist_ok=True)
+def build(force: bool = False, jobs: int | None = None, verbose: bool = False, debug: bool = False) -> str:
+    """Builds libswmd.so (debug=True: the debug library, DEBUG_LIB) and returns its path."""
+    if debug:
+        build(force, jobs, verbose)   # the release objects it links with
+    out_dir = DEBUG_BUILD if debug else BUILD
+    os.makedirs(os.path.join(out_dir, "obj"), exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = _headers()
     objs = []
     todo = []
     for src in sources:
-        obj = os.path.join(BUILD, "obj", os.path.basename(src) + ".o")
+        name = os.path.basename(src)
+        own = not debug or name in DEBUG_SOURCES
+        obj = os.path.join(out_dir if own else BUILD, "obj", name + ".o")
         objs.append(obj)
-        if force or _stale(obj, [src] + headers + [__file__]):
+        if own and (force or _stale(obj, [src] + headers + [__file__])):
             todo.append((src, obj))
     cc = nvcc()
+    extra = ["-DSWMD_DEBUG_CHECKS=1"] if debug else []
 
     def compile_one(item):
         src, obj = item
         tmp = obj + ".%d.tmp" % os.getpid()
-        cmd = [cc, *ARCH, *FLAGS, "-c", src, "-o", tmp]
+        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", tmp]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         p = subprocess.run(cmd, capture_output=True, text=True)
@@ -74,17 +87,18 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
             for log in ex.map(compile_one, todo):
                 if verbose and log:
                     print(log)
-    if force or todo or _stale(LIB, objs):
-        tmp = LIB + ".%d.tmp" % os.getpid()
+    lib = DEBUG_LIB if debug else LIB
+    if force or todo or _stale(lib, objs):
+        tmp = lib + ".%d.tmp" % os.getpid()
         cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fvisibility=hidden",
                "-lpthread", "-Xlinker", "--no-undefined"]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
             raise RuntimeError("link failed:\n" + p.stderr[-6000:])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

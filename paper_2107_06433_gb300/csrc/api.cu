@@ -37,18 +37,19 @@ int cuda_fail(cudaError_t e, const char *what) {
 namespace {
 
 template <class T>
-int dev_alloc(T **p, size_t count, int64_t *bytes) {
+int dev_alloc(swmd_corpus *c, T **p, size_t count, int64_t *bytes) {
     *p = nullptr;
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    cudaError_t e = corpus_malloc(c, reinterpret_cast<void **>(p), count * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(e, "device allocation");
     if (bytes) *bytes += (int64_t)(count * sizeof(T));
     return SWMD_OK;
 }
 
-void dev_free(void *p) {
-    if (p) cudaFree(p);
-}
+void dev_free(swmd_corpus *c, void *p) { corpus_free(c, p); }
+
+std::mutex g_alloc_mu;
+Allocator g_allocator;   // the allocator corpora created from now on take
 
 }  // namespace
 
@@ -56,6 +57,37 @@ void dev_free(void *p) {
 // padding, the per-iteration walks' power of two >= 4 and the column-split
 // solver's power of two >= 16 all fit.
 int max_vrp_of(int max_vr) { return std::max(vrp_for(max_vr, 8), cols_vrp(max_vr)); }
+
+cudaError_t corpus_malloc(swmd_corpus *c, void **p, size_t bytes) {
+    *p = nullptr;
+    if (!c->allocator.alloc) return cudaMalloc(p, bytes);
+    void *q = c->allocator.alloc(bytes, c->device, c->stream, c->allocator.user);
+    if (!q) return cudaErrorMemoryAllocation;
+    {
+        std::lock_guard<std::mutex> lk(c->alloc_mu);
+        c->alloc_sizes[q] = bytes;
+    }
+    *p = q;
+    return cudaSuccess;
+}
+
+void corpus_free(swmd_corpus *c, void *p) {
+    if (!p) return;
+    if (!c->allocator.release) {
+        cudaFree(p);
+        return;
+    }
+    size_t bytes = 0;
+    {
+        std::lock_guard<std::mutex> lk(c->alloc_mu);
+        auto it = c->alloc_sizes.find(p);
+        if (it != c->alloc_sizes.end()) {
+            bytes = it->second;
+            c->alloc_sizes.erase(it);
+        }
+    }
+    c->allocator.release(p, bytes, c->device, c->stream, c->allocator.user);
+}
 
 void clear_graphs(swmd_corpus *c) {
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
@@ -65,6 +97,8 @@ void clear_graphs(swmd_corpus *c) {
 }
 
 int status_to_code(int st) {
+    if (st & ST_BOUNDS)
+        return set_error(SWMD_EINVAL, "a device bounds check failed: a corpus index lies outside its array");
     if (st & (ST_BAD_ID | ST_BAD_R))
         return set_error(SWMD_EINVAL, "query id outside [0, V) or weight not finite and > 0");
     if (st & ST_BAD_SIZE)
@@ -75,30 +109,30 @@ int status_to_code(int st) {
 }
 
 int alloc_slot(swmd_corpus *c, Slot &s, int max_vr, int kprec, bool with_v) {
-    free_slot(s);
+    free_slot(c, s);
     const int vrp = max_vrp_of(max_vr);
     const size_t kb = kprec_bytes(kprec);
     int rc;
     unsigned char *kt = nullptr, *kmt = nullptr;
-    if ((rc = dev_alloc(&kt, (size_t)std::max(c->Vu, 1) * vrp * kb, &s.bytes))) return rc;
+    if ((rc = dev_alloc(c, &kt, (size_t)std::max(c->Vu, 1) * vrp * kb, &s.bytes))) return rc;
     s.KT = kt;
-    if ((rc = dev_alloc(&kmt, (size_t)std::max(c->Vu, 1) * vrp * kb, &s.bytes))) return rc;
+    if ((rc = dev_alloc(c, &kmt, (size_t)std::max(c->Vu, 1) * vrp * kb, &s.bytes))) return rc;
     s.KMT = kmt;
-    if ((rc = dev_alloc(&s.u, (size_t)std::max(c->Nl, 1) * vrp, &s.bytes))) return rc;
+    if ((rc = dev_alloc(c, &s.u, (size_t)std::max(c->Nl, 1) * vrp, &s.bytes))) return rc;
     if (with_v) {
         s.v_elems = std::max<int64_t>(std::max(c->nnz, c->slice_total), 1);
-        if ((rc = dev_alloc(&s.v, (size_t)s.v_elems, &s.bytes))) return rc;
+        if ((rc = dev_alloc(c, &s.v, (size_t)s.v_elems, &s.bytes))) return rc;
     }
-    if ((rc = dev_alloc(&s.q_ids, vrp, &s.bytes))) return rc;
-    if ((rc = dev_alloc(&s.r, vrp, &s.bytes))) return rc;
-    if ((rc = dev_alloc(&s.qp, 1, &s.bytes))) return rc;
+    if ((rc = dev_alloc(c, &s.q_ids, vrp, &s.bytes))) return rc;
+    if ((rc = dev_alloc(c, &s.r, vrp, &s.bytes))) return rc;
+    if ((rc = dev_alloc(c, &s.qp, 1, &s.bytes))) return rc;
     // the distances and, right after them, the status word: one device-to-host copy
-    if ((rc = dev_alloc(&s.out, (size_t)std::max(c->Nl, 1) + 1, &s.bytes))) return rc;
+    if ((rc = dev_alloc(c, &s.out, (size_t)std::max(c->Nl, 1) + 1, &s.bytes))) return rc;
     s.status = reinterpret_cast<int *>(s.out + std::max(c->Nl, 1));
-    if ((rc = dev_alloc(&s.conv, 1 + kMaxConvIters, &s.bytes))) return rc;
+    if ((rc = dev_alloc(c, &s.conv, 1 + kMaxConvIters, &s.bytes))) return rc;
     SWMD_CK(cudaMemset(s.conv, 0, sizeof(unsigned) * (1 + kMaxConvIters)));
     // the staged query ids and, right after them, its weights: one host-to-device copy
-    if ((rc = dev_alloc(&s.q_in, 2 * (size_t)vrp, &s.bytes))) return rc;
+    if ((rc = dev_alloc(c, &s.q_in, 2 * (size_t)vrp, &s.bytes))) return rc;
     s.r_in = reinterpret_cast<float *>(s.q_in + vrp);
     s.carved_io = true;
     SWMD_CK(cudaMemset(s.u, 0, (size_t)std::max(c->Nl, 1) * vrp * sizeof(float)));
@@ -107,13 +141,13 @@ int alloc_slot(swmd_corpus *c, Slot &s, int max_vr, int kprec, bool with_v) {
     return SWMD_OK;
 }
 
-void free_slot(Slot &s) {
-    dev_free(s.KT); dev_free(s.KMT); dev_free(s.u); dev_free(s.v); dev_free(s.q_ids);
-    dev_free(s.r); dev_free(s.qp); dev_free(s.out); dev_free(s.q_in);
-    dev_free(s.conv);
+void free_slot(swmd_corpus *c, Slot &s) {
+    dev_free(c, s.KT); dev_free(c, s.KMT); dev_free(c, s.u); dev_free(c, s.v); dev_free(c, s.q_ids);
+    dev_free(c, s.r); dev_free(c, s.qp); dev_free(c, s.out); dev_free(c, s.q_in);
+    dev_free(c, s.conv);
     if (!s.carved_io) {   // else they live inside out / q_in
-        dev_free(s.status);
-        dev_free(s.r_in);
+        dev_free(c, s.status);
+        dev_free(c, s.r_in);
     }
     s = Slot{};
 }
@@ -224,16 +258,16 @@ int build_tiles(swmd_corpus *c) {
     }
     int *dev = nullptr;
     int64_t bytes = 0;
-    int rc = dev_alloc(&dev, all.size(), &bytes);
+    int rc = dev_alloc(c, &dev, all.size(), &bytes);
     if (rc) return rc;
     cudaError_t e = cudaMemcpy(dev, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        cudaFree(dev);
+        dev_free(c, dev);
         return cuda_fail(e, "copy tiles");
     }
     if (c->tiles_dev) {
         cudaDeviceSynchronize();   // no launch may still read the old sets
-        cudaFree(c->tiles_dev);
+        dev_free(c, c->tiles_dev);
     }
     c->tiles_dev = dev;
     c->tile_off = off;
@@ -259,7 +293,7 @@ int build_tasks(swmd_corpus *c) {
         c->task_count[npl] = n;
     }
     int64_t bytes = 0;
-    int rc = dev_alloc(&c->tasks_dev, std::max<size_t>(all.size(), 1), &bytes);
+    int rc = dev_alloc(c, &c->tasks_dev, std::max<size_t>(all.size(), 1), &bytes);
     if (rc) return rc;
     c->base_bytes += bytes;
     if (!all.empty()) {
@@ -286,7 +320,7 @@ int build_tasks(swmd_corpus *c) {
         c->col_count[li] = (int)cols.size() - c->col_off[li];
     }
     bytes = 0;
-    if ((rc = dev_alloc(&c->col_tasks_dev, cols.size(), &bytes))) return rc;
+    if ((rc = dev_alloc(c, &c->col_tasks_dev, cols.size(), &bytes))) return rc;
     c->base_bytes += bytes;
     cudaError_t e = cudaMemcpy(c->col_tasks_dev, cols.data(), sizeof(int4) * cols.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "copy column-split tasks");
@@ -332,6 +366,8 @@ int run_resident_batch(swmd_corpus *c, const ResidentArgs &ra, Mapping m, int kp
         ca.doc_orig = c->doc_orig;
         ca.tasks = c->col_tasks_dev + c->col_off[li];
         ca.n_tasks = c->col_count[li];
+        ca.Vu = c->Vu;
+        ca.nnz = c->nnz;
         ca.kprec = kprec;
         ca.q0 = ra;
         ca.queries = d_batch;
@@ -413,6 +449,7 @@ static int launch_sequence(swmd_corpus *c, Slot &s, Mapping m, int vr, int t, in
     ia.qp = s.qp;
     ia.doc0 = 0;
     ia.N = c->Nl;
+    ia.Vu = c->Vu;
     ia.slice_ptr = c->slice_ptr;
     ia.slice_nz = c->slice_nz;
     ia.n_slices = c->n_slices;
@@ -518,6 +555,16 @@ void swmd_default_options(swmd_options *opt) {
 }
 
 const char *swmd_last_error(void) { return g_error.c_str(); }
+
+int swmd_set_allocator(swmd_alloc_fn alloc, swmd_free_fn release, void *user) {
+    if ((alloc == nullptr) != (release == nullptr))
+        return set_error(SWMD_EINVAL, "swmd_set_allocator: give both functions or neither");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_allocator.alloc = alloc;
+    g_allocator.release = release;
+    g_allocator.user = alloc ? user : nullptr;
+    return SWMD_OK;
+}
 
 int swmd_select(int32_t V, int32_t n, const int32_t *h_ids, const float *h_weights,
                 int32_t *h_out_ids, float *h_out_r, int32_t *out_vr) {
@@ -710,6 +757,10 @@ int swmd_create_corpus(int32_t V, int32_t N, int64_t nnz, const int64_t *row_ptr
         }
     }
     c->device = dev;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        c->allocator = g_allocator;
+    }
     DeviceGuard guard(dev);
     int rc = SWMD_OK;
     auto bail = [&](int code) {
@@ -726,13 +777,13 @@ int swmd_create_corpus(int32_t V, int32_t N, int64_t nnz, const int64_t *row_ptr
         ce = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
         if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamCreateWithFlags"));
     }
-    if ((rc = dev_alloc(&c->E, (size_t)V * c->d4, &c->base_bytes))) return bail(rc);
-    if ((rc = dev_alloc(&c->used, (size_t)std::max(c->Vu, 1), &c->base_bytes))) return bail(rc);
-    if ((rc = dev_alloc(&c->doc_ptr, (size_t)Nl + 1, &c->base_bytes))) return bail(rc);
-    if ((rc = dev_alloc(&c->nz, (size_t)std::max<int64_t>(nnz_l, 1), &c->base_bytes))) return bail(rc);
-    if ((rc = dev_alloc(&c->doc_orig, (size_t)std::max(Nl, 1), &c->base_bytes))) return bail(rc);
-    if ((rc = dev_alloc(&c->slice_ptr, (size_t)n_slices + 1, &c->base_bytes))) return bail(rc);
-    if ((rc = dev_alloc(&c->slice_nz, (size_t)std::max<int64_t>(slice_total, 1), &c->base_bytes)))
+    if ((rc = dev_alloc(c, &c->E, (size_t)V * c->d4, &c->base_bytes))) return bail(rc);
+    if ((rc = dev_alloc(c, &c->used, (size_t)std::max(c->Vu, 1), &c->base_bytes))) return bail(rc);
+    if ((rc = dev_alloc(c, &c->doc_ptr, (size_t)Nl + 1, &c->base_bytes))) return bail(rc);
+    if ((rc = dev_alloc(c, &c->nz, (size_t)std::max<int64_t>(nnz_l, 1), &c->base_bytes))) return bail(rc);
+    if ((rc = dev_alloc(c, &c->doc_orig, (size_t)std::max(Nl, 1), &c->base_bytes))) return bail(rc);
+    if ((rc = dev_alloc(c, &c->slice_ptr, (size_t)n_slices + 1, &c->base_bytes))) return bail(rc);
+    if ((rc = dev_alloc(c, &c->slice_nz, (size_t)std::max<int64_t>(slice_total, 1), &c->base_bytes)))
         return bail(rc);
     cudaError_t ce;
     if (c->d4 == d) {
@@ -782,20 +833,20 @@ void swmd_destroy_corpus(swmd_corpus *c) {
         DeviceGuard guard(c->device);
         if (c->stream) cudaStreamSynchronize(c->stream);
         clear_graphs(c);
-        free_slot(c->main);
-        dev_free(c->batch_ws);
-        dev_free(c->pair_ws);
-        dev_free(c->pair_kws);
-        dev_free(c->E);
-        dev_free(c->used);
-        dev_free(c->doc_ptr);
-        dev_free(c->nz);
-        dev_free(c->slice_ptr);
-        dev_free(c->slice_nz);
-        dev_free(c->doc_orig);
-        dev_free(c->tiles_dev);
-        dev_free(c->tasks_dev);
-        dev_free(c->col_tasks_dev);
+        free_slot(c, c->main);
+        dev_free(c, c->batch_ws);
+        dev_free(c, c->pair_ws);
+        dev_free(c, c->pair_kws);
+        dev_free(c, c->E);
+        dev_free(c, c->used);
+        dev_free(c, c->doc_ptr);
+        dev_free(c, c->nz);
+        dev_free(c, c->slice_ptr);
+        dev_free(c, c->slice_nz);
+        dev_free(c, c->doc_orig);
+        dev_free(c, c->tiles_dev);
+        dev_free(c, c->tasks_dev);
+        dev_free(c, c->col_tasks_dev);
         if (c->h_io) cudaFreeHost(c->h_io);
         if (c->stream) cudaStreamDestroy(c->stream);
     }
@@ -924,6 +975,7 @@ static IterArgs iter_args(swmd_corpus *c, Slot &s) {
     ia.qp = s.qp;
     ia.doc0 = 0;
     ia.N = c->Nl;
+    ia.Vu = c->Vu;
     ia.slice_ptr = c->slice_ptr;
     ia.slice_nz = c->slice_nz;
     ia.n_slices = c->n_slices;
@@ -982,7 +1034,7 @@ int swmd_step_iterate(swmd_corpus *c, int32_t v_r, int32_t n_iter, int32_t first
     if (path == SWMD_PATH_PLAIN && !s.v) {
         int64_t extra = 0;
         s.v_elems = std::max<int64_t>(std::max(c->nnz, c->slice_total), 1);
-        if ((rc = dev_alloc(&s.v, (size_t)s.v_elems, &extra))) return rc;
+        if ((rc = dev_alloc(c, &s.v, (size_t)s.v_elems, &extra))) return rc;
         s.bytes += extra;
         clear_graphs(c);
     }
@@ -1073,6 +1125,26 @@ int swmd_resolve_path(swmd_corpus *c, int32_t v_r, int32_t *out_path) {
     std::lock_guard<std::mutex> lk(c->mu);
     *out_path = resolve_path(c, v_r);
     return SWMD_OK;
+}
+
+int swmd_debug_plant(swmd_corpus *c, int32_t what, int64_t index, int32_t value) {
+#if SWMD_DEBUG_CHECKS
+    if (!c || (what != 0 && what != 1)) return set_error(SWMD_EINVAL, "swmd_debug_plant: bad arguments");
+    const int64_t n = what == 0 ? c->nnz : c->slice_total;
+    if (index < 0 || index >= n) return set_error(SWMD_EINVAL, "swmd_debug_plant: index outside [0, %lld)", (long long)n);
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard guard(c->device);
+    SWMD_CK(cudaStreamSynchronize(c->stream));
+    int2 *dst = (what == 0 ? c->nz : c->slice_nz) + index;
+    SWMD_CK(cudaMemcpy(&dst->x, &value, sizeof value, cudaMemcpyHostToDevice));
+    return SWMD_OK;
+#else
+    (void)c;
+    (void)what;
+    (void)index;
+    (void)value;
+    return set_error(SWMD_EINVAL, "swmd_debug_plant: available in debug builds only (build(debug=True))");
+#endif
 }
 
 int swmd_debug_read(swmd_corpus *c, int32_t what, int32_t v_r, void *h_dst) {

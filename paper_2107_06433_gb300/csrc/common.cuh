@@ -31,6 +31,28 @@ constexpr int ST_BAD_ID = 1;       // a query id outside [0, V)
 constexpr int ST_NUMERIC = 2;      // NaN / Inf / zero denominator
 constexpr int ST_GUARD = 4;        // the FP64 guard of K^T u was taken (informational)
 constexpr int ST_BAD_R = 8;        // a query weight that is not finite and > 0
+constexpr int ST_BOUNDS = 32;      // debug builds: a corpus index outside its array
+
+// Debug builds (SWMD_DEBUG_CHECKS=1, build(debug=True)) check the corpus indices the
+// kernels follow -- compact word ids and document offsets -- before using them: an
+// index outside [0, n) sets ST_BOUNDS in the status word and is replaced by 0, so
+// nothing outside the arrays is read (no trap, no assert).  Release builds use the
+// index as it is.
+#ifndef SWMD_DEBUG_CHECKS
+#define SWMD_DEBUG_CHECKS 0
+#endif
+__device__ __forceinline__ int checked_index(int i, long n, int *status) {
+#if SWMD_DEBUG_CHECKS
+    if (i < 0 || (long)i >= n) {
+        atomicOr(status, ST_BOUNDS);
+        return 0;
+    }
+#else
+    (void)n;
+    (void)status;
+#endif
+    return i;
+}
 
 // Query parameters read by the kernels from device memory, so that a captured
 // graph stays valid when lambda or v_r change.
@@ -60,6 +82,7 @@ struct IterArgs {
     const QParams *qp;
     long doc0;             // first document (internal order) of this launch
     int N;                 // documents in this launch
+    int Vu;                // rows of K^T (compact words): bounds of the debug checks
     int first;             // 1: u = v_r (x = 1/v_r), do not read u
     double *out;           // if not NULL, the distances go here instead of qp->out
     // sliced nonzeros (per-iteration walks): slices of 32 documents, entry (i, t)
@@ -311,6 +334,8 @@ struct ColArgs {
     const int4 *tasks;     // (first document, documents, bucket, 0) warp tasks
     int n_tasks;
     int kprec;
+    int Vu;                // rows of K^T (debug checks)
+    long nnz;              // nonzeros (debug checks)
     ResidentArgs q0;                 // the query when `queries` is NULL
     const ResidentArgs *queries;     // else: device array of nq queries of this layout, run
     int nq;                          // in one launch over (group of q_per_group queries,

@@ -9,6 +9,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -39,6 +40,13 @@ int cuda_fail(cudaError_t e, const char *what);
         cudaError_t e_ = (call);                             \
         if (e_ != cudaSuccess) return ::swmd::cuda_fail(e_, #call); \
     } while (0)
+
+// The device allocator of a corpus (swmd_set_allocator; NULL functions: cudaMalloc).
+struct Allocator {
+    swmd_alloc_fn alloc = nullptr;
+    swmd_free_fn release = nullptr;
+    void *user = nullptr;
+};
 
 // Device-side parameter block of one query slot.  Kernels read it through a
 // pointer, so a captured graph is reused for every query of the same shape.
@@ -142,6 +150,9 @@ struct swmd_corpus {
     std::map<std::pair<int, int>, int> tuned_qpt;
     size_t l2_bytes = 0;           // the device's L2 cache
     std::mutex mu;                 // serialises use of `main` and the graph cache
+    swmd::Allocator allocator;     // the allocator in force when the corpus was created
+    std::mutex alloc_mu;
+    std::unordered_map<void *, size_t> alloc_sizes;   // live blocks of a set allocator
     int servers = 0;               // servers attached (under mu): tuning and option changes wait
 };
 
@@ -150,7 +161,11 @@ namespace swmd {
 // The K^T / u row length a workspace needs for queries of up to max_vr words.
 int max_vrp_of(int max_vr);
 int alloc_slot(swmd_corpus *c, Slot &s, int max_vr, int kprec, bool with_v);
-void free_slot(Slot &s);
+void free_slot(swmd_corpus *c, Slot &s);
+// Device memory of the corpus's allocator (cudaMalloc when none was set);
+// corpus_free(c, NULL) does nothing.
+cudaError_t corpus_malloc(swmd_corpus *c, void **p, size_t bytes);
+void corpus_free(swmd_corpus *c, void *p);
 Mapping choose_mapping(swmd_corpus *c, int vr, int path);
 int layout_vrp(swmd_corpus *c, int vr, int path);
 // The tight resident layout (v_r padded to the solver's multiple of 4, 8 or 16)

@@ -124,6 +124,7 @@ extern "C" int swmd_query_noalloc(swmd_corpus *c, const int32_t *d_ids, const fl
     ia.qp = qp;
     ia.doc0 = 0;
     ia.N = c->Nl;
+    ia.Vu = c->Vu;
     ia.first = 1;
     ResidentArgs ra{ia, max_iter};
     return run_resident(c, ra, m, kprec, v_r, st);

@@ -396,11 +396,11 @@ int launch_pairs_t(swmd_corpus *c, const PairArgs &base, cudaStream_t st) {
         if (c->pair_kws_bytes < need) {
             if (c->pair_kws) {
                 SWMD_CK(cudaDeviceSynchronize());   // earlier pairs may still use the old regions
-                cudaFree(c->pair_kws);
+                corpus_free(c, c->pair_kws);
                 c->pair_kws = nullptr;
                 c->pair_kws_bytes = 0;
             }
-            SWMD_CK(cudaMalloc(&c->pair_kws, need));
+            SWMD_CK(corpus_malloc(c, reinterpret_cast<void **>(&c->pair_kws), need));
             c->pair_kws_bytes = need;
         }
         a.kws = c->pair_kws;
@@ -539,11 +539,11 @@ int swmd_wmd_pairs(swmd_corpus *c, int32_t n_pairs, const int64_t *h_q_ptr,
     if (c->pair_ws_bytes < bytes) {
         if (c->pair_ws) {
             SWMD_CK(cudaStreamSynchronize(st));
-            cudaFree(c->pair_ws);
+            corpus_free(c, c->pair_ws);
             c->pair_ws = nullptr;
             c->pair_ws_bytes = 0;
         }
-        cudaError_t e = cudaMalloc(&c->pair_ws, bytes);
+        cudaError_t e = corpus_malloc(c, &c->pair_ws, bytes);
         if (e != cudaSuccess) return cuda_fail(e, "swmd_wmd_pairs: workspace");
         c->pair_ws_bytes = bytes;
     }

@@ -197,14 +197,20 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
     const bool has = team < tk.y;
     const int doc = tk.x + team;
     int beg = 0, len = 0;
-    if (has) {
-        beg = __ldg(a.doc_ptr + doc);
-        len = __ldg(a.doc_ptr + doc + 1) - beg;
-    }
     const QParams *qp = q.it.qp;
     const int vr = qp->vr;
     const float u0 = qp->u0;
     int *const status = qp->status;
+    if (has) {
+        beg = checked_index(__ldg(a.doc_ptr + doc), a.nnz + 1, status);
+        len = checked_index(__ldg(a.doc_ptr + doc + 1), a.nnz + 1, status) - beg;
+#if SWMD_DEBUG_CHECKS
+        if (len < 0) {
+            atomicOr(status, ST_BOUNDS);
+            len = 0;
+        }
+#endif
+    }
     const int2 *ent = a.nz + beg;
     const int row0 = g * RL;                          // the group's first row
     const float *su_team = su + P * (team * TEAM);    // the team's u, column-ordered (guard only)
@@ -228,7 +234,7 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
     {
         int wv[RL];
 #pragma unroll
-        for (int i = 0; i < RL; ++i) wv[i] = row0 + i < len ? __ldg(&ent[row0 + i].x) : 0;
+        for (int i = 0; i < RL; ++i) wv[i] = row0 + i < len ? checked_index(__ldg(&ent[row0 + i].x), a.Vu, status) : 0;
         gather_rows<VRP, P, RL>(rv, q.it.KT, a.kprec, wv, ql);
     }
     permute_rows<RL, P, Q, R>(rv, ql);
@@ -253,7 +259,7 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
 #pragma unroll
             for (int o = 0; o < R; ++o) {
                 if (cown[o] != 0.f && !(s_own[o] >= 0x1p-100f)) {
-                    const int w = __ldg(&ent[row0 + ql * R + o].x);
+                    const int w = checked_index(__ldg(&ent[row0 + ql * R + o].x), a.Vu, status);
                     const double sd = dot_fp64<VRP>(q.it.KT, a.kprec, w, su_team);
                     tv[o] = sd > 0.0 ? (float)((double)cown[o] / sd) : 0.f;
                     atomicOr(status, sd > 0.0 ? ST_GUARD : ST_NUMERIC);
@@ -305,7 +311,7 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
     {
         int wv[RL];   // the word ids again (the registers were free during the iterations)
 #pragma unroll
-        for (int i = 0; i < RL; ++i) wv[i] = row0 + i < len ? __ldg(&ent[row0 + i].x) : 0;
+        for (int i = 0; i < RL; ++i) wv[i] = row0 + i < len ? checked_index(__ldg(&ent[row0 + i].x), a.Vu, status) : 0;
         gather_rows<VRP, P, RL>(rv, q.it.KMT, a.kprec, wv, ql);
     }
     permute_rows<RL, P, Q, R>(rv, ql);
@@ -324,7 +330,7 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
 #pragma unroll
         for (int o = 0; o < R; ++o) {
             if (cown[o] != 0.f && !(s_own[o] >= 0x1p-100f)) {
-                const int w = __ldg(&ent[row0 + ql * R + o].x);
+                const int w = checked_index(__ldg(&ent[row0 + ql * R + o].x), a.Vu, status);
                 const double sd = dot_fp64<VRP>(q.it.KT, a.kprec, w, su_team);
                 const double md = dot_fp64<VRP>(q.it.KMT, a.kprec, w, su_team);
                 dist += (double)cown[o] * (md / sd);

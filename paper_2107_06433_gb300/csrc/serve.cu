@@ -245,6 +245,7 @@ int launch_group(swmd_server *S, int li, int buf, const std::vector<ServerSlot *
         ia.doc_orig = c->doc_orig;
         ia.qp = sl.ws.qp;
         ia.N = c->Nl;
+        ia.Vu = c->Vu;
         ia.first = 1;
         hr[i] = ResidentArgs{ia, R.t};
     }
@@ -528,11 +529,11 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
         if (c->batch_ws) {
             cudaStreamSynchronize(st);
             clear_graphs(c);   // the captured batches point into the old workspace
-            cudaFree(c->batch_ws);
+            corpus_free(c, c->batch_ws);
             c->batch_ws = nullptr;
             c->batch_ws_bytes = 0;
         }
-        cudaError_t e = cudaMalloc(&c->batch_ws, bytes);
+        cudaError_t e = corpus_malloc(c, &c->batch_ws, bytes);
         if (e != cudaSuccess) return cuda_fail(e, "swmd_query_batch: workspace");
         c->batch_ws_bytes = bytes;
     }
@@ -592,6 +593,7 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
         ia.qp = qp;
         ia.doc0 = 0;
         ia.N = c->Nl;
+        ia.Vu = c->Vu;
         ia.first = 1;
         res[i] = ResidentArgs{ia, max_iter};
     }
@@ -743,7 +745,7 @@ int swmd_serve_start(swmd_corpus *c, const swmd_serve_config *cfg_in, swmd_serve
         for (auto &sl : S->slots) {
             sl.ws.KT = sl.ws.KMT = nullptr;
             sl.ws.u = sl.ws.v = nullptr;
-            free_slot(sl.ws);
+            free_slot(S->c, sl.ws);
             if (sl.stream) cudaStreamDestroy(sl.stream);
             if (sl.done) cudaEventDestroy(sl.done);
             cudaFreeHost(sl.h_q); cudaFreeHost(sl.h_r); cudaFreeHost(sl.h_out); cudaFreeHost(sl.h_status);
@@ -751,15 +753,15 @@ int swmd_serve_start(swmd_corpus *c, const swmd_serve_config *cfg_in, swmd_serve
         for (auto &L : S->lanes) {
             if (L.stream) cudaStreamDestroy(L.stream);
             for (int b = 0; b < kLaneDepth; ++b) {
-                cudaFree(L.d_args[b]);
+                corpus_free(S->c, L.d_args[b]);
                 cudaFreeHost(L.h_args[b]);
             }
         }
-        cudaFree(S->arena_mem);
+        corpus_free(S->c, S->arena_mem);
         delete S;
         return code;
     };
-    cudaError_t e = cudaMalloc(&S->arena_mem, (size_t)cfg.memory_budget);
+    cudaError_t e = corpus_malloc(c, reinterpret_cast<void **>(&S->arena_mem), (size_t)cfg.memory_budget);
     if (e != cudaSuccess) return bail(cuda_fail(e, "swmd_serve_start: arena"));
     S->arena.init(S->arena_mem, (size_t)cfg.memory_budget);
     S->slots.resize((size_t)cfg.max_batch);
@@ -767,15 +769,15 @@ int swmd_serve_start(swmd_corpus *c, const swmd_serve_config *cfg_in, swmd_serve
     for (auto &sl : S->slots) {
         Slot &w = sl.ws;
         int64_t b = 0;
-        e = cudaMalloc(&w.q_ids, sizeof(int) * vrp);
-        if (e == cudaSuccess) e = cudaMalloc(&w.r, sizeof(float) * vrp);
-        if (e == cudaSuccess) e = cudaMalloc(&w.qp, sizeof(QParams));
-        if (e == cudaSuccess) e = cudaMalloc(&w.out, sizeof(double) * std::max(c->Nl, 1));
-        if (e == cudaSuccess) e = cudaMalloc(&w.status, sizeof(int));
-        if (e == cudaSuccess) e = cudaMalloc(&w.conv, sizeof(unsigned) * (1 + kMaxConvIters));
+        e = corpus_malloc(c, reinterpret_cast<void **>(&w.q_ids), sizeof(int) * vrp);
+        if (e == cudaSuccess) e = corpus_malloc(c, reinterpret_cast<void **>(&w.r), sizeof(float) * vrp);
+        if (e == cudaSuccess) e = corpus_malloc(c, reinterpret_cast<void **>(&w.qp), sizeof(QParams));
+        if (e == cudaSuccess) e = corpus_malloc(c, reinterpret_cast<void **>(&w.out), sizeof(double) * std::max(c->Nl, 1));
+        if (e == cudaSuccess) e = corpus_malloc(c, reinterpret_cast<void **>(&w.status), sizeof(int));
+        if (e == cudaSuccess) e = corpus_malloc(c, reinterpret_cast<void **>(&w.conv), sizeof(unsigned) * (1 + kMaxConvIters));
         if (e == cudaSuccess) e = cudaMemset(w.conv, 0, sizeof(unsigned) * (1 + kMaxConvIters));
-        if (e == cudaSuccess) e = cudaMalloc(&w.q_in, sizeof(int) * vrp);
-        if (e == cudaSuccess) e = cudaMalloc(&w.r_in, sizeof(float) * vrp);
+        if (e == cudaSuccess) e = corpus_malloc(c, reinterpret_cast<void **>(&w.q_in), sizeof(int) * vrp);
+        if (e == cudaSuccess) e = corpus_malloc(c, reinterpret_cast<void **>(&w.r_in), sizeof(float) * vrp);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_q, sizeof(int32_t) * vrp);
@@ -799,7 +801,7 @@ int swmd_serve_start(swmd_corpus *c, const swmd_serve_config *cfg_in, swmd_serve
         L.args_bytes = lane_args_bytes(cfg.max_batch);
         e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking);
         for (int b = 0; b < kLaneDepth && e == cudaSuccess; ++b) {
-            e = cudaMalloc(&L.d_args[b], L.args_bytes);
+            e = corpus_malloc(c, reinterpret_cast<void **>(&L.d_args[b]), L.args_bytes);
             if (e == cudaSuccess) e = cudaMallocHost(&L.h_args[b], L.args_bytes);
         }
         if (e != cudaSuccess) return bail(cuda_fail(e, "swmd_serve_start: batch lane"));
@@ -910,7 +912,7 @@ int swmd_serve_stop(swmd_server *S) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         sl.ws.KT = sl.ws.KMT = nullptr;
         sl.ws.u = sl.ws.v = nullptr;
-        free_slot(sl.ws);
+        free_slot(S->c, sl.ws);
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.done) cudaEventDestroy(sl.done);
         cudaFreeHost(sl.h_q); cudaFreeHost(sl.h_r); cudaFreeHost(sl.h_out); cudaFreeHost(sl.h_status);
@@ -921,11 +923,11 @@ int swmd_serve_stop(swmd_server *S) {
             cudaStreamDestroy(L.stream);
         }
         for (int b = 0; b < kLaneDepth; ++b) {
-            cudaFree(L.d_args[b]);
+            corpus_free(S->c, L.d_args[b]);
             cudaFreeHost(L.h_args[b]);
         }
     }
-    cudaFree(S->arena_mem);
+    corpus_free(S->c, S->arena_mem);
     delete S;
     return SWMD_OK;
 }

@@ -270,7 +270,10 @@ __global__ void __launch_bounds__(NT, MINB) k_walk3(IterArgs a) {
                 // their tau is 0
                 uint32_t kw[RB][WORDS];
 #pragma unroll
-                for (int rr = 0; rr < RB; ++rr) load_words<WORDS>(KTl + (long)e[rr].x * kRowBytes, kw[rr], pol_keep);
+                for (int rr = 0; rr < RB; ++rr) {
+                    e[rr].x = checked_index(e[rr].x, a.Vu, status);
+                    load_words<WORDS>(KTl + (long)e[rr].x * kRowBytes, kw[rr], pol_keep);
+                }
                 float tau[RB];
                 if constexpr (KIND == Kind::Spmm) {
 #pragma unroll

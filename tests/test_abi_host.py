@@ -150,3 +150,10 @@ def test_pair_binding_marshals_ragged_sides(lib):
     assert ids.dtype == np.int32 and w.dtype == np.float32 and ptr.dtype == np.int64
     with pytest.raises(ValueError):
         swmd.swmd_wmd_pairs(None, [([1], [1.0])], [], 1.0, 15)
+
+
+def test_allocator_needs_both_functions(lib):
+    fn = swmd._ALLOC_FN(lambda n, d, s, u: None)
+    rc = lib.swmd_set_allocator(ctypes.cast(fn, ctypes.c_void_p), None, None)
+    assert rc == swmd.SWMD_EINVAL and b"both" in lib.swmd_last_error()
+    assert lib.swmd_set_allocator(None, None, None) == swmd.SWMD_OK
