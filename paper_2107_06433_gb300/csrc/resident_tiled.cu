@@ -59,7 +59,7 @@ __device__ __noinline__ void k_resident_tiled_body(const ResidentArgs &ra, const
     constexpr int UNIT = (ROWB % 16 == 0) ? 16 : 8;          // cp.async granule
     constexpr int CPR = ROWB / UNIT;                         // granules per row
     static_assert(ROWB % 8 == 0, "row must be a multiple of 8 bytes");
-    const IterArgs &a = ra.it;
+    const IterArgs a = ra.it;   // one copy of the arguments (read in every tile)
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     KT_t *sK = reinterpret_cast<KT_t *>(smem_raw);
