@@ -18,9 +18,9 @@
 // the remaining values each (LMAX (1 - 1/Q) shuffles per lane and direction).  For
 // the butterfly to need no selects, lane q stores row block b ^ q (blocks of R
 // rows) in register block b: then at every step all lanes keep the same register
-// blocks and send the same others.  Rows are gathered in natural order (one
-// coalesced 16-byte slice per lane of each row) and put into that order once, by
-// log2(Q) passes of conditional swaps.
+// blocks and send the same others.  The lane reads its word ids in that order, so
+// its gathers fill the register blocks directly (a lane's slice of one row is one
+// 8-column vector load, whichever row it is).
 //
 // A document of up to 12 rows per lane (16 in 128-column layouts) is one row
 // group; longer ones are G row groups (the team), whose partial acc are summed with
@@ -75,9 +75,9 @@ __device__ __forceinline__ void ldg_words(const void *p, uint32_t (&w)[P]) {
 }
 
 // Columns [P ql, P ql + P) of the rows of words wv[i] (word-major layout of VRP
-// columns), widened to float.  Rows past the document's end read word 0: finite
-// values whose tau is masked to 0.  One unrolled loop per storage type, so all RL
-// loads of a lane are in flight together.
+// columns), widened to float.  Rows past the document's end (wv[i] < 0) are not
+// loaded: zeros, whose tau is masked to 0.  One unrolled loop per storage type, so
+// all RL loads of a lane are in flight together.
 template <int VRP, int P, int RL>
 __device__ __forceinline__ void gather_rows(float (&rv)[RL][P], const void *base, int kprec, const int (&wv)[RL],
                                             int ql) {
@@ -85,16 +85,17 @@ __device__ __forceinline__ void gather_rows(float (&rv)[RL][P], const void *base
         const float *b = reinterpret_cast<const float *>(base) + ql * P;
 #pragma unroll
         for (int i = 0; i < RL; ++i) {
-            uint32_t w[P];
-            ldg_words<P>(b + (long)wv[i] * VRP, w);
+            uint32_t w[P] = {};
+            if (wv[i] >= 0) ldg_words<P>(b + (long)wv[i] * VRP, w);
 #pragma unroll
             for (int k = 0; k < P; ++k) rv[i][k] = __uint_as_float(w[k]);
         }
     } else {
         const unsigned short *b = reinterpret_cast<const unsigned short *>(base) + ql * P;
-        uint32_t raw[RL][P / 2];
+        uint32_t raw[RL][P / 2] = {};
 #pragma unroll
-        for (int i = 0; i < RL; ++i) ldg_words<P / 2>(b + (long)wv[i] * VRP, raw[i]);
+        for (int i = 0; i < RL; ++i)
+            if (wv[i] >= 0) ldg_words<P / 2>(b + (long)wv[i] * VRP, raw[i]);
 #pragma unroll
         for (int i = 0; i < RL; ++i)
 #pragma unroll
@@ -103,27 +104,6 @@ __device__ __forceinline__ void gather_rows(float (&rv)[RL][P], const void *base
                 rv[i][2 * k] = f.x;
                 rv[i][2 * k + 1] = f.y;
             }
-    }
-}
-
-// Puts row block b ^ ql into register block b (blocks of R rows): conditional
-// swaps of whole rows, one pass per bit of ql.
-template <int RL, int P, int Q, int R>
-__device__ __forceinline__ void permute_rows(float (&rv)[RL][P], int ql) {
-#pragma unroll
-    for (int bit = 1; bit < Q; bit <<= 1) {
-        const bool sw = (ql & bit) != 0;
-#pragma unroll
-        for (int i = 0; i < RL; ++i) {
-            if ((i / R) & bit) continue;   // each pair of blocks once, from its lower block
-            const int j = i + bit * R;
-#pragma unroll
-            for (int k = 0; k < P; ++k) {
-                const float x = rv[i][k], y = rv[j][k];
-                rv[i][k] = sw ? y : x;
-                rv[j][k] = sw ? x : y;
-            }
-        }
     }
 }
 
@@ -150,9 +130,10 @@ __device__ __forceinline__ void reduce_scatter(T (&s)[RL]) {
         for (int i = 0; i < m * R; ++i) s[i] += __shfl_xor_sync(kFull, s[i + m * R], m);
 }
 
-// All-gather over the Q lanes: tv[0..R) of every lane -> tv[i] for every register row.
-template <int RL, int Q, int R>
-__device__ __forceinline__ void all_gather(float (&tv)[RL]) {
+// All-gather over the Q lanes: tv[0..R) of every lane -> tv[i] for every register
+// row (block b of lane ql from lane ql ^ b: the register-block order).
+template <class T, int RL, int Q, int R>
+__device__ __forceinline__ void all_gather(T (&tv)[RL]) {
 #pragma unroll
     for (int m = 1; m < Q; m <<= 1)
 #pragma unroll
@@ -215,12 +196,20 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
     const int row0 = g * RL;                          // the group's first row
     const float *su_team = su + P * (team * TEAM);    // the team's u, column-ordered (guard only)
 
-    // c of the rows this lane finishes (zero past the end: their tau is 0)
+    // the nonzeros (word id, c) of the rows this lane finishes, row block ql of the
+    // group; past the end: word -1 (not loaded) and c = 0 (tau 0)
     float cown[R];
+    int wown[R];
 #pragma unroll
     for (int o = 0; o < R; ++o) {
         const int row = row0 + ql * R + o;
-        cown[o] = row < len ? __int_as_float(__ldg(&ent[row].y)) : 0.f;
+        int2 e = make_int2(-1, 0);
+        if (row < len) {
+            e = __ldg(&ent[row]);
+            e.x = checked_index(e.x, a.Vu, status);
+        }
+        wown[o] = e.x;
+        cown[o] = __int_as_float(e.y);
     }
     float rr[P], u[P];
 #pragma unroll
@@ -229,15 +218,15 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
         rr[k] = __ldg(q.it.r + col);
         u[k] = has && col < vr ? u0 : 0.f;
     }
-    // the group's rows of K^T: word ids in natural order, all loads in flight at once
+    // the group's rows of K^T in register-block order, all loads in flight at once
     float rv[RL][P];
     {
-        int wv[RL];
+        int wv[RL];   // word ids in register-block order: the team's own ids, all-gathered
 #pragma unroll
-        for (int i = 0; i < RL; ++i) wv[i] = row0 + i < len ? checked_index(__ldg(&ent[row0 + i].x), a.Vu, status) : 0;
+        for (int o = 0; o < R; ++o) wv[o] = wown[o];
+        all_gather<int, RL, Q, R>(wv);
         gather_rows<VRP, P, RL>(rv, q.it.KT, a.kprec, wv, ql);
     }
-    permute_rows<RL, P, Q, R>(rv, ql);
 
     bool bad = false;
     for (int it = 0; it < q.t; ++it) {
@@ -266,7 +255,7 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
                 }
             }
         }
-        all_gather<RL, Q, R>(tv);
+        all_gather<float, RL, Q, R>(tv);
         float2 acc[P / 2];
 #pragma unroll
         for (int k = 0; k < P / 2; ++k) acc[k] = make_float2(0.f, 0.f);
@@ -309,12 +298,12 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
         }
     }
     {
-        int wv[RL];   // the word ids again (the registers were free during the iterations)
+        int wv[RL];   // the word ids again
 #pragma unroll
-        for (int i = 0; i < RL; ++i) wv[i] = row0 + i < len ? checked_index(__ldg(&ent[row0 + i].x), a.Vu, status) : 0;
+        for (int o = 0; o < R; ++o) wv[o] = wown[o];
+        all_gather<int, RL, Q, R>(wv);
         gather_rows<VRP, P, RL>(rv, q.it.KMT, a.kprec, wv, ql);
     }
-    permute_rows<RL, P, Q, R>(rv, ql);
     double dist = 0.0;
     {
         float tv[RL];
