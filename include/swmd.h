@@ -108,7 +108,8 @@ typedef struct swmd_options {
                               1 = K^T rows in registers, whole rows per lane (v_r <= 32),
                               2 = rows staged in shared memory, 3 = rows re-gathered from
                               L2 each iteration, 4 = K^T rows in registers split by columns
-                              over a team of VRP / 4 lanes (documents of at most 32 words;
+                              (eight per lane) over row groups of VRP / 8 lanes, one to
+                              four groups per document (documents of at most 32 words;
                               v_r padded to a power of two from 16 to 128; on a corpus with
                               longer documents 4 acts as 0) */
     float tol;             /* 0 (default): exactly max_iter x-updates, as the paper's

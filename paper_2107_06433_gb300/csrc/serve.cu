@@ -3,11 +3,14 @@
 // Section III-D and Section V run many source documents against the same
 // targets; here that is (1) swmd_query_batch, a host call that runs a list of
 // queries over the resident corpus, and (2) a server that keeps the corpus on
-// the device and admits queries continuously: each admitted query gets a slot
-// (its own stream, parameter block and staging) and device memory for its K^T,
+// the device and admits queries continuously.  Each admitted query gets a slot
+// (parameter block, pinned staging, an event) and device memory for its K^T,
 // KM^T (and u on the per-iteration paths) carved from a fixed arena, so
-// admission is by the bytes a query of v_r words needs.  Queries admitted while
-// others run overlap on the device; finished slots are refilled at once.
+// admission is by the bytes a query of v_r words needs.  Queries on the
+// column-split solver are admitted in groups (same layout and cost split) that
+// run as one batched cost launch and one multi-query solver launch on the batch
+// lane, two groups deep, so the next group is queued while one runs; other
+// queries run alone on their slot's stream.  Finished slots are refilled at once.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
