@@ -8,23 +8,29 @@
 // WMD_j = sum_w c_wj (KM^T[w] . u_j) / (K^T[w] . u_j) (type 2).  A_j does not
 // change between iterations, so it is gathered once and kept in registers.
 //
-// Lanes.  A row group of Q = VRP / 8 lanes holds rows of A_j: lane q holds columns [P q, P q + P) of
-// every row of the group (LMAX rows in all, the document's length rounded up to
-// its bucket; rows past the end are masked), of u_j and of acc.  acc = A_j^T tau then
-// needs no exchange.  The dots s = A_j u_j are partial over the lane's columns and
-// are finished by a reduce-scatter over the team: after it lane q holds the full
-// dots of rows [qR, qR + R), R = LMAX / Q, computes their tau, and an all-gather
-// gives every lane all of tau.  Both are log2(Q) butterfly steps that move half of
-// the remaining values each (LMAX (1 - 1/Q) shuffles per lane and direction).  For
-// the butterfly to need no selects, lane q stores row block b ^ q (blocks of R
-// rows) in register block b: then at every step all lanes keep the same register
-// blocks and send the same others.  The lane reads its word ids in that order, so
-// its gathers fill the register blocks directly (a lane's slice of one row is one
-// 8-column vector load, whichever row it is).
+// Lanes.  A document of LMAX rows (its length rounded up to its bucket; rows past
+// the end are masked) is held by a team of G row groups of Q = VRP / 8 lanes; group
+// g holds rows [g RL, g RL + RL), RL = LMAX / G (at most 12, 16 in 128-column
+// layouts), and lane q of a group holds columns [P q, P q + P), P = 8, of each of
+// them.  acc = A_j^T tau is then partial over the groups only, the dots s = A_j u_j
+// partial over the Q lanes of a group.
 //
-// A document of up to 12 rows per lane (16 in 128-column layouts) is one row
-// group; longer ones are G row groups (the team), whose partial acc are summed with
-// shuffles.
+// Rows.  The dots are finished by a reduce-scatter over the group's Q lanes: after
+// it lane q holds the full dots of rows [qR, qR + R), R = RL / Q, computes their tau,
+// and an all-gather gives every lane of the group all of tau.  Both are log2(Q)
+// butterfly steps that move half of the remaining values each.  For the butterfly
+// to need no selects, lane q stores row block b ^ q (blocks of R rows) in register
+// block b: then at every step all lanes keep the same register blocks and send the
+// same others.  The lane reads its word ids in that order (its own R ids,
+// all-gathered the same way), so its gathers fill the register blocks directly.
+//
+// Columns, likewise over the G groups: group g stores column block c ^ g (blocks of
+// P / G columns of the lane's slice) in register block c, the partial acc go through
+// a reduce-scatter over the groups (group g ends with column block g), each group
+// takes u = r / acc for its P / G columns only, and an all-gather hands u back to
+// every group.  The final step reads KM^T in natural column order and puts u back
+// in that order once.
+//
 // Packed f32x2 FMAs work on column pairs of a row: a row's dot is P / 2 of them
 // plus one add, its contribution to acc another P / 2.
 //
@@ -60,7 +66,7 @@ __device__ __forceinline__ float2 widen2(uint32_t w, int kprec) {
     return __half22float2(h);
 }
 
-// P consecutive 32-bit words (P = 4 or 8) of the read-only path, one vector load.
+// P consecutive 32-bit words (P = 1, 2, 4 or 8) of the read-only path, one vector load.
 template <int P>
 __device__ __forceinline__ void ldg_words(const void *p, uint32_t (&w)[P]) {
     if constexpr (P == 8) {
@@ -69,33 +75,83 @@ __device__ __forceinline__ void ldg_words(const void *p, uint32_t (&w)[P]) {
             : "l"(p));
     } else if constexpr (P == 4) {
         asm("ld.global.nc.v4.b32 {%0,%1,%2,%3}, [%4];" : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "l"(p));
-    } else {
+    } else if constexpr (P == 2) {
         asm("ld.global.nc.v2.b32 {%0,%1}, [%2];" : "=r"(w[0]), "=r"(w[1]) : "l"(p));
+    } else {
+        asm("ld.global.nc.b32 %0, [%1];" : "=r"(w[0]) : "l"(p));
     }
 }
 
+// Swaps register blocks kb and kb ^ bit (blocks of P / G values) for every bit set
+// in g: natural column order <-> the XOR block order of group g.
+template <int P, int G>
+__device__ __forceinline__ void swap_blocks(float (&x)[P], int g) {
+    constexpr int B = P / G;
+#pragma unroll
+    for (int bit = 1; bit < G; bit <<= 1) {
+        const bool sw = (g & bit) != 0;
+#pragma unroll
+        for (int kb = 0; kb < G; ++kb) {
+            if (kb & bit) continue;
+#pragma unroll
+            for (int e = 0; e < B; ++e) {
+                const float lo = x[kb * B + e], hi = x[(kb ^ bit) * B + e];
+                x[kb * B + e] = sw ? hi : lo;
+                x[(kb ^ bit) * B + e] = sw ? lo : hi;
+            }
+        }
+    }
+}
+
+// How a lane puts its slice of a K^T row into the XOR column-block order: one vector
+// load per column block, or one whole-slice load and conditional swaps (fewer L1
+// requests, more registers).  Timed per layout on the 1,000,000-document workload: the
+// swaps win at 16 and 64 columns, the block loads at 32 and 128.
+__host__ __device__ constexpr bool cols_swap_blocks(int vrp) { return vrp == 16 || vrp == 64; }
+
 // Columns [P ql, P ql + P) of the rows of words wv[i] (word-major layout of VRP
-// columns), widened to float.  Rows past the document's end (wv[i] < 0) are not
-// loaded: zeros, whose tau is masked to 0.  One unrolled loop per storage type, so
-// all RL loads of a lane are in flight together.
-template <int VRP, int P, int RL>
+// columns), widened to float; PERM: in group g's column order (register block kb of
+// B = P / G columns holds column block kb ^ g), else in natural order.  Rows past the
+// document's end (wv[i] < 0) are not loaded: zeros, whose tau is masked to 0.  One
+// unrolled loop per storage type, so all loads of a lane are in flight together.
+template <int VRP, int P, int G, int RL, bool PERM = true>
 __device__ __forceinline__ void gather_rows(float (&rv)[RL][P], const void *base, int kprec, const int (&wv)[RL],
-                                            int ql) {
+                                            int ql, int g) {
+    constexpr bool SWAP_PERM = cols_swap_blocks(VRP);
+    constexpr int B = (PERM && !SWAP_PERM) ? P / G : P;
+    constexpr int GL = (PERM && !SWAP_PERM) ? G : 1;
     if (kprec == 0) {
         const float *b = reinterpret_cast<const float *>(base) + ql * P;
 #pragma unroll
         for (int i = 0; i < RL; ++i) {
             uint32_t w[P] = {};
-            if (wv[i] >= 0) ldg_words<P>(b + (long)wv[i] * VRP, w);
+            if (wv[i] >= 0) {
+#pragma unroll
+                for (int kb = 0; kb < GL; ++kb) {
+                    uint32_t wb[B];
+                    ldg_words<B>(b + (long)wv[i] * VRP + (GL > 1 ? (kb ^ g) * B : 0), wb);
+#pragma unroll
+                    for (int e = 0; e < B; ++e) w[kb * B + e] = wb[e];
+                }
+            }
 #pragma unroll
             for (int k = 0; k < P; ++k) rv[i][k] = __uint_as_float(w[k]);
+            if constexpr (PERM && SWAP_PERM) swap_blocks<P, G>(rv[i], g);
         }
     } else {
         const unsigned short *b = reinterpret_cast<const unsigned short *>(base) + ql * P;
         uint32_t raw[RL][P / 2] = {};
 #pragma unroll
         for (int i = 0; i < RL; ++i)
-            if (wv[i] >= 0) ldg_words<P / 2>(b + (long)wv[i] * VRP, raw[i]);
+            if (wv[i] >= 0) {
+#pragma unroll
+                for (int kb = 0; kb < GL; ++kb) {
+                    uint32_t wb[B / 2];
+                    ldg_words<B / 2>(b + (long)wv[i] * VRP + (GL > 1 ? (kb ^ g) * B : 0), wb);
+#pragma unroll
+                    for (int e = 0; e < B / 2; ++e) raw[i][kb * (B / 2) + e] = wb[e];
+                }
+            }
 #pragma unroll
         for (int i = 0; i < RL; ++i)
 #pragma unroll
@@ -104,6 +160,9 @@ __device__ __forceinline__ void gather_rows(float (&rv)[RL][P], const void *base
                 rv[i][2 * k] = f.x;
                 rv[i][2 * k + 1] = f.y;
             }
+        if constexpr (PERM && SWAP_PERM)
+#pragma unroll
+            for (int i = 0; i < RL; ++i) swap_blocks<P, G>(rv[i], g);
     }
 }
 
@@ -171,10 +230,13 @@ __device__ __forceinline__ double dot_fp64(const void *base, int kprec, int w, c
 template <int VRP, int G, int RL>
 __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &q, int4 tk, int lane,
                                           float *su) {
-    constexpr int P = cols_p(VRP), Q = VRP / P, R = RL / Q, TEAM = G * Q;
+    constexpr int P = cols_p(VRP), Q = VRP / P, R = RL / Q, TEAM = G * Q, B = P / G;
     static_assert(Q >= 1 && Q <= 32 && (Q & (Q - 1)) == 0, "row groups of a power of two lanes");
     static_assert(RL % Q == 0 && R >= 1 && TEAM <= 32 && (G & (G - 1)) == 0, "whole row blocks");
+    static_assert(B >= 2 && B * G == P, "column blocks of at least two (one 32-bit word of 16-bit K)");
     const int team = lane / TEAM, g = (lane / Q) % G, ql = lane % Q;
+    // the column of the lane's slice held in register k: block k / B holds block (k / B) ^ g
+    auto col_of = [g](int k) { return (((k / B) ^ g) * B) + k % B; };
     const bool has = team < tk.y;
     const int doc = tk.x + team;
     int beg = 0, len = 0;
@@ -211,13 +273,13 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
         wown[o] = e.x;
         cown[o] = __int_as_float(e.y);
     }
-    float rr[P], u[P];
+    // u in the lane's column order (register k: column ql P + col_of(k)); r of the B
+    // columns whose u this lane computes (column block g of its slice)
+    float rr[B], u[P];
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-        const int col = ql * P + k;
-        rr[k] = __ldg(q.it.r + col);
-        u[k] = has && col < vr ? u0 : 0.f;
-    }
+    for (int k = 0; k < P; ++k) u[k] = has && ql * P + col_of(k) < vr ? u0 : 0.f;
+#pragma unroll
+    for (int e = 0; e < B; ++e) rr[e] = __ldg(q.it.r + ql * P + g * B + e);
     // the group's rows of K^T in register-block order, all loads in flight at once
     float rv[RL][P];
     {
@@ -225,7 +287,7 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
 #pragma unroll
         for (int o = 0; o < R; ++o) wv[o] = wown[o];
         all_gather<int, RL, Q, R>(wv);
-        gather_rows<VRP, P, RL>(rv, q.it.KT, a.kprec, wv, ql);
+        gather_rows<VRP, P, G, RL>(rv, q.it.KT, a.kprec, wv, ql, g);
     }
 
     bool bad = false;
@@ -266,22 +328,28 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
             for (int k = 0; k < P / 2; ++k)
                 acc[k] = __ffma2_rn(make_float2(rv[i][2 * k], rv[i][2 * k + 1]), t2, acc[k]);
         }
-        // the row groups' partial sums (a + b = b + a: every group gets the same u)
+        // the row groups' partial sums: a reduce-scatter over the G groups leaves
+        // group g the full acc of column block g (register block 0) ...
 #pragma unroll
-        for (int m = Q; m < TEAM; m <<= 1)
+        for (int m = G / 2; m >= 1; m >>= 1)
 #pragma unroll
-            for (int k = 0; k < P / 2; ++k) {
-                acc[k].x += __shfl_xor_sync(kFull, acc[k].x, m);
-                acc[k].y += __shfl_xor_sync(kFull, acc[k].y, m);
+            for (int k = 0; k < m * B / 2; ++k) {
+                acc[k].x += __shfl_xor_sync(kFull, acc[k + m * B / 2].x, m * Q);
+                acc[k].y += __shfl_xor_sync(kFull, acc[k + m * B / 2].y, m * Q);
             }
+        // ... whose u it computes ...
 #pragma unroll
-        for (int k = 0; k < P; ++k) {
-            const int col = ql * P + k;
-            const bool live = has && col < vr;
-            const float nu = live ? rr[k] * rcp_approx((k & 1) ? acc[k / 2].y : acc[k / 2].x) : 0.f;
+        for (int e = 0; e < B; ++e) {
+            const bool live = has && ql * P + g * B + e < vr;
+            const float nu = live ? rr[e] * rcp_approx((e & 1) ? acc[e / 2].y : acc[e / 2].x) : 0.f;
             bad |= live && !(nu < INFINITY);
-            u[k] = nu;
+            u[e] = nu;
         }
+        // ... and an all-gather gives every group all P (register block b from group g ^ b)
+#pragma unroll
+        for (int m = 1; m < G; m <<= 1)
+#pragma unroll
+            for (int e = 0; e < m * B; ++e) u[m * B + e] = __shfl_xor_sync(kFull, u[e], m * Q);
     }
 
     // final step: s = K^T[w].u and m = KM^T[w].u per nonzero, WMD = sum c m / s
@@ -302,8 +370,9 @@ __device__ __forceinline__ void cols_task(const ColArgs &a, const ResidentArgs &
 #pragma unroll
         for (int o = 0; o < R; ++o) wv[o] = wown[o];
         all_gather<int, RL, Q, R>(wv);
-        gather_rows<VRP, P, RL>(rv, q.it.KMT, a.kprec, wv, ql);
+        gather_rows<VRP, P, G, RL, false>(rv, q.it.KMT, a.kprec, wv, ql, g);   // natural order
     }
+    swap_blocks<P, G>(u, g);   // u back to natural column order, like the KM^T rows
     double dist = 0.0;
     {
         float tv[RL];
