@@ -37,6 +37,7 @@ no collective on the data path) and rank 0 prints the line.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -75,6 +76,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-pairs", action="store_true")
+    ap.add_argument("--max-iter", type=int, default=None,
+                    help="x-updates per query in the timed step (default: the workload's, 15); "
+                         "0 times the gathers and the final step alone")
     return ap.parse_args()
 
 
@@ -692,6 +696,8 @@ def main():
     nbuild.build()
 
     w = synth.WORKLOADS[args.workload]
+    if args.max_iter is not None:
+        w = dataclasses.replace(w, max_iter=args.max_iter)
     # weak scaling: rank r holds its own partition of w.N documents (its own seed)
     E, C, (qi, qw) = synth.make(w, seed=synth.SEED + 7919 * rank)
     if rank > 0:   # every rank answers the same query

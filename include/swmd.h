@@ -507,7 +507,9 @@ SWMD_API int swmd_serve_submit(swmd_server *srv, const int32_t *h_ids, const flo
 
 /* Waits up to timeout_ms (< 0: forever) for the result of `ticket` and copies
  * its N distances to h_out_dist.  SWMD_ETIMEDOUT if it is not ready in time
- * (the request stays queued and can be waited for again). */
+ * (the request stays queued and can be waited for again).  A result is handed out
+ * once: a wait on a ticket already collected, or collected by a concurrent waiter,
+ * returns SWMD_EINVAL. */
 SWMD_API int swmd_serve_wait(swmd_server *srv, uint64_t ticket, double *h_out_dist, int32_t timeout_ms);
 
 SWMD_API int swmd_serve_stats(swmd_server *srv, swmd_serve_stats_t *out);

@@ -136,7 +136,7 @@ struct swmd_corpus {
     float *pair_kws = nullptr;     // 1-to-1 pairs: per-block K and K.*M regions too large
     size_t pair_kws_bytes = 0;     // for shared memory (grown on demand)
     int64_t base_bytes = 0;
-    void *h_io = nullptr;          // pinned staging of swmd_query: [ids | weights] then [distances | status]
+    void *h_io = nullptr;          // pinned staging of swmd_query: [ids | weights] then the status word
     size_t h_io_in_bytes = 0;
 
     std::map<swmd::GraphKey, cudaGraphExec_t> graphs;

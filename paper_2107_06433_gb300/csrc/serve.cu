@@ -100,8 +100,8 @@ struct ServerSlot {
     cudaEvent_t done = nullptr;
     int32_t *h_q = nullptr;   // pinned staging
     float *h_r = nullptr;
-    double *h_out = nullptr;
     int *h_status = nullptr;
+    std::vector<double> result;   // the finished query's distances, copied from ws.out
     std::shared_ptr<Request> req;
     size_t arena_bytes = 0;
     void *arena_ptr = nullptr;
@@ -136,6 +136,8 @@ struct swmd_server {
     swmd_serve_config cfg{};
     std::vector<ServerSlot> slots;
     std::vector<BatchLane> lanes;
+    cudaStream_t copy_stream = nullptr;   // finished queries' distances to host memory
+    std::vector<std::vector<double>> spare;   // result buffers given back by waiters (pages touched)
     Arena arena;
     char *arena_mem = nullptr;
     std::mutex m;
@@ -160,9 +162,8 @@ void finish(swmd_server *S, ServerSlot &sl, int code, const std::string &err) {
     R.err = err;
     R.state = 2;
     R.t_done = now_s();
-    if (code == SWMD_OK || code == SWMD_ENUMERIC) {
-        R.result.assign(sl.h_out, sl.h_out + S->c->Nl);
-    }
+    if (code == SWMD_OK || code == SWMD_ENUMERIC) R.result = std::move(sl.result);
+    sl.result = std::vector<double>();
     S->completed++;
     S->lat_ms.push_back((R.t_done - R.t_submit) * 1e3);
     S->t_last = R.t_done;
@@ -260,7 +261,6 @@ int launch_group(swmd_server *S, int li, int buf, const std::vector<ServerSlot *
                                 reinterpret_cast<const ResidentArgs *>(d_args + off_r), L.stream);
     if (rc) return rc;
     for (ServerSlot *sl : members) {
-        SWMD_CK(cudaMemcpyAsync(sl->h_out, sl->ws.out, sizeof(double) * c->Nl, cudaMemcpyDeviceToHost, L.stream));
         SWMD_CK(cudaMemcpyAsync(sl->h_status, sl->ws.status, sizeof(int), cudaMemcpyDeviceToHost, L.stream));
         SWMD_CK(cudaEventRecord(sl->done, L.stream));
     }
@@ -295,7 +295,6 @@ int launch_on_slot(swmd_server *S, ServerSlot &sl) {
                            sl.ws.status, sl.stream, false, path);
     }
     if (rc) return rc;
-    SWMD_CK(cudaMemcpyAsync(sl.h_out, sl.ws.out, sizeof(double) * c->Nl, cudaMemcpyDeviceToHost, sl.stream));
     SWMD_CK(cudaMemcpyAsync(sl.h_status, sl.ws.status, sizeof(int), cudaMemcpyDeviceToHost, sl.stream));
     SWMD_CK(cudaEventRecord(sl.done, sl.stream));
     return SWMD_OK;
@@ -408,6 +407,30 @@ void worker_main(swmd_server *S) {
             for (auto &f : failed) is_failed |= f.first == &sl;
             if (is_failed) continue;
             if (sl.req->state == 1 && cudaEventQuery(sl.done) == cudaSuccess) ready.push_back(&sl);
+        }
+        if (!ready.empty()) {
+            // the distances go from the slot's device buffer straight into host memory
+            // the request keeps (recycled buffers, their pages already touched)
+            lk.lock();
+            for (auto *sl : ready)
+                if (!S->spare.empty()) {
+                    sl->result = std::move(S->spare.back());
+                    S->spare.pop_back();
+                }
+            lk.unlock();
+            cudaError_t ce = cudaSuccess;
+            for (auto *sl : ready) {
+                sl->result.resize((size_t)S->c->Nl);
+                if (ce == cudaSuccess)
+                    ce = cudaMemcpyAsync(sl->result.data(), sl->ws.out, sizeof(double) * S->c->Nl,
+                                         cudaMemcpyDeviceToHost, S->copy_stream);
+            }
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(S->copy_stream);
+            if (ce != cudaSuccess) {
+                const int rc = cuda_fail(ce, "serve: copy distances");
+                for (auto *sl : ready) failed.push_back({sl, rc});
+                ready.clear();
+            }
         }
         const std::string last = swmd_last_error();
         lk.lock();
@@ -751,7 +774,7 @@ int swmd_serve_start(swmd_corpus *c, const swmd_serve_config *cfg_in, swmd_serve
             free_slot(S->c, sl.ws);
             if (sl.stream) cudaStreamDestroy(sl.stream);
             if (sl.done) cudaEventDestroy(sl.done);
-            cudaFreeHost(sl.h_q); cudaFreeHost(sl.h_r); cudaFreeHost(sl.h_out); cudaFreeHost(sl.h_status);
+            cudaFreeHost(sl.h_q); cudaFreeHost(sl.h_r); cudaFreeHost(sl.h_status);
         }
         for (auto &L : S->lanes) {
             if (L.stream) cudaStreamDestroy(L.stream);
@@ -760,6 +783,7 @@ int swmd_serve_start(swmd_corpus *c, const swmd_serve_config *cfg_in, swmd_serve
                 cudaFreeHost(L.h_args[b]);
             }
         }
+        if (S->copy_stream) cudaStreamDestroy(S->copy_stream);
         corpus_free(S->c, S->arena_mem);
         delete S;
         return code;
@@ -767,11 +791,15 @@ int swmd_serve_start(swmd_corpus *c, const swmd_serve_config *cfg_in, swmd_serve
     cudaError_t e = corpus_malloc(c, reinterpret_cast<void **>(&S->arena_mem), (size_t)cfg.memory_budget);
     if (e != cudaSuccess) return bail(cuda_fail(e, "swmd_serve_start: arena"));
     S->arena.init(S->arena_mem, (size_t)cfg.memory_budget);
+    if ((e = cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(cuda_fail(e, "swmd_serve_start: copy stream"));
+    // result buffers for the first max_batch queries, their pages touched now (a copy
+    // into fresh memory would first fault them in)
+    S->spare.resize((size_t)cfg.max_batch, std::vector<double>((size_t)std::max(c->Nl, 1)));
     S->slots.resize((size_t)cfg.max_batch);
     const int vrp = max_vrp_of(c->opt.max_vr);
     for (auto &sl : S->slots) {
         Slot &w = sl.ws;
-        int64_t b = 0;
         e = corpus_malloc(c, reinterpret_cast<void **>(&w.q_ids), sizeof(int) * vrp);
         if (e == cudaSuccess) e = corpus_malloc(c, reinterpret_cast<void **>(&w.r), sizeof(float) * vrp);
         if (e == cudaSuccess) e = corpus_malloc(c, reinterpret_cast<void **>(&w.qp), sizeof(QParams));
@@ -785,10 +813,8 @@ int swmd_serve_start(swmd_corpus *c, const swmd_serve_config *cfg_in, swmd_serve
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_q, sizeof(int32_t) * vrp);
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_r, sizeof(float) * vrp);
-        if (e == cudaSuccess) e = cudaMallocHost(&sl.h_out, sizeof(double) * std::max(c->Nl, 1));
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_status, sizeof(int));
         if (e != cudaSuccess) return bail(cuda_fail(e, "swmd_serve_start: slot"));
-        (void)b;
         w.vrp_cap = vrp;
         w.kprec = c->opt.k_precision;
         w.external = true;
@@ -855,16 +881,33 @@ int swmd_serve_wait(swmd_server *S, uint64_t ticket, double *h_out_dist, int32_t
     bool ok = true;
     if (timeout_ms < 0) S->cv_done.wait(lk, ready);
     else ok = S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
-    --S->waiters;
-    S->cv_done.notify_all();   // a stopping server waits for the last waiter to leave
-    if (!ok)
+    if (!ok) {
+        --S->waiters;
+        S->cv_done.notify_all();   // a stopping server waits for the last waiter to leave
         return set_error(SWMD_ETIMEDOUT, "swmd_serve_wait: ticket %llu not ready after %d ms",
                          (unsigned long long)ticket, timeout_ms);
+    }
     auto again = S->table.find(ticket);   // another waiter of the same ticket may have taken it
-    if (again != S->table.end()) S->table.erase(again);
-    if (!R->result.empty() && h_out_dist)
-        std::memcpy(h_out_dist, R->result.data(), sizeof(double) * R->result.size());
-    if (R->code) return set_error(R->code, "%s", R->err.c_str());
+    if (again == S->table.end()) {
+        --S->waiters;
+        S->cv_done.notify_all();
+        return set_error(SWMD_EINVAL, "swmd_serve_wait: ticket %llu was collected by another waiter",
+                         (unsigned long long)ticket);
+    }
+    S->table.erase(again);
+    std::vector<double> res = std::move(R->result);
+    const int code = R->code;
+    const std::string err = R->err;
+    // the copy into the caller's buffer runs outside the lock (the server stays alive
+    // while this thread counts as a waiter); the buffer then goes back to the pool
+    lk.unlock();
+    if (!res.empty() && h_out_dist) std::memcpy(h_out_dist, res.data(), sizeof(double) * res.size());
+    lk.lock();
+    if (!res.empty() && S->spare.size() < 2 * S->slots.size()) S->spare.push_back(std::move(res));
+    --S->waiters;
+    S->cv_done.notify_all();
+    lk.unlock();
+    if (code) return set_error(code, "%s", err.c_str());
     return SWMD_OK;
 }
 
@@ -918,7 +961,7 @@ int swmd_serve_stop(swmd_server *S) {
         free_slot(S->c, sl.ws);
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.done) cudaEventDestroy(sl.done);
-        cudaFreeHost(sl.h_q); cudaFreeHost(sl.h_r); cudaFreeHost(sl.h_out); cudaFreeHost(sl.h_status);
+        cudaFreeHost(sl.h_q); cudaFreeHost(sl.h_r); cudaFreeHost(sl.h_status);
     }
     for (auto &L : S->lanes) {
         if (L.stream) {
@@ -930,6 +973,7 @@ int swmd_serve_stop(swmd_server *S) {
             cudaFreeHost(L.h_args[b]);
         }
     }
+    if (S->copy_stream) cudaStreamDestroy(S->copy_stream);
     corpus_free(S->c, S->arena_mem);
     delete S;
     return SWMD_OK;
