@@ -452,13 +452,13 @@ SWMD_API int swmd_autotune_batch(swmd_corpus *corpus, int32_t n_queries, const i
  *   h_lambdas[n_queries] (float, host): lambda of each query.
  *   h_out[n_queries * N] (double, host): row i = the distances of query i.
  * Each query takes its own path (swmd_resolve_path).  The resident queries of one
- * K^T layout and solver run as one batched cost launch and one solver launch.
- * With the column-split solver that launch walks (query group, document task)
- * tiles: a group is swmd_options.queries_per_tile queries (or the autotuned or
- * L2-sized number), a task's nonzeros are read from DRAM once per group, and the
- * groups follow one another inside the launch.  The other resident solvers run
- * the group's queries as grid rows on corpora under 20,000 documents and one
- * launch pair per query above.  The per-iteration queries run one after another.  The device
+ * K^T layout and solver run as batched cost and solver launches.  With the
+ * column-split solver a launch pair takes one group of swmd_options.queries_per_tile
+ * queries (or the autotuned or L2-sized number), so the group's K^T is still in L2
+ * when its solver runs, and the solver walks (query, document task) tiles: a
+ * task's nonzeros are read from DRAM once for the group.  The other resident
+ * solvers run the layout's queries as grid rows of one launch pair on corpora
+ * under 20,000 documents and one launch pair per query above.  The per-iteration queries run one after another.  The device
  * work of the whole call is captured once per batch shape (the queries' paths and
  * sizes, the per-iteration queries' lambdas, max_iter) as a CUDA graph and replayed
  * on the next batch of that shape.  The workspace grows on demand (cudaMalloc) and

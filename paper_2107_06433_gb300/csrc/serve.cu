@@ -255,11 +255,18 @@ int launch_group(swmd_server *S, int li, int buf, const std::vector<ServerSlot *
     }
     SWMD_CK(cudaMemcpyAsync(d_args, h_args, lane_args_bytes(n), cudaMemcpyHostToDevice, L.stream));
     SWMD_CK(launch_prep_batch(reinterpret_cast<const PrepArgs *>(d_args), n, c->V, L.stream));
-    SWMD_CK(launch_cost_batch(hc[0], vrp, kprec, n, reinterpret_cast<const CostArgs *>(d_args + off_c), L.stream));
+    // the cost and solver launches one tile group at a time: the group's K^T and KM^T,
+    // just written, are still in L2 when its solver runs
     const Mapping m = walk_mapping(c, vrp, SWMD_PATH_RESIDENT);
-    int rc = run_resident_batch(c, hr[0], m, kprec, members[0]->req->vr, n,
-                                reinterpret_cast<const ResidentArgs *>(d_args + off_r), L.stream);
-    if (rc) return rc;
+    const int step = cols_queries_per_group(c, vrp, kprec);
+    for (int j0 = 0; j0 < n; j0 += step) {
+        const int nj = std::min(step, n - j0);
+        SWMD_CK(launch_cost_batch(hc[j0], vrp, kprec, nj, reinterpret_cast<const CostArgs *>(d_args + off_c) + j0,
+                                  L.stream));
+        int rc = run_resident_batch(c, hr[j0], m, kprec, members[j0]->req->vr, nj,
+                                    reinterpret_cast<const ResidentArgs *>(d_args + off_r) + j0, L.stream);
+        if (rc) return rc;
+    }
     for (ServerSlot *sl : members) {
         SWMD_CK(cudaMemcpyAsync(sl->h_status, sl->ws.status, sizeof(int), cudaMemcpyDeviceToHost, L.stream));
         SWMD_CK(cudaEventRecord(sl->done, L.stream));
@@ -670,9 +677,12 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
                 // (each gathers its own K^T); there the group's queries run one after
                 // another (still one graph, no host round trips).  Smaller corpora run
                 // the group as one batched cost and one batched solver launch.
-                // The column-split solver walks the whole group in one launch (its
-                // tiles keep one query group's K^T in L2 at a time).
-                const int step = (c->Nl >= kAutoResidentDocs && std::get<1>(gstart[gi].first) != kSolverCols) ? 1 : ng;
+                // The column-split solver takes a tile group of queries per cost and
+                // solver launch pair: the group's K^T and KM^T, just written, are still
+                // in L2 when its solver runs.
+                const int step = std::get<1>(gstart[gi].first) == kSolverCols ? cols_queries_per_group(c, v, kprec)
+                                 : c->Nl >= kAutoResidentDocs                  ? 1
+                                                                               : ng;
                 for (int j0 = 0; j0 < ng; j0 += step) {
                     const int nj = std::min(step, ng - j0);
                     SWMD_CK(launch_cost_batch(cost_g[g0 + j0], v, kprec, nj,

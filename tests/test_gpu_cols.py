@@ -159,8 +159,9 @@ def test_large_workload_sampled():
 
 @pytest.mark.parametrize("qpt", [1, 3, 8])
 def test_multi_query_launch_equals_alone_bitwise(short_docs, qpt):
-    """swmd_query_batch runs each column-split layout group as one launch over (query
-    group, document task) tiles; every tile size gives the single queries' bits."""
+    """swmd_query_batch runs the column-split queries of a layout in groups of qpt,
+    one cost and one multi-query solver launch per group, the solver over (query,
+    document task) tiles; every group size gives the single queries' bits."""
     E, C = short_docs
     corpus = swmd.corpus_from_synth(E, C, path="resident", queries_per_tile=qpt)
     qs = synth.batch_queries(C.V, 17, 1, 128, seed=60 + qpt)
