@@ -1,8 +1,8 @@
 """The server's failure paths, made on the host (no GPU fault involved): admission
 refused for a memory budget below one query, submissions refused at the queue's
 capacity, a wait that runs out of time, pending requests failed by a stop (and
-their blocked waiters released), and tuning / option changes refused while a
-server is attached.
+their blocked waiters released), a result handed out once to two concurrent
+waiters, and tuning / option changes refused while a server is attached.
 
 A long query (20,000 or 200,000 x-updates on the 5,000-document workload, tens of
 ms to about a second on the device) keeps the server's only slot busy while the
@@ -124,3 +124,32 @@ def test_tuning_and_options_wait_for_the_server(served):
     finally:
         srv.stop()
     swmd.swmd_corpus_set_options(corpus, k_precision="fp32")   # allowed again
+
+
+def test_two_waiters_of_one_ticket_get_it_once(served):
+    """Both block until the query is done; one receives the distances, the other
+    SWMD_EINVAL (the result is handed out once)."""
+    E, C, qi, qw, corpus = served
+    srv = swmd.swmd_serve_start(corpus, max_batch=1, memory_budget=1 << 30)
+    try:
+        tk = swmd.swmd_serve_submit(srv, qi, qw, 1.0, LONG)
+        got = {}
+
+        def waiter(name):
+            try:
+                got[name] = swmd.swmd_serve_wait(srv, tk, -1)
+            except swmd.SwmdError as err:
+                got[name] = err.code
+
+        threads = [threading.Thread(target=waiter, args=(n,)) for n in ("a", "b")]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join(timeout=120)
+            assert not th.is_alive()
+        arrays = [v for v in got.values() if isinstance(v, np.ndarray)]
+        codes = [v for v in got.values() if not isinstance(v, np.ndarray)]
+        assert len(arrays) == 1 and codes == [swmd.SWMD_EINVAL], got
+        assert np.all(np.isfinite(arrays[0])) and np.all(arrays[0] > 0)
+    finally:
+        srv.stop()
