@@ -328,6 +328,21 @@ def test_batch_spanning_every_layout_equals_alone_bitwise(paper):
         np.testing.assert_array_equal(batch[i], swmd.swmd_query(corpus, qi, qw, 1.0, 15))
 
 
+def test_one_kernel_with_different_shared_memory_in_turn(paper):
+    """Two corpora whose shared-memory resident launches take different dynamic
+    shared memory (64-nonzero tiles, then tiles of about 110 KB), queried in turn in
+    one process: each launch sets the attribute it needs on its device, and every
+    query agrees with the oracle (a launcher that kept the first size would fail the
+    larger launch)."""
+    E, C, _ = paper
+    qi, qw = synth.query(np.random.default_rng(40), C.V, 40)
+    ref = oracle_wmd(E, C, qi, qw, 1.0, 15)
+    small = swmd.corpus_from_synth(E, C, path="resident", solver=2, tile_nnz=64)
+    large = swmd.corpus_from_synth(E, C, path="resident", solver=2)
+    for corpus in (small, large, small, large):
+        assert rel_err(swmd.swmd_query(corpus, qi, qw, 1.0, 15), ref) <= RTOL
+
+
 @pytest.mark.parametrize("vr", [5, 19, 32, 64])
 def test_autotune_then_query_matches_oracle(paper, vr):
     E, C, _ = paper
