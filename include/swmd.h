@@ -494,6 +494,8 @@ SWMD_API void swmd_default_serve_config(swmd_serve_config *cfg);
  * device batches as memory (K, K.*M and u of each query) frees up, and a batch
  * runs while later requests queue (continuous batching).  cfg may be NULL.
  * SWMD_ENOMEM if memory_budget is below the bytes one query of max_vr words needs.
+ * Host memory: max_batch result buffers of N doubles, recycled through
+ * swmd_serve_wait (up to 2 max_batch are kept).
  * While a server is attached, swmd_autotune and swmd_corpus_set_options on its
  * corpus are refused (SWMD_EINVAL): a request's path and layout are resolved once,
  * when it is admitted. */
