@@ -24,7 +24,8 @@ of the 1,000,000-document workload (V=500,000, d=300, documents of 5-30 Zipf wor
   serving    a query server over the resident 1,000,000-document corpus with BF16 K
              fed by Poisson arrivals at 50, 200 and 1000 queries/s (v_r uniform in
              [4,128]): queries/s and p50/p99 latency, against the same queries run
-             one at a time through swmd_query with FP32 K, and the BF16 error.
+             one at a time through swmd_query (FP32 and BF16 K) and through
+             swmd_query_batch (BF16 K, 16 per call), and the BF16 error.
   cpu_baseline  the FP64 oracle timed on the host cores on whole queries of the
              workload, and on one host thread on a document sample (`single_core`);
              the dense oracle on the 200-document workload and on 64 documents of the
@@ -651,6 +652,14 @@ def serving(swmd, synth, torch, rates=(50.0, 200.0, 1000.0), n=200, E=None, C=No
         lat16.append((time.perf_counter() - a) * 1e3)
     res["one_at_a_time_bf16"] = {"qps": n / (time.perf_counter() - t0), "p50_ms": float(np.percentile(lat16, 50)),
                                  "p99_ms": float(np.percentile(lat16, 99))}
+    # the same queries through swmd_query_batch, 16 per call (one cost and one
+    # multi-query solver launch per layout group of each call)
+    nb = 16
+    swmd.swmd_query_batch(c16, qs[:nb], 1.0, 15)
+    t0 = time.perf_counter()
+    for i in range(0, n, nb):
+        swmd.swmd_query_batch(c16, qs[i:i + nb], 1.0, 15)
+    res["batched_bf16"] = {"qps": n / (time.perf_counter() - t0), "queries_per_call": nb}
     served = {}
     err = 0.0
     for rate in rates:
