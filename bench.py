@@ -596,15 +596,19 @@ def batched(swmd, synth, torch):
             tr = swmd.swmd_autotune(corpus, vr, 2)
             paths[tr["path"]] = paths.get(tr["path"], 0) + 1
         tune_s = time.perf_counter() - t0
-        # the first call of a batch shape captures its graph; later calls replay it
+        # the first call of a batch shape runs eagerly, the second captures its
+        # graph; later calls replay it
         t0 = time.perf_counter()
         swmd.swmd_query_batch(corpus, qs, 1.0, 15)
         first = time.perf_counter() - t0
         t0 = time.perf_counter()
+        swmd.swmd_query_batch(corpus, qs, 1.0, 15)
+        second = time.perf_counter() - t0
+        t0 = time.perf_counter()
         out = swmd.swmd_query_batch(corpus, qs, 1.0, 15)
         tb = time.perf_counter() - t0
         row = {"batch_qps": len(qs) / tb, "batch_wmds_per_s": len(qs) * C.N / tb,
-               "batch_s": tb, "first_call_s": first, "autotune_s": tune_s,
+               "batch_s": tb, "first_call_s": first, "capture_call_s": second, "autotune_s": tune_s,
                "paths_chosen": {("fused" if k == 0 else "resident"): v for k, v in paths.items()}}
         if kp == "fp32":
             t0 = time.perf_counter()

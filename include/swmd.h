@@ -458,11 +458,12 @@ SWMD_API int swmd_autotune_batch(swmd_corpus *corpus, int32_t n_queries, const i
  * when its solver runs, and the solver walks (query, document task) tiles: a
  * task's nonzeros are read from DRAM once for the group.  The other resident
  * solvers run the layout's queries as grid rows of one launch pair on corpora
- * under 20,000 documents and one launch pair per query above.  The per-iteration queries run one after another.  The device
- * work of the whole call is captured once per batch shape (the queries' paths and
- * sizes, the per-iteration queries' lambdas, max_iter) as a CUDA graph and replayed
- * on the next batch of that shape.  The workspace grows on demand (cudaMalloc) and
- * is kept.  The result of each query equals its swmd_query result bit for bit.
+ * under 20,000 documents and one launch pair per query above.  The per-iteration
+ * queries run one after another.  The device work of the whole call runs eagerly
+ * the first time a batch shape (the queries' paths and sizes, the per-iteration
+ * queries' lambdas, max_iter) is seen, is captured as a CUDA graph the second
+ * time, and is replayed after that (up to 64 shapes are remembered).  The
+ * workspace grows on demand and is kept.  The result of each query equals its swmd_query result bit for bit.
  * Returns the first failing query's error, or SWMD_ENUMERIC if any query flagged
  * a NaN / infinity (the distances are still written). */
 SWMD_API int swmd_query_batch(swmd_corpus *corpus, int32_t n_queries, const int64_t *q_ptr,

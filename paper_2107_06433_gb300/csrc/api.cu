@@ -94,6 +94,7 @@ void clear_graphs(swmd_corpus *c) {
     c->graphs.clear();
     for (auto &kv : c->batch_graphs) cudaGraphExecDestroy(kv.second);
     c->batch_graphs.clear();
+    c->batch_seen.clear();
 }
 
 int status_to_code(int st) {

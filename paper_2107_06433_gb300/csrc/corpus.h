@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <map>
+#include <set>
 #include <mutex>
 #include <string>
 #include <tuple>
@@ -141,6 +142,7 @@ struct swmd_corpus {
 
     std::map<swmd::GraphKey, cudaGraphExec_t> graphs;
     std::map<std::vector<int64_t>, cudaGraphExec_t> batch_graphs;   // swmd_query_batch shapes
+    std::set<std::vector<int64_t>> batch_seen;   // shapes run once, eagerly (captured when seen again)
     std::map<std::tuple<int, int, int>, swmd::Mapping> tuned;  // (vr bucket, path, kprec)
     // autotuned resident-path settings per (v_r, K precision): solver, rows per lane, cost split
     std::map<std::pair<int, int>, std::tuple<int, int, int>> tuned_resident;

@@ -176,6 +176,10 @@ void finish(swmd_server *S, ServerSlot &sl, int code, const std::string &err) {
 }
 
 size_t up256(size_t n) { return (n + 255) & ~size_t(255); }
+
+// Batch shapes remembered (as captured graphs, or as seen once); beyond this many
+// the memory is dropped and shapes start over.
+constexpr size_t kMaxBatchShapes = 64;
 size_t lane_args_bytes(int n) {
     return up256(sizeof(PrepArgs) * n) + up256(sizeof(CostArgs) * n) + up256(sizeof(ResidentArgs) * n);
 }
@@ -718,7 +722,19 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
             }
         }
         auto it = c->batch_graphs.find(key);
-        if (it == c->batch_graphs.end()) {
+        if (it == c->batch_graphs.end() && !c->batch_seen.count(key)) {
+            // a shape seen for the first time runs eagerly: capturing and instantiating
+            // a graph pays only for shapes that come back
+            if (c->batch_seen.size() >= kMaxBatchShapes) c->batch_seen.clear();
+            c->batch_seen.insert(key);
+            int rc = body();
+            if (rc) return rc;
+        } else if (it == c->batch_graphs.end()) {
+            if (c->batch_graphs.size() >= kMaxBatchShapes) {
+                for (auto &kv : c->batch_graphs) cudaGraphExecDestroy(kv.second);
+                c->batch_graphs.clear();
+            }
+            c->batch_seen.erase(key);
             cudaGraph_t g = nullptr;
             SWMD_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
             int rc = body();
@@ -733,8 +749,10 @@ int swmd_query_batch(swmd_corpus *c, int32_t n_queries, const int64_t *q_ptr,
             cudaGraphDestroy(g);
             SWMD_CK(e);
             it = c->batch_graphs.emplace(key, ge).first;
+            SWMD_CK(cudaGraphLaunch(it->second, st));
+        } else {
+            SWMD_CK(cudaGraphLaunch(it->second, st));
         }
-        SWMD_CK(cudaGraphLaunch(it->second, st));
     }
     std::vector<int> h_status((size_t)n_queries, 0);
     SWMD_CK(cudaMemcpyAsync(h_out, d_out, sizeof(double) * (size_t)n_queries * c->Nl, cudaMemcpyDeviceToHost, st));

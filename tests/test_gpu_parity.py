@@ -414,8 +414,9 @@ def test_autotune_records_the_path(wide):
 
 
 def test_batch_graph_replays_new_inputs(paper, wide):
-    """A batch runs as one captured CUDA graph per shape; a second batch of the same
-    shape with other weights and lambdas replays it on the new inputs."""
+    """A batch shape runs eagerly the first time and as a captured CUDA graph the
+    second; the third batch of that shape, with other weights and lambdas than the
+    captured one, replays the graph on its own inputs."""
     for E, C in ((paper[0], paper[1]), wide):
         corpus = swmd.corpus_from_synth(E, C)
         qs1 = [synth.query(np.random.default_rng(10 + k), C.V, vr) for k, vr in enumerate((6, 19, 40))]
