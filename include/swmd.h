@@ -101,8 +101,11 @@ typedef struct swmd_options {
                               (0 = chosen from the query size) */
     int32_t tile_nnz;      /* resident path: nonzeros staged per block (0 = as many as fit
                               in about 100 KB of shared memory) */
-    int32_t cost_split;    /* cost kernel: threads sharing one word's embedding row
-                              (1, 2 or 4; 0 = 2, or 1 from 65,536 used words up) */
+    int32_t cost_split;    /* cost kernel: 0 = automatic (the tiled product-form kernel
+                              for layouts of 16, 32, 64 and 128 columns, else the row
+                              kernel with 2 threads per word, 1 from 65,536 used words
+                              up); 1, 2 or 4 = the row kernel with that many threads
+                              sharing one word's embedding row */
     int32_t solver;        /* resident path kernel: 0 = automatic (4 when every document has
                               at most 32 words, else 1 for v_r <= 32 and 2 above),
                               1 = K^T rows in registers, whole rows per lane (v_r <= 32),
@@ -400,7 +403,7 @@ typedef struct swmd_tune_result {
     int32_t vrp;           /* the resident layout of the chosen solver (VRP for v_r) */
     int32_t solver;        /* chosen resident solver (see swmd_options.solver) */
     int32_t nnz_per_lane;  /* chosen rows of K^T per lane (register solver) */
-    int32_t cost_split;    /* chosen threads per word of the cost kernel */
+    int32_t cost_split;    /* chosen cost kernel (see swmd_options.cost_split) */
     float default_ms;      /* whole-query time with the settings before tuning */
     float best_ms;         /* whole-query time with the chosen settings */
     int32_t candidates;    /* configurations timed */
@@ -410,8 +413,8 @@ typedef struct swmd_tune_result {
 
 /* Times the resident-path kernels of this corpus for queries of v_r words over
  * the candidate solvers and lane mappings (column-split register solver; register
- * solver rows per lane; shared-memory solver; threads per word of the cost
- * kernel), each `reps` times (>= 1) with CUDA events on a query of v_r distinct
+ * solver rows per lane; shared-memory solver; the cost kernel: product form or
+ * row kernel with 1, 2 or 4 threads per word), each `reps` times (>= 1) with CUDA events on a query of v_r distinct
  * words, and keeps the fastest: later queries of v_r words with the same K
  * precision use it unless swmd_options fixes the field.  On a corpus with SWMD_PATH_AUTO it also times the
  * per-iteration fused path and records, for this v_r, whichever path was faster.

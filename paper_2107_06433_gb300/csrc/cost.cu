@@ -5,6 +5,11 @@
 // (the third dense input of SDDMM_SpMM type 2).  Only vocabulary words that
 // occur in the corpus get a row: no nonzero of c ever reads the others.
 //
+// Two forms.  Layouts of 16 and 32 columns (and the 32-column chunks of wider ones)
+// take k_cost_tile, which evaluates M^2 = |q|^2 + |e|^2 - 2 q.e as a register-tiled
+// product and falls back to the difference form near M = 0 (below).  The others,
+// and any layout when a cost split is asked for, take the row kernels:
+//
 // Mapping: T adjacent threads own one word w and split the VRP query words,
 // KPT = VRP / T each.  The query rows are staged transposed in shared memory,
 // DC dimensions at a time, and read as float4 broadcasts; each thread streams
@@ -383,6 +388,318 @@ __global__ void __launch_bounds__(kCostThreads) k_cost_finish(const __grid_const
     else k_cost_finish_body<VRP, KT_t>(a0);
 }
 
+// ---------------------------------------------------------------- the product form
+//
+// The same distances from M^2 = |q|^2 + |e|^2 - 2 q.e: the block is then a plain
+// product E_used Q^T (one FMA per word, query word and dimension, half the direct
+// form's two), register-tiled like a GEMM.  The product form cancels where M is
+// small against |q| and |e| (a query word that is itself a corpus word has M = 0
+// exactly, and the form leaves an O(1e-7) residue there, so M ~ 3e-4): every entry
+// with M^2 below a quarter of |q|^2 + |e|^2 is evaluated again in the direct
+// difference form.  The product form's rounding error is a few eps (|q|^2 + |e|^2)
+// (2 |q.e| <= |q|^2 + |e|^2), so above that threshold it is a few eps relative to
+// M^2, the same order as the direct form's.
+//
+// Tiles: a block of 4 warps owns 128 words (32 per warp); lane (wg = lane % 8,
+// qg = lane / 8) of a warp holds the dots of its warp's words wg + 8 j (j < 4) with
+// query words [qg KQ, qg KQ + KQ), KQ = VRP / 4, as packed f32x2 FMAs over query
+// pairs.  The embedding rows go through shared memory 16 dimensions at a time
+// (cp.async, three stages in flight, zero-filled past the vocabulary and past d);
+// the transposed query block Q^T stays in shared memory.  Three blocks per SM
+// (about 70 KB of shared memory and 136 registers a thread each at 32 columns) measured
+// faster than two blocks of 4 warps with 8 words a thread or of 8 warps with 4.
+constexpr int kTileDK = 16;              // embedding dimensions per stage
+constexpr int kTileLd = kTileDK + 4;     // floats per word row of a stage: 8 consecutive rows of
+                                         // float4 reads fall in distinct banks
+constexpr int kTileStages = 3;           // stages in flight
+constexpr int kTileCT = 128;             // threads per block
+constexpr int kTileNW = 4;               // words per thread
+constexpr int kTileMinB = 3;             // blocks per SM the registers are fitted to
+constexpr int kTileWords = kTileCT / 32 * 8 * kTileNW;   // words per block tile: 8 NW per warp
+
+__host__ __device__ constexpr bool cost_tile_vrp(int vrp) { return vrp == 16 || vrp == 32; }
+
+// Dynamic shared memory of the product-form kernel: the stages, Q^T over d4
+// rounded up to whole stages, the tile's |e|^2, partial and whole |q|^2.
+inline size_t cost_tile_smem(int d4, int vrp) {
+    const size_t dq = (size_t)(d4 + kTileDK - 1) / kTileDK * kTileDK;
+    return ((size_t)kTileStages * kTileWords * kTileLd + dq * vrp + kTileWords + 5 * (size_t)vrp) * sizeof(float);
+}
+
+// 16 bytes global -> shared on the asynchronous path (L2 only); valid = false
+// copies nothing and writes zeros.
+__device__ __forceinline__ void cp_async16_zfill(float *smem, const float *gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// sum_d (q_d - e_d)^2 over the d4 dimensions: query column k of the staged Q^T
+// (row stride vrp) against an embedding row in global memory.
+__device__ __noinline__ float direct_sq(const float *sQ, int vrp, int k, const float *erow, int d4) {
+    float s = 0.f;
+    for (int d = 0; d < d4; d += 4) {
+        const float4 e = __ldg(reinterpret_cast<const float4 *>(erow + d));
+        float t = sQ[d * vrp + k] - e.x;
+        s = fmaf(t, t, s);
+        t = sQ[(d + 1) * vrp + k] - e.y;
+        s = fmaf(t, t, s);
+        t = sQ[(d + 2) * vrp + k] - e.z;
+        s = fmaf(t, t, s);
+        t = sQ[(d + 3) * vrp + k] - e.w;
+        s = fmaf(t, t, s);
+    }
+    return s;
+}
+
+// chunk >= 0: the query columns [VRP chunk, VRP chunk + VRP) of a wider layout of
+// vrp_full columns; the distances go to the rows' scratch (cost_scratch), for
+// k_cost_finish.
+template <int VRP, class KT_t>
+__device__ __noinline__ void k_cost_tile_body(const CostArgs &a, int chunk, int vrp_full) {
+    static_assert(cost_tile_vrp(VRP), "VRP");
+    constexpr int KQ = VRP / 4;                 // query words per thread
+    constexpr int NW = kTileNW;                 // words per thread
+    constexpr int CT = kTileCT;
+    constexpr int TW = kTileWords;
+    constexpr int CPT = TW * (kTileDK / 4) / CT;   // 16-byte copies per thread and stage
+    constexpr int EPT = TW / CT;                   // |e|^2 sums per thread
+    static_assert(CT % 32 == 0 && CT >= 4 * VRP && CPT >= 1 && EPT >= 1, "tile shape");
+    extern __shared__ __align__(16) float smem[];
+    const int d4 = a.d4;
+    const int dq = (d4 + kTileDK - 1) / kTileDK * kTileDK;
+    float *const sE = smem;                                    // [stages][TW][kTileLd]
+    float *const sQ = sE + kTileStages * TW * kTileLd;         // [dq][VRP]
+    float *const sEn = sQ + dq * VRP;                          // [TW]
+    float *const sQp = sEn + TW;                               // [4][VRP]
+    float *const sQn = sQp + 4 * VRP;                          // [VRP]
+
+    // the arguments in registers (the asynchronous-copy waits are compiler barriers)
+    const float *const E = a.E;
+    const int *const used = a.used;
+    const long Vu = a.Vu;
+    const int shift = a.shift;
+    KT_t *const KT = reinterpret_cast<KT_t *>(a.KT);
+    KT_t *const KMT = reinterpret_cast<KT_t *>(a.KMT);
+    const int col0 = chunk >= 0 ? VRP * chunk : 0;
+    const int vr = chunk >= 0 ? max(0, min(VRP, a.qp->vr - col0)) : a.qp->vr;
+    const float lam = a.qp->lambda;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wg = lane & 7, qg = lane >> 3;
+
+    const int ntiles = (int)((Vu + TW - 1) / TW);
+    const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int ns = dq / kTileDK;
+    const int total = my_tiles * ns;   // stages this block runs, tile-major
+
+    // Stage g (tile g / ns of this block, dimensions [16 (g % ns), +16)) into buffer
+    // g % 3: thread tid copies dimensions 4 (tid % 4) .. + 4 of words tid / 4 + (CT / 4) r.
+    auto issue = [&](int g) {
+        if (g < total) {
+            const long tile = (long)blockIdx.x + (long)(g / ns) * gridDim.x;
+            const int dim = (g % ns) * kTileDK + 4 * (tid & 3);
+            float *dst = sE + (g % kTileStages) * (TW * kTileLd) + (tid >> 2) * kTileLd + 4 * (tid & 3);
+            int row[CPT];   // all word ids first, so their loads are in flight together
+#pragma unroll
+            for (int r = 0; r < CPT; ++r) {
+                const long wi = tile * TW + (tid >> 2) + (CT / 4) * r;
+                row[r] = wi < Vu ? __ldg(used + wi) : -1;
+            }
+#pragma unroll
+            for (int r = 0; r < CPT; ++r) {
+                const bool ok = row[r] >= 0 && dim < d4;
+                cp_async16_zfill(dst + (CT / 4) * r * kTileLd, ok ? E + (size_t)row[r] * d4 + dim : E, ok);
+            }
+        }
+        cp_async_commit();
+    };
+
+    // Q^T, zero past v_r and past d4 (query word fastest across threads)
+    for (int i = tid; i < (dq / 4) * VRP; i += CT) {
+        const int c = i / VRP, k = i - c * VRP;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < vr && 4 * c < d4) {
+            const int qid = __ldg(a.q_ids + col0 + k);
+            if (qid >= 0 && qid < a.V) v = __ldg(reinterpret_cast<const float4 *>(E + (size_t)qid * d4) + c);
+        }
+        sQ[(4 * c) * VRP + k] = v.x;
+        sQ[(4 * c + 1) * VRP + k] = v.y;
+        sQ[(4 * c + 2) * VRP + k] = v.z;
+        sQ[(4 * c + 3) * VRP + k] = v.w;
+    }
+    for (int g = 0; g < kTileStages - 1; ++g) issue(g);
+    __syncthreads();
+    // |q_k|^2: four partial sums over quarters of the dimensions, added in order
+    {
+        const int k = tid % VRP, p = tid / VRP, len = dq / 4;
+        if (p < 4) {
+            float sum = 0.f;
+            for (int dd = p * len; dd < (p + 1) * len; ++dd) sum = fmaf(sQ[dd * VRP + k], sQ[dd * VRP + k], sum);
+            sQp[p * VRP + k] = sum;
+        }
+    }
+    __syncthreads();
+    if (tid < VRP) sQn[tid] = ((sQp[tid] + sQp[VRP + tid]) + sQp[2 * VRP + tid]) + sQp[3 * VRP + tid];
+    // (read after the main loop's first barrier)
+
+    float2 acc[NW][KQ / 2];   // the dots of query pairs
+#pragma unroll
+    for (int j = 0; j < NW; ++j)
+#pragma unroll
+        for (int i = 0; i < KQ / 2; ++i) acc[j][i] = make_float2(0.f, 0.f);
+    float en[EPT];   // |e|^2 of the tile's words tid + CT r
+#pragma unroll
+    for (int r = 0; r < EPT; ++r) en[r] = 0.f;
+
+    for (int g = 0; g < total; ++g) {
+        cp_async_wait<kTileStages - 2>();   // this thread's copies of stage g have landed
+        __syncthreads();                    // everyone's; the buffer of stage g - 1 is free
+        issue(g + kTileStages - 1);
+        const int s = g % ns;
+        const float *buf = sE + (g % kTileStages) * (TW * kTileLd);
+        const float *qs = sQ + s * kTileDK * VRP + qg * KQ;
+        const float *wrow = buf + (warp * 8 * NW + wg) * kTileLd;
+#pragma unroll
+        for (int quad = 0; quad < kTileDK / 4; ++quad) {
+            float4 ev[NW];
+#pragma unroll
+            for (int j = 0; j < NW; ++j) ev[j] = *reinterpret_cast<const float4 *>(wrow + 8 * j * kTileLd + 4 * quad);
+#pragma unroll
+            for (int dd = 0; dd < 4; ++dd) {
+                float qv[KQ];
+#pragma unroll
+                for (int c = 0; c < KQ / 4; ++c) {
+                    const float4 q4 = *reinterpret_cast<const float4 *>(qs + (4 * quad + dd) * VRP + 4 * c);
+                    qv[4 * c] = q4.x;
+                    qv[4 * c + 1] = q4.y;
+                    qv[4 * c + 2] = q4.z;
+                    qv[4 * c + 3] = q4.w;
+                }
+#pragma unroll
+                for (int j = 0; j < NW; ++j) {
+                    const float e = dd == 0 ? ev[j].x : dd == 1 ? ev[j].y : dd == 2 ? ev[j].z : ev[j].w;
+                    const float2 e2 = make_float2(e, e);
+#pragma unroll
+                    for (int i = 0; i < KQ / 2; ++i)
+                        acc[j][i] = __ffma2_rn(make_float2(qv[2 * i], qv[2 * i + 1]), e2, acc[j][i]);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < EPT; ++r)
+#pragma unroll
+            for (int c = 0; c < kTileDK / 4; ++c) {
+                const float4 x = *reinterpret_cast<const float4 *>(buf + (tid + CT * r) * kTileLd + 4 * c);
+                en[r] = fmaf(x.x, x.x, en[r]);
+                en[r] = fmaf(x.y, x.y, en[r]);
+                en[r] = fmaf(x.z, x.z, en[r]);
+                en[r] = fmaf(x.w, x.w, en[r]);
+            }
+        if (s != ns - 1) continue;
+
+        // the tile is complete: distances, then K and K.*M (or the chunk's scratch)
+#pragma unroll
+        for (int r = 0; r < EPT; ++r) {
+            sEn[tid + CT * r] = en[r];
+            en[r] = 0.f;
+        }
+        __syncthreads();
+        const long tile = (long)blockIdx.x + (long)(g / ns) * gridDim.x;
+#pragma unroll
+        for (int j = 0; j < NW; ++j) {
+            const int wl = warp * 8 * NW + wg + 8 * j;
+            const long wi = tile * TW + wl;
+            const bool active = wi < Vu;
+            const float enw = sEn[wl];
+            float m[KQ];
+#pragma unroll
+            for (int i = 0; i < KQ; ++i) {
+                const int k = qg * KQ + i;
+                const float dot = (i & 1) ? acc[j][i / 2].y : acc[j][i / 2].x;
+                const float nn = sQn[k] + enw;
+                float d2 = fmaf(-2.f, dot, nn);
+                if (active && !(d2 >= 0.25f * nn)) d2 = direct_sq(sQ, VRP, k, E + (size_t)__ldg(used + wi) * d4, d4);
+                m[i] = sqrtf(fmaxf(d2, 0.f));
+            }
+#pragma unroll
+            for (int i = 0; i < KQ / 2; ++i) acc[j][i] = make_float2(0.f, 0.f);
+            if (chunk >= 0) {
+                if (active)
+#pragma unroll
+                    for (int c = 0; c < KQ / 4; ++c) {
+                        float *dst = cost_scratch(a, wi, col0 + qg * KQ + 4 * c, vrp_full, (int)sizeof(KT_t));
+                        *reinterpret_cast<float4 *>(dst) = make_float4(m[4 * c], m[4 * c + 1], m[4 * c + 2], m[4 * c + 3]);
+                    }
+                continue;
+            }
+            // column shift (minimum over the query words) and FP16 scale (maximum): the
+            // word's columns are spread over the lanes wg, wg + 8, wg + 16, wg + 24
+            float mn = INFINITY, mx = 0.f;
+#pragma unroll
+            for (int i = 0; i < KQ; ++i)
+                if (qg * KQ + i < vr) {
+                    mn = fminf(mn, m[i]);
+                    mx = fmaxf(mx, m[i]);
+                }
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 8));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 16));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+            if (!active) continue;
+            const float sh = (shift && mn < INFINITY) ? mn : 0.f;
+            const float bw = shift ? storage_scale<KT_t>(mx) : 1.f;
+#pragma unroll
+            for (int c = 0; c < KQ / 4; ++c) {
+                float kv[4], kmv[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int k = qg * KQ + 4 * c + e;
+                    const float kk = (k < vr) ? expf(-lam * (m[4 * c + e] - sh)) : 0.f;
+                    kv[e] = kk * bw;
+                    kmv[e] = (kk * m[4 * c + e]) * bw;
+                }
+                const long idx4 = (wi * VRP + qg * KQ) / 4 + c;
+                KIO<KT_t>::store4(KT, idx4, make_float4(kv[0], kv[1], kv[2], kv[3]));
+                KIO<KT_t>::store4(KMT, idx4, make_float4(kmv[0], kmv[1], kmv[2], kmv[3]));
+            }
+        }
+    }
+    cp_async_wait<0>();   // (the groups still open are empty)
+}
+
+template <int VRP, class KT_t>
+__global__ void __launch_bounds__(kTileCT, kTileMinB) k_cost_tile(const __grid_constant__ CostArgs a0,
+                                                                  const CostArgs *batch, int chunk, int vrp_full) {
+    // one query per grid row when batched (batch[blockIdx.y]), else the argument
+    if (batch) k_cost_tile_body<VRP, KT_t>(batch[blockIdx.y], chunk, vrp_full);
+    else k_cost_tile_body<VRP, KT_t>(a0, chunk, vrp_full);
+}
+
+// Blocks: one per tile of words, at most the resident blocks of the device shared
+// by the nq queries of a batch.
+template <int VRP, class KT_t>
+cudaError_t run_tile(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *batch, int chunk = -1,
+                     int vrp_full = 0) {
+    auto kern = k_cost_tile<VRP, KT_t>;
+    const size_t smem = cost_tile_smem(a.d4, VRP);
+    static LaunchCache cache;
+    int per_sm = 1;
+    cudaError_t e = cache.blocks_per_sm(kern, kTileCT, smem, -1, &per_sm);
+    if (e != cudaSuccess) return e;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long blocks = (a.Vu + kTileWords - 1) / kTileWords;
+    long cap = ((long)sms * per_sm + nq - 1) / nq;
+    if (cap < 1) cap = 1;
+    if (blocks > cap) blocks = cap;
+    if (blocks > 0) kern<<<dim3((unsigned)blocks, (unsigned)nq), kTileCT, smem, s>>>(a, batch, chunk, vrp_full);
+    return cudaGetLastError();
+}
+
 template <int VRP, int TS, class KT_t>
 cudaError_t run_rows(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *batch, int chunk = -1,
                      int vrp_full = 0) {
@@ -409,7 +726,8 @@ cudaError_t run_rows(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *
 template <int VRP, class KT_t>
 cudaError_t run_chunked(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *batch, int ts) {
     for (int ch = 0; ch < VRP / 32; ++ch) {
-        cudaError_t e = ts == 2 ? run_rows<32, 2, KT_t>(a, s, nq, batch, ch, VRP)
+        cudaError_t e = ts == 0 ? run_tile<32, KT_t>(a, s, nq, batch, ch, VRP)
+                      : ts == 2 ? run_rows<32, 2, KT_t>(a, s, nq, batch, ch, VRP)
                       : ts == 4 ? run_rows<32, 4, KT_t>(a, s, nq, batch, ch, VRP)
                                 : run_rows<32, 1, KT_t>(a, s, nq, batch, ch, VRP);
         if (e != cudaSuccess) return e;
@@ -439,8 +757,18 @@ cudaError_t run(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *batch
     return cudaGetLastError();
 }
 
+// The product-form kernel where it applies (layouts of 16 and 32 columns, and the
+// 32-column chunks of 64 and 128, with Q^T within about 100 KB of shared memory in
+// all) unless a cost split asks for the row kernel.
+constexpr size_t kCostTileSmemMax = 110 * 1024;
+
 template <class KT_t>
 cudaError_t dispatch(const CostArgs &a, int vrp, cudaStream_t s, int nq, const CostArgs *batch) {
+    const bool rows_asked = a.split == 1 || a.split == 2 || a.split == 4;
+    if (!rows_asked && cost_tile_vrp(vrp) && cost_tile_smem(a.d4, vrp) <= kCostTileSmemMax)
+        return vrp == 16 ? run_tile<16, KT_t>(a, s, nq, batch) : run_tile<32, KT_t>(a, s, nq, batch);
+    if (!rows_asked && (vrp == 64 || vrp == 128) && cost_tile_smem(a.d4, 32) <= kCostTileSmemMax)
+        return vrp == 64 ? run_chunked<64, KT_t>(a, s, nq, batch, 0) : run_chunked<128, KT_t>(a, s, nq, batch, 0);
     if (vrp <= 32 && (size_t)a.d4 * vrp * sizeof(float) <= 100 * 1024) {
         // threads per word: 2 by default; 1 on large vocabularies, where one thread
         // per word already fills the GPU (measured 1.3-1.5x faster from 90,000 used
