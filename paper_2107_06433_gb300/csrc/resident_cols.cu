@@ -82,13 +82,14 @@ __device__ __forceinline__ void ldg_words(const void *p, uint32_t (&w)[P]) {
     }
 }
 
-// Swaps register blocks kb and kb ^ bit (blocks of P / G values) for every bit set
-// in g: natural column order <-> the XOR block order of group g.
-template <int P, int G>
+// Swaps register blocks kb and kb ^ bit (blocks of P / G values) for every bit below
+// 2^H set in g (H = log2 G: every bit): natural column order <-> the XOR block order
+// of group g, or the rest of it after a load that placed the higher bits.
+template <int P, int G, int H = 31 - __builtin_clz(G)>
 __device__ __forceinline__ void swap_blocks(float (&x)[P], int g) {
     constexpr int B = P / G;
 #pragma unroll
-    for (int bit = 1; bit < G; bit <<= 1) {
+    for (int bit = 1; bit < G && bit < (1 << H); bit <<= 1) {
         const bool sw = (g & bit) != 0;
 #pragma unroll
         for (int kb = 0; kb < G; ++kb) {
@@ -103,11 +104,18 @@ __device__ __forceinline__ void swap_blocks(float (&x)[P], int g) {
     }
 }
 
-// How a lane puts its slice of a K^T row into the XOR column-block order: one vector
-// load per column block, or one whole-slice load and conditional swaps (fewer L1
-// requests, more registers).  Timed per layout on the 1,000,000-document workload: the
-// swaps win at 16 and 64 columns, the block loads at 32 and 128.
-__host__ __device__ constexpr bool cols_swap_blocks(int vrp) { return vrp == 16 || vrp == 64; }
+// How a lane puts its slice of a K^T row into the XOR column-block order of its
+// group g (blocks of P / G values): G >> H vector loads of 2^H blocks each, placed
+// by the high bits of g, then conditional swaps for the low H bits.  H = 0: one load
+// per block, no swap; H = log2 G: one whole-slice load, every bit swapped (fewer L1
+// requests, more registers).  Timed per layout and group count on the
+// 1,000,000-document workload: whole slices at 16 and 64 columns; at 32 columns two
+// half-slice loads and one swap for four groups (solver 1.489 ms, against 1.513 ms
+// with four block loads; swapping for two groups too spilled more and took 1.536 ms),
+// block loads for two; block loads at 128 columns.
+__host__ __device__ constexpr int cols_gather_h(int vrp, int g) {
+    return (vrp == 16 || vrp == 64) ? (g >= 8 ? 3 : g >= 4 ? 2 : g >= 2 ? 1 : 0) : vrp == 32 ? (g >= 4 ? 1 : 0) : 0;
+}
 
 // Columns [P ql, P ql + P) of the rows of words wv[i] (word-major layout of VRP
 // columns), widened to float; PERM: in group g's column order (register block kb of
@@ -117,9 +125,12 @@ __host__ __device__ constexpr bool cols_swap_blocks(int vrp) { return vrp == 16 
 template <int VRP, int P, int G, int RL, bool PERM = true>
 __device__ __forceinline__ void gather_rows(float (&rv)[RL][P], const void *base, int kprec, const int (&wv)[RL],
                                             int ql, int g) {
-    constexpr bool SWAP_PERM = cols_swap_blocks(VRP);
-    constexpr int B = (PERM && !SWAP_PERM) ? P / G : P;
-    constexpr int GL = (PERM && !SWAP_PERM) ? G : 1;
+    constexpr int LG2G = 31 - __builtin_clz(G);
+    constexpr int H = PERM ? cols_gather_h(VRP, G) : LG2G;   // natural order: whole-slice loads
+    constexpr int L = (P / G) << H;                          // values per load
+    constexpr int NL = P / L;                                // loads per row
+    static_assert(H <= LG2G && NL * L == P, "load shape");
+    const int ghi = PERM ? (g >> H) : 0;                     // the load-placed bits of g
     if (kprec == 0) {
         const float *b = reinterpret_cast<const float *>(base) + ql * P;
 #pragma unroll
@@ -127,16 +138,16 @@ __device__ __forceinline__ void gather_rows(float (&rv)[RL][P], const void *base
             uint32_t w[P] = {};
             if (wv[i] >= 0) {
 #pragma unroll
-                for (int kb = 0; kb < GL; ++kb) {
-                    uint32_t wb[B];
-                    ldg_words<B>(b + (long)wv[i] * VRP + (GL > 1 ? (kb ^ g) * B : 0), wb);
+                for (int kl = 0; kl < NL; ++kl) {
+                    uint32_t wb[L];
+                    ldg_words<L>(b + (long)wv[i] * VRP + (NL > 1 ? (kl ^ ghi) * L : 0), wb);
 #pragma unroll
-                    for (int e = 0; e < B; ++e) w[kb * B + e] = wb[e];
+                    for (int e = 0; e < L; ++e) w[kl * L + e] = wb[e];
                 }
             }
 #pragma unroll
             for (int k = 0; k < P; ++k) rv[i][k] = __uint_as_float(w[k]);
-            if constexpr (PERM && SWAP_PERM) swap_blocks<P, G>(rv[i], g);
+            if constexpr (PERM && H > 0) swap_blocks<P, G, H>(rv[i], g);
         }
     } else {
         const unsigned short *b = reinterpret_cast<const unsigned short *>(base) + ql * P;
@@ -145,11 +156,11 @@ __device__ __forceinline__ void gather_rows(float (&rv)[RL][P], const void *base
         for (int i = 0; i < RL; ++i)
             if (wv[i] >= 0) {
 #pragma unroll
-                for (int kb = 0; kb < GL; ++kb) {
-                    uint32_t wb[B / 2];
-                    ldg_words<B / 2>(b + (long)wv[i] * VRP + (GL > 1 ? (kb ^ g) * B : 0), wb);
+                for (int kl = 0; kl < NL; ++kl) {
+                    uint32_t wb[L / 2];
+                    ldg_words<L / 2>(b + (long)wv[i] * VRP + (NL > 1 ? (kl ^ ghi) * L : 0), wb);
 #pragma unroll
-                    for (int e = 0; e < B / 2; ++e) raw[i][kb * (B / 2) + e] = wb[e];
+                    for (int e = 0; e < L / 2; ++e) raw[i][kl * (L / 2) + e] = wb[e];
                 }
             }
 #pragma unroll
@@ -160,9 +171,9 @@ __device__ __forceinline__ void gather_rows(float (&rv)[RL][P], const void *base
                 rv[i][2 * k] = f.x;
                 rv[i][2 * k + 1] = f.y;
             }
-        if constexpr (PERM && SWAP_PERM)
+        if constexpr (PERM && H > 0)
 #pragma unroll
-            for (int i = 0; i < RL; ++i) swap_blocks<P, G>(rv[i], g);
+            for (int i = 0; i < RL; ++i) swap_blocks<P, G, H>(rv[i], g);
     }
 }
 
