@@ -416,14 +416,21 @@ constexpr int kTileCT = 128;             // threads per block
 constexpr int kTileNW = 4;               // words per thread
 constexpr int kTileMinB = 3;             // blocks per SM the registers are fitted to
 constexpr int kTileWords = kTileCT / 32 * 8 * kTileNW;   // words per block tile: 8 NW per warp
+constexpr size_t kCostTileSmemMax = 110 * 1024;          // largest dynamic shared memory taken
 
-__host__ __device__ constexpr bool cost_tile_vrp(int vrp) { return vrp == 16 || vrp == 32; }
+__host__ __device__ constexpr bool cost_tile_vrp(int vrp) { return vrp == 16 || vrp == 32 || vrp == 64; }
+// Blocks per SM the registers are fitted to: 64-column layouts hold twice the dots
+// and Q^T (about 107 KB of shared memory in all at d = 300), so two.
+__host__ __device__ constexpr int cost_tile_min_blocks(int vrp) { return vrp >= 64 ? 2 : kTileMinB; }
+// Partial sums of |q|^2 per query word (each over a share of the dimensions).
+__host__ __device__ constexpr int cost_tile_qparts(int vrp) { return kTileCT / vrp < 4 ? kTileCT / vrp : 4; }
 
 // Dynamic shared memory of the product-form kernel: the stages, Q^T over d4
 // rounded up to whole stages, the tile's |e|^2, partial and whole |q|^2.
 inline size_t cost_tile_smem(int d4, int vrp) {
     const size_t dq = (size_t)(d4 + kTileDK - 1) / kTileDK * kTileDK;
-    return ((size_t)kTileStages * kTileWords * kTileLd + dq * vrp + kTileWords + 5 * (size_t)vrp) * sizeof(float);
+    return ((size_t)kTileStages * kTileWords * kTileLd + dq * vrp + kTileWords +
+            (size_t)(cost_tile_qparts(vrp) + 1) * vrp) * sizeof(float);
 }
 
 // 16 bytes global -> shared on the asynchronous path (L2 only); valid = false
@@ -467,15 +474,16 @@ __device__ __noinline__ void k_cost_tile_body(const CostArgs &a, int chunk, int 
     constexpr int TW = kTileWords;
     constexpr int CPT = TW * (kTileDK / 4) / CT;   // 16-byte copies per thread and stage
     constexpr int EPT = TW / CT;                   // |e|^2 sums per thread
-    static_assert(CT % 32 == 0 && CT >= 4 * VRP && CPT >= 1 && EPT >= 1, "tile shape");
+    constexpr int QP = cost_tile_qparts(VRP);      // partial sums of |q_k|^2
+    static_assert(CT % 32 == 0 && CT >= QP * VRP && QP >= 1 && CPT >= 1 && EPT >= 1, "tile shape");
     extern __shared__ __align__(16) float smem[];
     const int d4 = a.d4;
     const int dq = (d4 + kTileDK - 1) / kTileDK * kTileDK;
     float *const sE = smem;                                    // [stages][TW][kTileLd]
     float *const sQ = sE + kTileStages * TW * kTileLd;         // [dq][VRP]
     float *const sEn = sQ + dq * VRP;                          // [TW]
-    float *const sQp = sEn + TW;                               // [4][VRP]
-    float *const sQn = sQp + 4 * VRP;                          // [VRP]
+    float *const sQp = sEn + TW;                               // [QP][VRP]
+    float *const sQn = sQp + QP * VRP;                         // [VRP]
 
     // the arguments in registers (the asynchronous-copy waits are compiler barriers)
     const float *const E = a.E;
@@ -532,17 +540,22 @@ __device__ __noinline__ void k_cost_tile_body(const CostArgs &a, int chunk, int 
     }
     for (int g = 0; g < kTileStages - 1; ++g) issue(g);
     __syncthreads();
-    // |q_k|^2: four partial sums over quarters of the dimensions, added in order
+    // |q_k|^2: QP partial sums over equal shares of the dimensions, added in order
     {
-        const int k = tid % VRP, p = tid / VRP, len = dq / 4;
-        if (p < 4) {
+        const int k = tid % VRP, p = tid / VRP, len = dq / QP;
+        if (p < QP) {
             float sum = 0.f;
             for (int dd = p * len; dd < (p + 1) * len; ++dd) sum = fmaf(sQ[dd * VRP + k], sQ[dd * VRP + k], sum);
             sQp[p * VRP + k] = sum;
         }
     }
     __syncthreads();
-    if (tid < VRP) sQn[tid] = ((sQp[tid] + sQp[VRP + tid]) + sQp[2 * VRP + tid]) + sQp[3 * VRP + tid];
+    if (tid < VRP) {
+        float sum = sQp[tid];
+#pragma unroll
+        for (int p = 1; p < QP; ++p) sum += sQp[p * VRP + tid];
+        sQn[tid] = sum;
+    }
     // (read after the main loop's first barrier)
 
     float2 acc[NW][KQ / 2];   // the dots of query pairs
@@ -671,7 +684,7 @@ __device__ __noinline__ void k_cost_tile_body(const CostArgs &a, int chunk, int 
 }
 
 template <int VRP, class KT_t>
-__global__ void __launch_bounds__(kTileCT, kTileMinB) k_cost_tile(const __grid_constant__ CostArgs a0,
+__global__ void __launch_bounds__(kTileCT, cost_tile_min_blocks(VRP)) k_cost_tile(const __grid_constant__ CostArgs a0,
                                                                   const CostArgs *batch, int chunk, int vrp_full) {
     // one query per grid row when batched (batch[blockIdx.y]), else the argument
     if (batch) k_cost_tile_body<VRP, KT_t>(batch[blockIdx.y], chunk, vrp_full);
@@ -724,14 +737,7 @@ cudaError_t run_rows(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *
 // A layout wider than 32 columns: the row kernel on each 32-column chunk (distances
 // to the scratch), then the finishing pass over whole rows.
 template <int VRP, class KT_t>
-cudaError_t run_chunked(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *batch, int ts) {
-    for (int ch = 0; ch < VRP / 32; ++ch) {
-        cudaError_t e = ts == 0 ? run_tile<32, KT_t>(a, s, nq, batch, ch, VRP)
-                      : ts == 2 ? run_rows<32, 2, KT_t>(a, s, nq, batch, ch, VRP)
-                      : ts == 4 ? run_rows<32, 4, KT_t>(a, s, nq, batch, ch, VRP)
-                                : run_rows<32, 1, KT_t>(a, s, nq, batch, ch, VRP);
-        if (e != cudaSuccess) return e;
-    }
+cudaError_t run_finish(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *batch) {
     auto kern = k_cost_finish<VRP, KT_t>;
     static LaunchCache cache;
     int per_sm = 1;
@@ -748,6 +754,25 @@ cudaError_t run_chunked(const CostArgs &a, cudaStream_t s, int nq, const CostArg
     return cudaGetLastError();
 }
 
+template <int VRP, class KT_t>
+cudaError_t run_chunked(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *batch, int ts) {
+    if (ts == 0 && VRP % 64 == 0 && cost_tile_smem(a.d4, 64) <= kCostTileSmemMax) {
+        for (int ch = 0; ch < VRP / 64; ++ch) {   // 64-column chunks of the product form
+            cudaError_t e = run_tile<64, KT_t>(a, s, nq, batch, ch, VRP);
+            if (e != cudaSuccess) return e;
+        }
+        return run_finish<VRP, KT_t>(a, s, nq, batch);
+    }
+    for (int ch = 0; ch < VRP / 32; ++ch) {
+        cudaError_t e = ts == 0 ? run_tile<32, KT_t>(a, s, nq, batch, ch, VRP)
+                      : ts == 2 ? run_rows<32, 2, KT_t>(a, s, nq, batch, ch, VRP)
+                      : ts == 4 ? run_rows<32, 4, KT_t>(a, s, nq, batch, ch, VRP)
+                                : run_rows<32, 1, KT_t>(a, s, nq, batch, ch, VRP);
+        if (e != cudaSuccess) return e;
+    }
+    return run_finish<VRP, KT_t>(a, s, nq, batch);
+}
+
 template <int KPT, int T, class KT_t>
 cudaError_t run(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *batch) {
     const int words_per_block = kCostThreads / T;
@@ -757,16 +782,17 @@ cudaError_t run(const CostArgs &a, cudaStream_t s, int nq, const CostArgs *batch
     return cudaGetLastError();
 }
 
-// The product-form kernel where it applies (layouts of 16 and 32 columns, and the
-// 32-column chunks of 64 and 128, with Q^T within about 100 KB of shared memory in
-// all) unless a cost split asks for the row kernel.
-constexpr size_t kCostTileSmemMax = 110 * 1024;
+// The product-form kernel where it applies (layouts of 16, 32 and 64 columns, and
+// the 64- or 32-column chunks of 128, within about 110 KB of shared memory) unless a
+// cost split asks for the row kernel.
 
 template <class KT_t>
 cudaError_t dispatch(const CostArgs &a, int vrp, cudaStream_t s, int nq, const CostArgs *batch) {
     const bool rows_asked = a.split == 1 || a.split == 2 || a.split == 4;
     if (!rows_asked && cost_tile_vrp(vrp) && cost_tile_smem(a.d4, vrp) <= kCostTileSmemMax)
-        return vrp == 16 ? run_tile<16, KT_t>(a, s, nq, batch) : run_tile<32, KT_t>(a, s, nq, batch);
+        return vrp == 16 ? run_tile<16, KT_t>(a, s, nq, batch)
+             : vrp == 32 ? run_tile<32, KT_t>(a, s, nq, batch)
+                         : run_tile<64, KT_t>(a, s, nq, batch);
     if (!rows_asked && (vrp == 64 || vrp == 128) && cost_tile_smem(a.d4, 32) <= kCostTileSmemMax)
         return vrp == 64 ? run_chunked<64, KT_t>(a, s, nq, batch, 0) : run_chunked<128, KT_t>(a, s, nq, batch, 0);
     if (vrp <= 32 && (size_t)a.d4 * vrp * sizeof(float) <= 100 * 1024) {
