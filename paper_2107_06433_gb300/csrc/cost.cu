@@ -5,7 +5,7 @@
 // (the third dense input of SDDMM_SpMM type 2).  Only vocabulary words that
 // occur in the corpus get a row: no nonzero of c ever reads the others.
 //
-// Two forms.  Layouts of 16 and 32 columns (and the 32-column chunks of wider ones)
+// Two forms.  Layouts of 16, 32 and 64 columns (and the 64-column chunks of 128)
 // take k_cost_tile, which evaluates M^2 = |q|^2 + |e|^2 - 2 q.e as a register-tiled
 // product and falls back to the difference form near M = 0 (below).  The others,
 // and any layout when a cost split is asked for, take the row kernels:
