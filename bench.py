@@ -100,8 +100,8 @@ def load_peaks():
 
 # the kernel sources each measured traffic figure depends on
 KERNEL_SOURCES = {
-    "resident": ["common.cuh", "resident_cols.cu", "resident_regs.cuh", "resident_tiled.cu", "walk.cuh",
-                 "walk3.cuh", "walk_resident.cu"],
+    "resident": ["common.cuh", "resident_cols.cu", "resident_cols.cuh", "resident_cols_long.cu",
+                 "resident_regs.cuh", "resident_tiled.cu", "walk.cuh", "walk3.cuh", "walk_resident.cu"],
     "cost": ["common.cuh", "cost.cu"],
     "fused": ["common.cuh", "walk.cuh", "walk3.cuh", "walk_fused.cu"],
     "plain": ["common.cuh", "walk.cuh", "walk3.cuh", "walk_plain.cu"],

@@ -112,9 +112,11 @@ typedef struct swmd_options {
                               2 = rows staged in shared memory, 3 = rows re-gathered from
                               L2 each iteration, 4 = K^T rows in registers split by columns
                               (eight per lane) over row groups of VRP / 8 lanes, one to
-                              four groups per document (documents of at most 32 words;
-                              v_r padded to a power of two from 16 to 128; on a corpus with
-                              longer documents 4 acts as 0) */
+                              eight groups per document; v_r padded to a power of two from
+                              16 to 128.  It holds documents of up to 96 words at 16 and 32
+                              columns, 32 at 64 and 128; at 16 and 32 columns longer
+                              documents run on solver 1 in a launch before it, at 64 and 128
+                              a corpus with longer documents makes 4 act as 0 */
     float tol;             /* 0 (default): exactly max_iter x-updates, as the paper's
                               experiments run.  > 0: Algorithm 1's "while x changes": the
                               fused per-iteration path stops after the x-update in which

@@ -23,7 +23,7 @@ LIB = os.path.join(BUILD, "libswmd.so")
 # with the release objects of the rest.
 DEBUG_BUILD = os.path.join(HERE, "_build_debug")
 DEBUG_LIB = os.path.join(DEBUG_BUILD, "libswmd.so")
-DEBUG_SOURCES = ("api.cu", "resident_cols.cu", "walk_fused.cu", "walk_final.cu", "walk_plain.cu")
+DEBUG_SOURCES = ("api.cu", "resident_cols.cu", "resident_cols_long.cu", "walk_fused.cu", "walk_final.cu", "walk_plain.cu")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",

@@ -333,6 +333,7 @@ struct ColArgs {
     const int *doc_orig;
     const int4 *tasks;     // (first document, documents, bucket, 0) warp tasks
     int n_tasks;
+    int long_docs;         // the tasks include buckets of 48, 64 or 96 rows
     int kprec;
     int Vu;                // rows of K^T (debug checks)
     long nnz;              // nonzeros (debug checks)
@@ -341,11 +342,13 @@ struct ColArgs {
     int nq;                          // in one launch over (group of q_per_group queries,
     int q_per_group;                 // document task) tiles
 };
-// Documents longer than this are not held by the column-split solver.
-constexpr int kColMaxLen = 32;
 // Rows a document of `len` words occupies in the column-split solver for layout
-// `vrp` (the bucket: 8, 16, 24 or 32, a multiple of vrp / 4); 0 if too long.
+// `vrp` (the bucket: 8, 16, 24, 32, 48, 64 or 96 rows, those the layout's row groups
+// can hold); 0 if too long for the layout.
 int cols_bucket(int len, int vrp);
+// The longest document the column-split solver holds in layout `vrp`: 96 words at
+// 16 and 32 columns, 32 at 64 and 128.
+int cols_max_len(int vrp);
 constexpr int kColMaxRowsPerLane = 12;   // rows a lane holds with eight columns
 // Columns of every row a lane holds (P = 8) and lanes of a row group (Q = vrp / P).
 __host__ __device__ constexpr int cols_p(int) { return 8; }
@@ -377,6 +380,8 @@ constexpr int kColLayouts = 4;
 // Runs all t iterations and the final step for every document of the tasks, for
 // a.q0, or (a.queries != NULL) for the a.nq = nq queries of a.queries in one launch.
 cudaError_t launch_resident_cols(const ColArgs &a, int vrp, int sms, cudaStream_t s, int nq);
+// The same for task lists with buckets of 48 to 96 rows (a.long_docs; 16 and 32 columns).
+cudaError_t launch_resident_cols_long(const ColArgs &a, int vrp, int sms, cudaStream_t s, int nq);
 
 
 }  // namespace swmd

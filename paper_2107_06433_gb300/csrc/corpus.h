@@ -124,10 +124,18 @@ struct swmd_corpus {
     int task_off[9] = {0};         // indexed by rows per lane (1..8)
     int task_count[9] = {0};
     // warp tasks of the column-split register solver, one list per layout (VRP 16,
-    // 32, 64, 128); built only when no document has more than kColMaxLen words
+    // 32, 64, 128) over the documents [col_first, Nl) it holds: documents are in
+    // decreasing length, so those too long for the layout's buckets (cols_max_len)
+    // are the first col_first; col_long: the list has buckets above 32 rows
     int4 *col_tasks_dev = nullptr;
     int col_off[swmd::kColLayouts] = {0};
     int col_count[swmd::kColLayouts] = {0};
+    int col_first[swmd::kColLayouts] = {0};
+    int col_long[swmd::kColLayouts] = {0};
+    // register-solver tasks (per rows-per-lane list) that cover exactly the documents
+    // [0, col_first) of the layouts of 16 and 32 columns: the register solver takes
+    // them when a column-split query runs on a corpus with longer documents
+    int task_prefix[9][2] = {{0}};
 
     swmd::Slot main;               // workspace of the single-query path
     void *batch_ws = nullptr;      // workspace of swmd_query_batch (grown on demand)
@@ -201,11 +209,16 @@ int run_resident_batch(swmd_corpus *c, const ResidentArgs &shape, Mapping m, int
 // Resident solvers (swmd_options.solver).
 constexpr int kSolverAuto = 0, kSolverRegs = 1, kSolverTiled = 2, kSolverL2 = 3, kSolverCols = 4;
 // The solver a resident query of vr words runs: swmd_options.solver, else the
-// autotuned one, else the column-split register solver when the corpus allows it
-// (no document above kColMaxLen words), else kSolverAuto (register solver for
-// VRP <= 32, else the shared-memory tiled one).  Never kSolverCols on a corpus
-// without column-split tasks.
+// autotuned one, else the column-split register solver when its layout holds every
+// document in buckets of up to 32 rows, else kSolverAuto (register solver for
+// VRP <= 32, else the shared-memory tiled one).  Never kSolverCols for a layout it
+// does not take (cols_takes).
 int resident_solver(swmd_corpus *c, int vr, int kprec);
+// Whether the column-split solver takes a query of vr words on this corpus: its
+// layout (cols_vrp) holds every document, or (16 and 32 columns) all but the
+// longest, which the register solver then runs in a launch before it.
+// whole: set to whether it holds every document.
+bool cols_takes(swmd_corpus *c, int vr, bool *whole = nullptr);
 // Queries per (query group, document task) tile of the multi-query column-split
 // walk for a layout: swmd_options.queries_per_tile, else the autotuned value, else
 // as many (1..8) as keep their K^T and KM^T within a quarter of L2.

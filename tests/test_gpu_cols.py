@@ -1,13 +1,16 @@
 """The column-split register solver against the FP64 oracle, through the C ABI.
 
 The solver keeps each document's K^T rows in registers for all t iterations, split
-by columns over a team of VRP / 8 lanes, 4 for 128 columns (resident_cols.cu).  It runs on corpora
-whose documents have at most 32 words, in buckets of 8, 16, 24 or 32 rows; query
-layouts of 16, 32, 64 and 128 columns.  These tests cover every bucket and team
-size, ragged buckets (every document length 1..32), the iteration counts 0, 1 and
-15, lambda 1 and 10, and the invariances the other solvers have (document ranges,
-batches and the server give the same bits).  Tolerance: 1e-5 relative on every
-distance (FP32), the stated bounds for BF16 / FP16 K.
+by columns over a team of VRP / 8 lanes, 4 for 128 columns (resident_cols.cu).  Query
+layouts of 16, 32, 64 and 128 columns; buckets of 8, 16, 24 and 32 rows in every
+layout, and of 48, 64 and 96 rows (four and eight row groups) at 16 and 32 columns.
+Documents longer than a layout's largest bucket run on the register solver in a
+launch before the column-split one (16 and 32 columns), else the query falls back
+to the other resident solvers.  These tests cover every bucket and team size, ragged
+buckets (every document length 1..32, and 1..300 for the long buckets), the
+iteration counts 0, 1 and 15, lambda 1 and 10, and the invariances the other solvers
+have (document ranges, batches and the server give the same bits).  Tolerance: 1e-5
+relative on every distance (FP32), the stated bounds for BF16 / FP16 K.
 """
 import numpy as np
 import pytest
@@ -117,15 +120,84 @@ def test_default_solver_on_short_documents(short_docs):
 
 def test_falls_back_on_long_documents():
     """Asking for the column-split solver on a corpus with documents above 32 words
-    runs the other resident solvers (still within the tolerance)."""
+    runs, at 64 columns (buckets up to 32 rows), the other resident solvers in their
+    own layout (still within the tolerance)."""
     rng = np.random.default_rng(12)
     V = 2000
     E = synth.embeddings(rng, V, 32)
     C = synth.corpus(rng, V, 80, rng.integers(1, 60, size=80), 5)
-    qi, qw = synth.query(rng, V, 20)
+    qi, qw = synth.query(rng, V, 40)
     corpus = swmd.corpus_from_synth(E, C, path="resident", solver=SOLVER_COLS)
-    assert swmd.swmd_get_mapping(corpus, 20, "resident")[0] == 20   # the tight layout
+    assert swmd.swmd_get_mapping(corpus, 40, "resident")[0] == 40   # the tight layout
     assert rel_err(swmd.swmd_query(corpus, qi, qw, 1.0, 15), oracle_wmd(E, C, qi, qw, 1.0, 15)) <= RTOL
+
+
+@pytest.fixture(scope="module")
+def long_docs():
+    """250 documents: lengths spread over 1..300 (every bucket from 8 to 96 rows,
+    and 60 documents above 96 words for the register solver), shuffled."""
+    rng = np.random.default_rng(33)
+    V, d = 6000, 48
+    E = synth.embeddings(rng, V, d)
+    lens = np.concatenate([rng.integers(1, 33, size=60), rng.integers(33, 49, size=40),
+                           rng.integers(49, 65, size=40), rng.integers(65, 97, size=50),
+                           rng.integers(97, 301, size=60)])
+    rng.shuffle(lens)
+    C = synth.corpus(rng, V, len(lens), lens, 10)
+    return E, C
+
+
+@pytest.mark.parametrize("vr", [1, 8, 16, 19, 32])
+@pytest.mark.parametrize("t", [0, 1, 15])
+def test_long_buckets_and_register_prefix(long_docs, vr, t):
+    """Documents of 33-96 words in the buckets of 48, 64 and 96 rows, longer ones on
+    the register solver in the same query: every distance against the oracle."""
+    E, C = long_docs
+    qi, qw = synth.query(np.random.default_rng(200 + vr), C.V, vr)
+    corpus = swmd.corpus_from_synth(E, C, path="resident", solver=SOLVER_COLS)
+    assert swmd.swmd_get_mapping(corpus, vr, "resident")[0] == (16 if vr <= 16 else 32)
+    for lam in (1.0, 10.0):
+        got = swmd.swmd_query(corpus, qi, qw, lam, t)
+        assert rel_err(got, oracle_wmd(E, C, qi, qw, lam, t)) <= RTOL, (vr, t, lam)
+
+
+@pytest.mark.parametrize("kprec", ["bf16", "fp16"])
+def test_long_buckets_reduced_precision(long_docs, kprec):
+    E, C = long_docs
+    corpus = swmd.corpus_from_synth(E, C, path="resident", solver=SOLVER_COLS, k_precision=kprec)
+    for vr in (12, 30):
+        qi, qw = synth.query(np.random.default_rng(vr), C.V, vr)
+        for lam in (1.0, 10.0):
+            err = rel_err(swmd.swmd_query(corpus, qi, qw, lam, 15), oracle_wmd(E, C, qi, qw, lam, 15))
+            assert err <= BOUND[kprec], (kprec, vr, lam, err)
+
+
+def test_long_buckets_invariances(long_docs):
+    """The mixed launch gives the same bits in any document range, batched and
+    served; and agrees with the register solver alone within the tolerance."""
+    E, C = long_docs
+    rp, col, val = C.csr()
+    qi, qw = synth.query(np.random.default_rng(77), C.V, 24)
+    whole = swmd.swmd_query(swmd.swmd_create_corpus(C.V, C.N, rp, col, val, E, path="resident",
+                                                    solver=SOLVER_COLS), qi, qw, 1.0, 15)
+    cut = [0, 61, 170, C.N]
+    parts = [swmd.swmd_query(swmd.swmd_create_corpus(C.V, C.N, rp, col, val, E, path="resident",
+                                                     solver=SOLVER_COLS, doc_begin=a, doc_end=b),
+                             qi, qw, 1.0, 15) for a, b in zip(cut[:-1], cut[1:])]
+    np.testing.assert_array_equal(np.concatenate(parts), whole)
+    regs = swmd.swmd_query(swmd.corpus_from_synth(E, C, path="resident", solver=1), qi, qw, 1.0, 15)
+    assert rel_err(whole, regs) <= RTOL
+    corpus = swmd.corpus_from_synth(E, C, path="resident", solver=SOLVER_COLS)
+    qs = synth.batch_queries(C.V, 9, 1, 32, seed=81)
+    alone = [swmd.swmd_query(corpus, q, w, 1.0, 15) for q, w in qs]
+    batch = swmd.swmd_query_batch(corpus, qs, 1.0, 15)
+    for i in range(len(qs)):
+        np.testing.assert_array_equal(batch[i], alone[i])
+    srv = swmd.swmd_serve_start(corpus, max_batch=4, memory_budget=1 << 28)
+    tickets = [swmd.swmd_serve_submit(srv, q, w, 1.0, 15) for q, w in qs]
+    for tk, ref in zip(tickets, alone):
+        np.testing.assert_array_equal(swmd.swmd_serve_wait(srv, tk, 60000), ref)
+    srv.stop()
 
 
 def test_batch_and_server_equal_alone_bitwise(short_docs):

@@ -350,7 +350,7 @@ def test_autotune_then_query_matches_oracle(paper, vr):
     res = swmd.swmd_autotune(corpus, vr, 3)
     assert res["candidates"] >= 2 and res["best_ms"] > 0
     assert res["best_ms"] <= res["default_ms"] * 1.0001
-    assert res["solver"] in (0, 1, 2) and res["vrp"] >= vr
+    assert res["solver"] in (0, 1, 2, 4) and res["vrp"] >= vr
     qi, qw = synth.query(np.random.default_rng(vr), C.V, vr)
     got = swmd.swmd_query(corpus, qi, qw, 1.0, 15)
     assert rel_err(got, oracle_wmd(E, C, qi, qw, 1.0, 15)) <= RTOL
