@@ -64,8 +64,9 @@ extern "C" {
  *             independent problems in Algorithm 1.
  *   AUTO:     RESIDENT or FUSED for each query: the choice swmd_autotune measured
  *             for its v_r, else RESIDENT when the resident solver is the
- *             column-split one (swmd_options.solver 4, the default on corpora of
- *             documents up to 32 words), else RESIDENT for corpora under 20,000
+ *             column-split one and it holds every document (swmd_options.solver 4,
+ *             the default on corpora of documents up to 32 words), else RESIDENT
+ *             for corpora under 20,000
  *             documents or v_r up to 24 and FUSED otherwise (on large corpora the
  *             per-iteration walk beats the other resident solvers for wide queries).  The choice depends only on v_r and
  *             the tuning, so a query's result is the same alone, batched or served. */
