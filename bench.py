@@ -388,8 +388,8 @@ def compare_paths(swmd, corpus, d_ids, d_r, d_out, d_status, flush, stream, vr, 
     import torch
     res = {}
     reps = 50
-    for path in ("resident", "fused", "plain"):
-        swmd.swmd_corpus_set_options(corpus, path=path)
+
+    def timed(path):
         times = []
         with torch.cuda.stream(stream):
             for k in range(reps + 3):
@@ -404,6 +404,19 @@ def compare_paths(swmd, corpus, d_ids, d_r, d_out, d_status, flush, stream, vr, 
         torch.cuda.synchronize()
         ms = statistics.mean(a.elapsed_time(b) for a, b in times)
         res[path] = {"ms_per_query": ms, "wmds_per_s": C.N / (ms * 1e-3)}
+
+    for path in ("resident", "fused", "plain"):
+        swmd.swmd_corpus_set_options(corpus, path=path)
+        timed(path)
+    # the column-split solver with its buckets of up to 96 rows and the longest
+    # documents on the register solver (solver 4; not the automatic choice here): a
+    # supplementary figure, which cannot cost the line
+    try:
+        swmd.swmd_corpus_set_options(corpus, path="resident", solver=4)
+        timed("resident_long_buckets")
+    except Exception as e:
+        res["resident_long_buckets"] = {"error": str(e)[:200]}
+    swmd.swmd_corpus_set_options(corpus, path="auto", solver=0)
     res["iteration_kernel"] = iteration_kernels(swmd, corpus, d_ids, d_r, d_status, flush, stream,
                                                 vr, lam, info, C, peaks, kb)
     swmd.swmd_corpus_set_options(corpus, path="auto")
