@@ -434,7 +434,9 @@ inline size_t cost_tile_smem(int d4, int vrp) {
 }
 
 // 16 bytes global -> shared on the asynchronous path (L2 only); valid = false
-// copies nothing and writes zeros.
+// copies nothing and writes zeros.  No memory clobber: the copies only target a
+// stage buffer that every thread finished reading before the barrier preceding
+// their issue, and the wait below (which has one) orders the reads after them.
 __device__ __forceinline__ void cp_async16_zfill(float *smem, const float *gmem, bool valid) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     const int n = valid ? 16 : 0;
